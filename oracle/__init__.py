@@ -1,0 +1,155 @@
+"""CPU oracle for exact DTW alignment -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+(and its ``--impl reference`` arm) may import this package.  The product path
+never does, and this package imports nothing from the product package.
+
+Wraps ``dtw_oracle.c`` (plain C, FP64 / int64):
+
+* :func:`dtw`       -- oracle 1, textbook DTW with backpointers and backtrace
+                       (Section 2.1, Eq. "recurrence" and Eq. "dtwboundary"),
+                       ties broken DIAG, then UP, then LEFT.
+* :func:`linmdtw`   -- oracle 2, the divide-and-conquer linear-memory alignment
+                       (Algorithm 2 with Algorithm 1 as its sweep), counting
+                       processed cells (Section 3.2).
+* :func:`acc_matrix`-- whole forward D or backward B matrix (small cases), for
+                       the split-cost identity of Lemma 2.
+* :func:`path_cost` -- sum of C along a path (re-scoring in FP64 / int64).
+
+Parity status: every function here is pinned by ``tests/test_oracle.py``
+against brute-force enumeration, closed forms and invariants.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = [os.path.join(_HERE, "dtw_oracle.c"), os.path.join(_HERE, "oracle_impl.h")]
+
+EUCLID_F32 = 0
+ABS_I32 = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add) if it is stale."""
+    stale = force or not os.path.exists(_SO) or any(
+        os.path.getmtime(s) > os.path.getmtime(_SO) for s in _SRC)
+    if stale:
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c99", "-Wall", "-ffp-contract=off", "-shared", "-fPIC",
+             _SRC[0], "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        p, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.oracle_dtw.argtypes = [p, i64, p, i64, i32, i32, p, p, p, p]
+        lib.oracle_linmdtw.argtypes = [p, i64, p, i64, i32, i32, i64, p, p, p, p, p]
+        lib.oracle_acc_matrix.argtypes = [p, i64, p, i64, i32, i32, i32, p, p]
+        lib.oracle_path_cost.argtypes = [p, i64, p, i64, i32, i32, p, i64, p, p]
+        for f in (lib.oracle_dtw, lib.oracle_linmdtw, lib.oracle_acc_matrix, lib.oracle_path_cost):
+            f.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _prep(X, Y):
+    """Returns contiguous (X, Y, M, N, d, kind) from 1-D/2-D float32 or int32 arrays."""
+    X = np.asarray(X)
+    Y = np.asarray(Y)
+    if X.dtype != Y.dtype:
+        raise TypeError("X and Y must share a dtype")
+    if X.dtype == np.int32:
+        kind = ABS_I32
+        X = np.ascontiguousarray(X.reshape(-1))
+        Y = np.ascontiguousarray(Y.reshape(-1))
+        d = 1
+    elif X.dtype == np.float32:
+        kind = EUCLID_F32
+        if X.ndim == 1:
+            X = X[:, None]
+        if Y.ndim == 1:
+            Y = Y[:, None]
+        X = np.ascontiguousarray(X)
+        Y = np.ascontiguousarray(Y)
+        if X.shape[1] != Y.shape[1]:
+            raise ValueError("feature dimensions differ")
+        d = X.shape[1]
+    else:
+        raise TypeError("features must be float32 (Euclidean) or int32 (|x-y|)")
+    return X, Y, X.shape[0], Y.shape[0], d, kind
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _cost(kind, c, ci):
+    return int(ci.value) if kind == ABS_I32 else float(c.value)
+
+
+def dtw(X, Y):
+    """Oracle 1.  Returns (path as int32 array of shape (K, 2), optimal cost).
+
+    The cost is an ``int`` for int32 inputs (exact int64 sum) and a ``float``
+    (FP64) for float32 inputs."""
+    X, Y, M, N, d, kind = _prep(X, Y)
+    path = np.empty((M + N - 1, 2), dtype=np.int32)
+    K, c, ci = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+    rc = _L().oracle_dtw(_ptr(X), M, _ptr(Y), N, d, kind, _ptr(path), ctypes.byref(K),
+                         ctypes.byref(c), ctypes.byref(ci))
+    if rc != 0:
+        raise RuntimeError(f"oracle_dtw failed: {rc}")
+    return path[:K.value].copy(), _cost(kind, c, ci)
+
+
+def linmdtw(X, Y, m: int = 500):
+    """Oracle 2 (Algorithm 2).  Returns (path, cost of that path, processed cells)."""
+    X, Y, M, N, d, kind = _prep(X, Y)
+    path = np.empty((M + N - 1, 2), dtype=np.int32)
+    K, c, ci, cells = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    rc = _L().oracle_linmdtw(_ptr(X), M, _ptr(Y), N, d, kind, int(m), _ptr(path), ctypes.byref(K),
+                             ctypes.byref(c), ctypes.byref(ci), ctypes.byref(cells))
+    if rc != 0:
+        raise RuntimeError(f"oracle_linmdtw failed: {rc}")
+    return path[:K.value].copy(), _cost(kind, c, ci), int(cells.value)
+
+
+def acc_matrix(X, Y, reverse: bool = False):
+    """Whole forward D (reverse=False) or backward B (reverse=True) matrix."""
+    X, Y, M, N, d, kind = _prep(X, Y)
+    if kind == ABS_I32:
+        out = np.empty((M, N), dtype=np.int64)
+        rc = _L().oracle_acc_matrix(_ptr(X), M, _ptr(Y), N, d, kind, int(reverse), None, _ptr(out))
+    else:
+        out = np.empty((M, N), dtype=np.float64)
+        rc = _L().oracle_acc_matrix(_ptr(X), M, _ptr(Y), N, d, kind, int(reverse), _ptr(out), None)
+    if rc != 0:
+        raise RuntimeError(f"oracle_acc_matrix failed: {rc}")
+    return out
+
+
+def path_cost(X, Y, path):
+    """Sum of C(i, j) over the (K, 2) array of path cells, in path order."""
+    X, Y, M, N, d, kind = _prep(X, Y)
+    path = np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1, 2))
+    c, ci = ctypes.c_double(), ctypes.c_int64()
+    rc = _L().oracle_path_cost(_ptr(X), M, _ptr(Y), N, d, kind, _ptr(path), path.shape[0],
+                               ctypes.byref(c), ctypes.byref(ci))
+    if rc != 0:
+        raise RuntimeError(f"oracle_path_cost failed: {rc}")
+    return _cost(kind, c, ci)

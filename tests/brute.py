@@ -1,0 +1,102 @@
+"""Brute-force DTW by enumerating every warping path (tiny inputs only).
+
+Independent of the oracle and of the CUDA path: the frame cost is evaluated here
+in plain Python (double, dims in ascending order, correctly rounded sqrt), and a
+path's cost is its cost terms summed from the first cell to the last.
+
+A warping path (Section 2.1) starts at (0,0), ends at (M-1,N-1) and advances by
+(0,1), (1,0) or (1,1).  Among all optimal paths, the "canonical" one is the path
+whose sequence of moves, read backward from (M-1,N-1), is lexicographically
+smallest with DIAG < UP < LEFT -- the path a backtrace yields when each
+backpointer is the first minimum in the order DIAG, UP, LEFT.
+"""
+from __future__ import annotations
+
+import math
+from math import comb
+
+DIAG, UP, LEFT = 0, 1, 2
+
+
+def frame_cost(x, y):
+    if isinstance(x, (int,)) or (hasattr(x, "dtype") and x.dtype.kind == "i" and x.ndim == 0):
+        return abs(int(x) - int(y))
+    s = 0.0
+    for a, b in zip(x, y):
+        t = float(a) - float(b)
+        s = s + t * t
+    return math.sqrt(s)
+
+
+def cost_table(X, Y):
+    return [[frame_cost(X[i], Y[j]) for j in range(len(Y))] for i in range(len(X))]
+
+
+def all_paths(M, N):
+    """Every warping path from (0,0) to (M-1,N-1), as lists of cells."""
+    out = []
+
+    def rec(i, j, acc):
+        acc.append((i, j))
+        if i == M - 1 and j == N - 1:
+            out.append(list(acc))
+        else:
+            if j + 1 < N:
+                rec(i, j + 1, acc)
+            if i + 1 < M:
+                rec(i + 1, j, acc)
+            if i + 1 < M and j + 1 < N:
+                rec(i + 1, j + 1, acc)
+        acc.pop()
+
+    rec(0, 0, [])
+    return out
+
+
+def delannoy(m, n):
+    """Closed form for the number of lattice paths with steps E, N, NE."""
+    return sum(comb(m, k) * comb(n, k) * (1 << k) for k in range(min(m, n) + 1))
+
+
+def backward_moves(path):
+    mv = []
+    for (i1, j1), (i0, j0) in zip(path[:0:-1], path[-2::-1]):
+        if i1 - i0 == 1 and j1 - j0 == 1:
+            mv.append(DIAG)
+        elif i1 - i0 == 1:
+            mv.append(UP)
+        else:
+            mv.append(LEFT)
+    return tuple(mv)
+
+
+def solve(X, Y):
+    """(optimal cost, canonical path, number of optimal paths, number of paths)."""
+    M, N = len(X), len(Y)
+    C = cost_table(X, Y)
+    best = None
+    opt = []
+    paths = all_paths(M, N)
+    for p in paths:
+        s = 0
+        for (i, j) in p:
+            s = s + C[i][j]
+        if best is None or s < best:
+            best = s
+            opt = [p]
+        elif s == best:
+            opt.append(p)
+    canon = min(opt, key=backward_moves)
+    return best, canon, len(opt), len(paths)
+
+
+def prefix_optimum(X, Y, i, j):
+    """Optimal cost over warping paths from (0,0) to (i,j)."""
+    return solve(X[: i + 1], Y[: j + 1])[0]
+
+
+def suffix_optimum(X, Y, i, j):
+    """Optimal cost over warping paths from (i,j) to (M-1,N-1), C(i,j) included,
+    summed from the last cell back to (i,j)."""
+    Xr, Yr = X[i:][::-1], Y[j:][::-1]
+    return solve(Xr, Yr)[0]
