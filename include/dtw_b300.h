@@ -1,0 +1,188 @@
+/*
+ * dtw_b300.h -- C ABI of the B300 (sm_103a) exact linear-memory DTW alignment
+ * library (Tralie & Dempsey, "Exact, Parallelizable Dynamic Time Warping
+ * Alignment with Linear Memory").
+ *
+ * Problem (Section 2.1): X holds M frames and Y holds N frames of dimension d.
+ * A warping path is a list of K index pairs starting at (0,0), ending at
+ * (M-1,N-1), each step adding (0,1), (1,0) or (1,1).  Its cost is the sum of the
+ * frame costs C(i,j) over its pairs; DTW finds a path of minimum cost D*.
+ * Frame costs: Euclidean distance of FP32 frames (Section 4.1) or |x - y| of
+ * int32 samples (d must be 1).
+ *
+ * The library computes D* and an optimal path with the divide-and-conquer
+ * recursion of Section 3.2 (Algorithm 2): at each level every box of the level
+ * is swept by a tiled wavefront (Algorithm 1's anti-diagonal order, Section 3.1)
+ * that keeps only O(M+N) boundary state, a split row fixes one path cell per box
+ * (Lemmas 1 and 2), and boxes below a size cutoff finish with a full-table DP
+ * and backtrace (Section 2.1).
+ *
+ * Tie rule: the returned path is the path a textbook backtrace yields when each
+ * backpointer is the first minimum in the order DIAG (i-1,j-1), UP (i-1,j),
+ * LEFT (i,j-1).  For DTW_ABS_I32 the result is exact (int accumulation) and the
+ * path is that canonical path bit for bit.  For DTW_EUCLID_F32 the frame cost
+ * is evaluated in FP32 and accumulated in FP64; the cost is within 1e-6
+ * relative of the FP64 optimum and the path is optimal within that tolerance
+ * (another path of equal cost may be returned).
+ *
+ * Memory: the caller owns X, Y, the path buffers and every output.  The library
+ * owns a device workspace of dtw_footprint() bytes that grows on demand
+ * (cudaMalloc) unless the caller provides an arena with dtw_set_arena().
+ *
+ * Pointers: X, Y and path_out may be host or device pointers; the library
+ * detects which (cudaPointerGetAttributes) and stages host buffers through its
+ * workspace.  All work runs on the stream set with dtw_set_stream() (default:
+ * the legacy default stream) on the current device.
+ *
+ * Errors: every call returns a status (negative on error, see dtw_status); no
+ * call aborts the process or throws.  The library is not re-entrant: calls
+ * from several host threads are serialised by an internal lock.
+ */
+#ifndef DTW_B300_H
+#define DTW_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DTW_API __attribute__((visibility("default")))
+#else
+#define DTW_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Frame cost kinds: the low byte of cost_kind. */
+enum dtw_kind {
+    DTW_EUCLID_F32 = 0, /* sqrt(sum_k (x_k - y_k)^2) of FP32 frames; FP64 accumulation */
+    DTW_ABS_I32 = 1     /* |x - y| of int32 samples (d == 1); exact int accumulation */
+};
+
+/* Form flags, OR-ed into cost_kind. */
+enum dtw_form {
+    /* The paper's own GPU design (Algorithm 1 inside Algorithm 2): one kernel
+     * launch per anti-diagonal, one thread per cell, three rotating diagonal
+     * buffers, FP64 cost and accumulation, recursion on the host, textbook DTW
+     * when a box side drops below 500 (Section 3.2).  It is the comparator the
+     * tiled path is measured against; its path is optimal but, under ties, not
+     * necessarily the canonical one. */
+    DTW_PLAIN_F64 = 1 << 8
+};
+
+enum dtw_status {
+    DTW_OK = 0,
+    DTW_PENDING = 1,    /* dtw_poll: the request has not finished */
+    DTW_EINVAL = -1,    /* bad argument (null pointer, M or N < 1, d mismatch, unknown kind) */
+    DTW_ENOMEM = -2,    /* workspace allocation failed or exceeds the budget */
+    DTW_ECUDA = -3,     /* a CUDA runtime call failed */
+    DTW_ETIMEOUT = -4,  /* a device-side wait exceeded its bound; the call was abandoned */
+    DTW_EOVERFLOW = -5, /* max|x-y| * (M+N-1) does not fit the exact integer accumulator */
+    DTW_EBUSY = -6,     /* the serving queue is full */
+    DTW_EINTERNAL = -7  /* a device-side consistency check failed (a library bug) */
+};
+
+/*
+ * dtw_align -- exact DTW cost and optimal warping path of one pair.
+ *   X        M*d row-major frames (float for DTW_EUCLID_F32, int32 for DTW_ABS_I32)
+ *   Y        N*d row-major frames of the same type
+ *   d        feature dimension (1 for DTW_ABS_I32)
+ *   path_out capacity 2*(M+N-1) int32; receives K (i,j) pairs, (0,0) first
+ *   cost_out host double; receives D* (exact integer value for DTW_ABS_I32)
+ * Returns K (the path length, max(M,N) <= K <= M+N-1) or a negative dtw_status.
+ * Blocks until the result is in path_out and *cost_out.
+ */
+DTW_API int64_t dtw_align(const void* X, int64_t M, const void* Y, int64_t N, int32_t d,
+                  int32_t cost_kind, int32_t* path_out, double* cost_out);
+
+/*
+ * dtw_cost -- D* only: one forward sweep of the whole accumulated-cost matrix
+ * (Section 3.1), O(M+N) memory, no path.  Same arguments as dtw_align.
+ * Returns DTW_OK or a negative dtw_status.
+ */
+DTW_API int dtw_cost(const void* X, int64_t M, const void* Y, int64_t N, int32_t d, int32_t cost_kind,
+             double* cost_out);
+
+/*
+ * dtw_align_batch -- B independent pairs of uneven lengths, all aligned
+ * together: every pair's boxes of a recursion level go out in the same kernel
+ * launches.  X[b], Y[b], path_out[b] as in dtw_align (path_out[b] capacity
+ * 2*(M[b]+N[b]-1) int32); K_out[b] and cost_out[b] receive path length and D*.
+ * All pairs share d and cost_kind.  Returns DTW_OK or a negative dtw_status
+ * (which then applies to the whole batch).
+ */
+DTW_API int dtw_align_batch(int32_t B, const void* const* X, const int64_t* M, const void* const* Y,
+                    const int64_t* N, int32_t d, int32_t cost_kind, int32_t* const* path_out,
+                    int64_t* K_out, double* cost_out);
+
+/* One request of the asynchronous interface. */
+typedef struct dtw_request {
+    const void* X;
+    int64_t M;
+    const void* Y;
+    int64_t N;
+    int32_t d;
+    int32_t cost_kind;
+    int32_t* path_out; /* capacity 2*(M+N-1) int32, host or device */
+} dtw_request;
+
+/*
+ * dtw_submit -- queue one alignment.  Returns a ticket >= 0 or a negative
+ * dtw_status.  The request's buffers must stay valid until dtw_poll() for the
+ * ticket returns something other than DTW_PENDING.
+ * dtw_poll -- DTW_PENDING while running; DTW_OK once *K_out and *cost_out hold
+ * the result (the ticket is then released); or a negative dtw_status.
+ */
+DTW_API int64_t dtw_submit(const dtw_request* r);
+DTW_API int dtw_poll(int64_t ticket, int64_t* K_out, double* cost_out);
+
+/* Stream for all subsequent work (a cudaStream_t; NULL = legacy default). */
+DTW_API int dtw_set_stream(void* cuda_stream);
+
+/* Device-memory budget for admission (0 = unlimited).  A call whose
+ * dtw_footprint() exceeds it fails with DTW_ENOMEM before touching the GPU. */
+DTW_API int dtw_set_budget(uint64_t bytes);
+
+/* Caller-provided device arena (256-byte aligned) used instead of cudaMalloc for
+ * the workspace; NULL releases it.  The arena must outlive every call made while
+ * it is set. */
+DTW_API int dtw_set_arena(void* device_ptr, uint64_t bytes);
+
+/* Workspace bytes dtw_align needs for one pair; linear in M+N (Section 4.3's
+ * memory argument): features staged from the host, per-level boundary rows,
+ * box lists and the path. */
+DTW_API size_t dtw_footprint(int64_t M, int64_t N, int32_t d, int32_t cost_kind);
+
+DTW_API const char* dtw_strerror(int status);
+
+/* Counters of the most recent dtw_align / dtw_cost / dtw_align_batch call. */
+typedef struct dtw_stats {
+    int64_t problem_cells;   /* sum of M*N over the pairs */
+    int64_t sweep_cells;     /* cells evaluated by wavefront sweeps */
+    int64_t tag_cells;       /* of which carried a split tag (integer kind) */
+    int64_t base_cells;      /* cells evaluated by full-table base cases */
+    int32_t levels;          /* recursion levels swept */
+    int32_t sweep_launches;  /* sweep kernel launches */
+    int32_t base_boxes;      /* boxes finished by the base-case kernel */
+    int32_t kernel_launches; /* CUDA kernels the call launched */
+    double sweep_ms;         /* summed device time of the sweep launches (timing on) */
+    double device_ms;        /* device time of the whole call (timing on) */
+} dtw_stats;
+
+DTW_API int dtw_get_stats(dtw_stats* out);
+
+/* Tuning and instrumentation switches (dtw_set_option keys). */
+enum dtw_option {
+    DTW_OPT_TIMING = 1,      /* 1: record CUDA events around each launch (default 0) */
+    DTW_OPT_BASE_AREA = 2,   /* boxes of at most this many cells finish in the base case */
+    DTW_OPT_SPIN_LIMIT = 3,  /* polls before a device-side wait gives up (DTW_ETIMEOUT) */
+    DTW_OPT_SKIP_PUBLISH = 4 /* test hook: one band never publishes (exercises DTW_ETIMEOUT) */
+};
+DTW_API int dtw_set_option(int32_t key, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DTW_B300_H */

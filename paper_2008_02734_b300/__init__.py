@@ -1,0 +1,280 @@
+"""Exact linear-memory DTW alignment on B300 (sm_103a): thin Python binding.
+
+Every function here only marshals arguments for the C ABI declared in
+``include/dtw_b300.h`` and implemented in ``libdtw_b300.so`` (CUDA kernels for
+the divide-and-conquer recursion of Section 3.2).  There is no Python or CPU
+fallback: the first call into the library fails if it has not been built.
+
+Inputs may be torch tensors (CPU or CUDA) or numpy arrays: float32 frames of
+shape (M, d) use the Euclidean frame cost, int32 sequences of shape (M,) use
+|x - y|.  CUDA inputs are aligned on the tensors' device with the current torch
+stream; host inputs are staged by the library (host-to-device copy inside the
+call).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libdtw_b300.so")
+
+EUCLID_F32 = 0
+ABS_I32 = 1
+PLAIN_F64 = 1 << 8
+
+OK, PENDING, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBUSY, EINTERNAL = 0, 1, -1, -2, -3, -4, -5, -6, -7
+OPT_TIMING, OPT_BASE_AREA, OPT_SPIN_LIMIT, OPT_SKIP_PUBLISH = 1, 2, 3, 4
+
+
+class DTWError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {_strerror(status)} ({status})")
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("problem_cells", ctypes.c_int64), ("sweep_cells", ctypes.c_int64),
+                ("tag_cells", ctypes.c_int64), ("base_cells", ctypes.c_int64),
+                ("levels", ctypes.c_int32), ("sweep_launches", ctypes.c_int32),
+                ("base_boxes", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("sweep_ms", ctypes.c_double), ("device_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("M", ctypes.c_int64), ("Y", ctypes.c_void_p), ("N", ctypes.c_int64),
+                ("d", ctypes.c_int32), ("cost_kind", ctypes.c_int32), ("path_out", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+    sig = {
+        "dtw_align": (i64, [vp, i64, vp, i64, i32, i32, vp, vp]),
+        "dtw_cost": (ctypes.c_int, [vp, i64, vp, i64, i32, i32, vp]),
+        "dtw_align_batch": (ctypes.c_int, [i32, vp, vp, vp, vp, i32, i32, vp, vp, vp]),
+        "dtw_submit": (i64, [vp]),
+        "dtw_poll": (ctypes.c_int, [i64, vp, vp]),
+        "dtw_set_stream": (ctypes.c_int, [vp]),
+        "dtw_set_budget": (ctypes.c_int, [u64]),
+        "dtw_set_arena": (ctypes.c_int, [vp, u64]),
+        "dtw_footprint": (ctypes.c_size_t, [i64, i64, i32, i32]),
+        "dtw_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "dtw_get_stats": (ctypes.c_int, [vp]),
+        "dtw_set_option": (ctypes.c_int, [i32, i64]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB_PATH = _LIB_PATH
+_lib = None
+
+
+def _get_lib():
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+def __getattr__(name):
+    # the ctypes library is loaded on first use, so that ``synth`` imports without it
+    if name == "lib":
+        return _get_lib()
+    raise AttributeError(name)
+
+# exported names of the C ABI, for the symbol check
+ABI_FUNCTIONS = ("dtw_align", "dtw_cost", "dtw_align_batch", "dtw_submit", "dtw_poll", "dtw_set_stream",
+                 "dtw_set_budget", "dtw_set_arena", "dtw_footprint", "dtw_strerror", "dtw_get_stats",
+                 "dtw_set_option")
+
+
+def _strerror(status: int) -> str:
+    return _get_lib().dtw_strerror(int(status)).decode()
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise DTWError(int(rc), where)
+    return rc
+
+
+# ------------------------------------------------------------------ marshalling
+
+def _as_buffer(a):
+    """(object kept alive, data pointer, shape, dtype-kind, is_cuda) of a tensor or array."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                a = a.contiguous()
+            kind = {torch.float32: EUCLID_F32, torch.int32: ABS_I32}.get(a.dtype)
+            if kind is None:
+                raise TypeError("frames must be float32 (Euclidean) or int32 (|x-y|)")
+            return a, a.data_ptr(), tuple(a.shape), kind, a.is_cuda
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(a)
+    kind = {np.dtype(np.float32): EUCLID_F32, np.dtype(np.int32): ABS_I32}.get(a.dtype)
+    if kind is None:
+        raise TypeError("frames must be float32 (Euclidean) or int32 (|x-y|)")
+    return a, a.ctypes.data, a.shape, kind, False
+
+
+def _dims(shape, kind):
+    if kind == ABS_I32:
+        if len(shape) == 2 and shape[1] != 1:
+            raise ValueError("int32 sequences are 1-D")
+        return shape[0], 1
+    if len(shape) == 1:
+        return shape[0], 1
+    return shape[0], shape[1]
+
+
+def _prep_pair(X, Y):
+    xo, xp, xs, xk, xc = _as_buffer(X)
+    yo, yp, ys, yk, yc = _as_buffer(Y)
+    if xk != yk:
+        raise TypeError("X and Y must have the same dtype")
+    M, dx = _dims(xs, xk)
+    N, dy = _dims(ys, yk)
+    if dx != dy:
+        raise ValueError("feature dimensions differ")
+    return (xo, yo), xp, M, yp, N, dx, xk, (xc or yc), (xo if xc else yo if yc else None)
+
+
+def _sync_stream(cuda_tensor):
+    """Run on the tensor's device and the current torch stream."""
+    import torch
+    dev = cuda_tensor.device
+    torch.cuda.set_device(dev)
+    _get_lib().dtw_set_stream(ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream))
+
+
+def _path_buffer(M, N, like_cuda):
+    import torch
+    if like_cuda is not None:
+        return torch.empty((M + N - 1, 2), dtype=torch.int32, device=like_cuda.device)
+    return torch.empty((M + N - 1, 2), dtype=torch.int32)
+
+
+def align(X, Y, *, plain: bool = False, path_out=None):
+    """Exact DTW of one pair: returns (path as an int32 tensor of shape (K, 2), D*).
+
+    ``plain=True`` runs the paper's plain FP64 form (one launch per anti-diagonal)
+    instead of the tiled path.  ``path_out`` may supply the (M+N-1, 2) int32 output
+    buffer (host or device)."""
+    keep, xp, M, yp, N, d, kind, on_cuda, cu = _prep_pair(X, Y)
+    if cu is not None:
+        _sync_stream(cu)
+    path = _path_buffer(M, N, cu) if path_out is None else path_out
+    ck = kind | (PLAIN_F64 if plain else 0)
+    cost = ctypes.c_double()
+    K = _get_lib().dtw_align(xp, M, yp, N, d, ck, ctypes.c_void_p(path.data_ptr()), ctypes.byref(cost))
+    _check(K, "dtw_align")
+    c = cost.value
+    return path[:K], (int(c) if kind == ABS_I32 else c)
+
+
+def cost(X, Y):
+    """D* only (one forward sweep, no path)."""
+    keep, xp, M, yp, N, d, kind, on_cuda, cu = _prep_pair(X, Y)
+    if cu is not None:
+        _sync_stream(cu)
+    c = ctypes.c_double()
+    _check(_get_lib().dtw_cost(xp, M, yp, N, d, kind, ctypes.byref(c)), "dtw_cost")
+    return int(c.value) if kind == ABS_I32 else c.value
+
+
+def align_batch(Xs, Ys):
+    """Aligns B pairs together; returns a list of (path, D*)."""
+    B = len(Xs)
+    if B != len(Ys) or B == 0:
+        raise ValueError("need equally many, and at least one, X and Y")
+    keep, xps, yps, Ms, Ns, paths = [], [], [], [], [], []
+    d0 = kind0 = None
+    cu0 = None
+    for X, Y in zip(Xs, Ys):
+        k, xp, M, yp, N, d, kind, on_cuda, cu = _prep_pair(X, Y)
+        if d0 is None:
+            d0, kind0 = d, kind
+        elif (d, kind) != (d0, kind0):
+            raise ValueError("all pairs of a batch share dtype and feature dimension")
+        cu0 = cu0 if cu0 is not None else cu
+        keep.append(k)
+        xps.append(xp)
+        yps.append(yp)
+        Ms.append(M)
+        Ns.append(N)
+        paths.append(_path_buffer(M, N, cu))
+    if cu0 is not None:
+        _sync_stream(cu0)
+    VP = ctypes.c_void_p * B
+    I64 = ctypes.c_int64 * B
+    K = I64()
+    C = (ctypes.c_double * B)()
+    rc = _get_lib().dtw_align_batch(B, VP(*xps), I64(*Ms), VP(*yps), I64(*Ns), d0, kind0,
+                             VP(*[p.data_ptr() for p in paths]), K, C)
+    _check(rc, "dtw_align_batch")
+    return [(paths[b][:K[b]], int(C[b]) if kind0 == ABS_I32 else C[b]) for b in range(B)]
+
+
+def submit(X, Y, path_out=None):
+    """Queues one alignment; returns (ticket, path buffer, keep-alive)."""
+    keep, xp, M, yp, N, d, kind, on_cuda, cu = _prep_pair(X, Y)
+    if cu is not None:
+        _sync_stream(cu)
+    path = _path_buffer(M, N, cu) if path_out is None else path_out
+    r = Request(xp, M, yp, N, d, kind, path.data_ptr())
+    t = _check(_get_lib().dtw_submit(ctypes.byref(r)), "dtw_submit")
+    return t, path, keep
+
+
+def poll(ticket: int):
+    """(status, K, D*) of a submitted request."""
+    K, c = ctypes.c_int64(), ctypes.c_double()
+    rc = _get_lib().dtw_poll(int(ticket), ctypes.byref(K), ctypes.byref(c))
+    return rc, K.value, c.value
+
+
+def footprint(M: int, N: int, d: int = 1, kind: int = ABS_I32) -> int:
+    return int(_get_lib().dtw_footprint(M, N, d, kind))
+
+
+def set_budget(nbytes: int) -> None:
+    _check(_get_lib().dtw_set_budget(int(nbytes)), "dtw_set_budget")
+
+
+def set_arena(tensor_or_none) -> None:
+    """Hands a CUDA tensor's storage to the library as its workspace (None releases it)."""
+    if tensor_or_none is None:
+        _check(_get_lib().dtw_set_arena(None, 0), "dtw_set_arena")
+    else:
+        t = tensor_or_none
+        _check(_get_lib().dtw_set_arena(ctypes.c_void_p(t.data_ptr()), t.numel() * t.element_size()), "dtw_set_arena")
+
+
+def set_option(key: int, value: int) -> None:
+    _check(_get_lib().dtw_set_option(int(key), int(value)), "dtw_set_option")
+
+
+def set_stream(stream) -> None:
+    _get_lib().dtw_set_stream(ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream))
+
+
+def get_stats() -> dict:
+    s = Stats()
+    _check(_get_lib().dtw_get_stats(ctypes.byref(s)), "dtw_get_stats")
+    return s.as_dict()

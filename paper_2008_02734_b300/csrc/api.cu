@@ -1,0 +1,610 @@
+// C ABI of the library: argument checks, workspace, staging of host buffers,
+// and the host side of the level loop of Algorithm 2 (Section 3.2).  The device
+// does all the arithmetic; per level the host launches plan -> sweep -> split
+// and reads back one small control block to learn whether another level exists.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "dtw_b300.h"
+#include "dtw_common.cuh"
+#include "dtw_kernels.h"
+
+using namespace dtwb;
+
+namespace {
+
+struct Ctx {
+    std::mutex mu;
+    cudaStream_t stream = nullptr;
+    uint64_t budget = 0;
+    void* arena = nullptr;
+    uint64_t arena_bytes = 0;
+    void* ws = nullptr;  // library-owned workspace
+    size_t ws_bytes = 0;
+    int timing = 0;
+    long long base_area = 16384;
+    int spin_limit = 1 << 24;
+    long long skip_publish = -1;
+    int num_sms = 0;
+    int device = -1;
+    dtw_stats stats = {};
+    // asynchronous interface
+    long long next_ticket = 0;
+    struct Done {
+        int status;
+        int64_t K;
+        double cost;
+    };
+    std::unordered_map<long long, Done> done;
+};
+
+Ctx& ctx() {
+    static Ctx c;
+    return c;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int ensure_device(Ctx& c) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DTW_ECUDA;
+    if (dev != c.device || c.num_sms == 0) {
+        if (cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return DTW_ECUDA;
+        if (c.ws) {
+            cudaFree(c.ws);
+            c.ws = nullptr;
+            c.ws_bytes = 0;
+        }
+        c.device = dev;
+    }
+    return DTW_OK;
+}
+
+// Returns a device workspace of at least `bytes` (the arena or a cached cudaMalloc).
+int workspace(Ctx& c, size_t bytes, void** out) {
+    if (c.budget && bytes > c.budget) return DTW_ENOMEM;
+    if (c.arena) {
+        if (bytes > c.arena_bytes) return DTW_ENOMEM;
+        *out = c.arena;
+        return DTW_OK;
+    }
+    if (c.ws_bytes < bytes) {
+        if (c.ws) {
+            cudaStreamSynchronize(c.stream);
+            cudaFree(c.ws);
+            c.ws = nullptr;
+            c.ws_bytes = 0;
+        }
+        const size_t want = bytes + bytes / 4;
+        if (cudaMalloc(&c.ws, want) != cudaSuccess) {
+            cudaGetLastError();
+            return DTW_ENOMEM;
+        }
+        c.ws_bytes = want;
+    }
+    *out = c.ws;
+    return DTW_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Byte layout of the workspace for a batch (every size linear in sum(M+N)).
+struct Layout {
+    size_t feat, pairs, pres, boxA, boxB, base, sweeps, sres, bufpool, tagpool, outpool, progpool, jlo, jhi, off,
+        path, ctl, total;
+    long long cap_box, cap_base, cap_sweeps, cap_buf, cap_out, cap_prog;
+};
+
+Layout make_layout(int B, long long sumM, long long sumN, long long feat_bytes, long long path_pairs) {
+    Layout L{};
+    const long long S = sumM + sumN;
+    L.cap_box = S / 2 + B + 16;
+    L.cap_base = S + B + 16;
+    L.cap_sweeps = 2 * L.cap_box;
+    L.cap_buf = 2 * (S + 2 * L.cap_box) + 2 * L.cap_box * 8;
+    L.cap_out = 2 * (S + 2 * L.cap_box);
+    L.cap_prog = S + 3 * L.cap_box;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = align_up(o + bytes);
+        return r;
+    };
+    L.feat = take((size_t)feat_bytes);
+    L.pairs = take(sizeof(PairDesc) * B);
+    L.pres = take(sizeof(PairRes) * B);
+    L.boxA = take(sizeof(Box) * L.cap_box);
+    L.boxB = take(sizeof(Box) * L.cap_box);
+    L.base = take(sizeof(Box) * L.cap_base);
+    L.sweeps = take(sizeof(Sweep) * L.cap_sweeps);
+    L.sres = take(sizeof(SweepRes) * L.cap_sweeps);
+    L.bufpool = take(8 * (size_t)L.cap_buf);
+    L.tagpool = take(4 * (size_t)L.cap_buf);
+    L.outpool = take(8 * (size_t)L.cap_out);
+    L.progpool = take(4 * (size_t)L.cap_prog);
+    L.jlo = take(4 * (size_t)sumM);
+    L.jhi = take(4 * (size_t)sumM);
+    L.off = take(4 * (size_t)sumM);
+    L.path = take(8 * (size_t)path_pairs);
+    L.ctl = take(sizeof(LevelCtl));
+    L.total = o;
+    return L;
+}
+
+int map_device_error(int err) {
+    switch (err) {
+        case ERR_NONE: return DTW_OK;
+        case ERR_TIMEOUT: return DTW_ETIMEOUT;
+        case ERR_OVERFLOW: return DTW_EOVERFLOW;
+        case ERR_CAPACITY: return DTW_ENOMEM;
+        default: return DTW_EINTERNAL;
+    }
+}
+
+int check_kind(int32_t cost_kind, int32_t d, int* kind, bool* plain) {
+    const int k = cost_kind & 0xff;
+    const int flags = cost_kind & ~0xff;
+    if (k != DTW_EUCLID_F32 && k != DTW_ABS_I32) return DTW_EINVAL;
+    if (flags & ~(int)DTW_PLAIN_F64) return DTW_EINVAL;
+    if (d < 1 || (k == DTW_ABS_I32 && d != 1)) return DTW_EINVAL;
+    *kind = k == DTW_ABS_I32 ? KIND_ABS : KIND_EUC;
+    *plain = (flags & DTW_PLAIN_F64) != 0;
+    return DTW_OK;
+}
+
+struct Timer {
+    bool on;
+    cudaStream_t st;
+    std::vector<cudaEvent_t> ev;
+    cudaEvent_t mark() {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, st);
+        ev.push_back(e);
+        return e;
+    }
+    ~Timer() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+// The tiled path for a batch.  want_path == false: dtw_cost (one full sweep).
+int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void* const* Y, const int64_t* N, int d,
+              int kind, bool want_path, int32_t* const* path_out, int64_t* K_out, double* cost_out) {
+    const size_t esize = 4;  // float or int32
+    long long sumM = 0, sumN = 0, feat_bytes = 0, path_pairs = 0, maxM = 0;
+    std::vector<char> xdev(B), ydev(B), pdev(B);
+    for (int b = 0; b < B; ++b) {
+        if (!X[b] || !Y[b] || M[b] < 1 || N[b] < 1 || M[b] > (1LL << 30) || N[b] > (1LL << 30)) return DTW_EINVAL;
+        if (want_path && !path_out[b]) return DTW_EINVAL;
+        sumM += M[b];
+        sumN += N[b];
+        maxM = std::max<long long>(maxM, M[b]);
+        xdev[b] = is_device_ptr(X[b]);
+        ydev[b] = is_device_ptr(Y[b]);
+        if (!xdev[b]) feat_bytes += align_up((size_t)M[b] * d * esize);
+        if (!ydev[b]) feat_bytes += align_up((size_t)N[b] * d * esize);
+        if (want_path) {
+            pdev[b] = is_device_ptr(path_out[b]);
+            if (!pdev[b]) path_pairs += M[b] + N[b] - 1;
+        }
+    }
+    const Layout L = make_layout(B, sumM, sumN, feat_bytes, path_pairs);
+    void* wsv = nullptr;
+    int rc = workspace(c, L.total, &wsv);
+    if (rc) return rc;
+    char* ws = static_cast<char*>(wsv);
+    cudaStream_t st = c.stream;
+    Timer T{c.timing != 0, st, {}};
+    cudaEvent_t t_begin = c.timing ? T.mark() : nullptr;
+
+    // stage host features and describe the pairs
+    std::vector<PairDesc> pd(B);
+    size_t fo = L.feat;
+    long long row_off = 0, path_off = 0;
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < B && e == cudaSuccess; ++b) {
+        PairDesc& p = pd[b];
+        p.M = (int32_t)M[b];
+        p.N = (int32_t)N[b];
+        p.row_off = (int32_t)row_off;
+        p.flags = 0;
+        row_off += M[b];
+        if (xdev[b]) {
+            p.X = X[b];
+        } else {
+            p.X = ws + fo;
+            e = cudaMemcpyAsync(ws + fo, X[b], (size_t)M[b] * d * esize, cudaMemcpyHostToDevice, st);
+            fo += align_up((size_t)M[b] * d * esize);
+        }
+        if (e == cudaSuccess && !ydev[b]) {
+            p.Y = ws + fo;
+            e = cudaMemcpyAsync(ws + fo, Y[b], (size_t)N[b] * d * esize, cudaMemcpyHostToDevice, st);
+            fo += align_up((size_t)N[b] * d * esize);
+        } else if (ydev[b]) {
+            p.Y = Y[b];
+        }
+        if (want_path) {
+            if (pdev[b]) {
+                p.path = path_out[b];
+            } else {
+                p.path = reinterpret_cast<int32_t*>(ws + L.path) + 2 * path_off;
+                path_off += M[b] + N[b] - 1;
+            }
+        } else {
+            p.path = nullptr;
+        }
+    }
+    if (e != cudaSuccess) return DTW_ECUDA;
+    for (int b = 0; b < B; ++b) {
+        if (kind == KIND_EUC && d % 4 == 0 && d == 12 &&
+            ((reinterpret_cast<uintptr_t>(pd[b].X) | reinterpret_cast<uintptr_t>(pd[b].Y)) & 15))
+            return DTW_EINVAL;  // the d=12 kernels load frames as float4
+    }
+
+    PairDesc* d_pairs = reinterpret_cast<PairDesc*>(ws + L.pairs);
+    PairRes* d_pres = reinterpret_cast<PairRes*>(ws + L.pres);
+    Box* boxA = reinterpret_cast<Box*>(ws + L.boxA);
+    Box* boxB = reinterpret_cast<Box*>(ws + L.boxB);
+    Box* d_base = reinterpret_cast<Box*>(ws + L.base);
+    Sweep* d_sweeps = reinterpret_cast<Sweep*>(ws + L.sweeps);
+    SweepRes* d_sres = reinterpret_cast<SweepRes*>(ws + L.sres);
+    LevelCtl* d_ctl = reinterpret_cast<LevelCtl*>(ws + L.ctl);
+    int32_t* d_jlo = reinterpret_cast<int32_t*>(ws + L.jlo);
+    int32_t* d_jhi = reinterpret_cast<int32_t*>(ws + L.jhi);
+    int32_t* d_off = reinterpret_cast<int32_t*>(ws + L.off);
+
+    // root boxes: small ones go straight to the base case
+    const long long base_area = want_path ? c.base_area : 0;
+    std::vector<Box> roots, base_roots;
+    for (int b = 0; b < B; ++b) {
+        Box r{};
+        r.pair = b;
+        r.i0 = 0;
+        r.j0 = 0;
+        r.H = (int32_t)M[b];
+        r.W = (int32_t)N[b];
+        r.flags = BOX_ROOT;
+        r.known_i = -1;
+        r.known_f = NAN;
+        if (want_path && M[b] * N[b] <= base_area) base_roots.push_back(r);
+        else roots.push_back(r);
+    }
+    LevelCtl ctl0{};
+    ctl0.n_base = (int32_t)base_roots.size();
+    e = cudaMemcpyAsync(d_pairs, pd.data(), sizeof(PairDesc) * B, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !roots.empty())
+        e = cudaMemcpyAsync(boxA, roots.data(), sizeof(Box) * roots.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !base_roots.empty())
+        e = cudaMemcpyAsync(d_base, base_roots.data(), sizeof(Box) * base_roots.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ctl, &ctl0, sizeof(LevelCtl), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_pres, 0, sizeof(PairRes) * B, st);
+    if (e == cudaSuccess && want_path) {
+        e = launch_fill_i32(d_jlo, sumM, INT32_MAX, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_jhi, 0xff, 4 * (size_t)sumM, st);
+    }
+    if (e == cudaSuccess && kind == KIND_ABS) e = launch_int_range_check(d_pairs, B, d_ctl, st);
+    if (e != cudaSuccess) return DTW_ECUDA;
+
+    // ---- the level loop (Algorithm 2, breadth first: all boxes of a level together)
+    const int mode = !want_path ? MODE_COST : (kind == KIND_ABS ? MODE_TAG : MODE_FB);
+    const int U = sweep_block_cols(kind, d);
+    const int BR = sweep_band_rows(kind, d);
+    Box* cur = boxA;
+    Box* nxt = boxB;
+    int n_cur = (int)roots.size();
+    int levels = 0, sweeps = 0;
+    double sweep_ms = 0;
+    LevelCtl hc = ctl0;
+    // every level shrinks each box's longer side to at most about half, so the
+    // depth is bounded by twice the bits of the longest sequence
+    int launches = (want_path ? 1 : 0) + (kind == KIND_ABS ? 1 : 0);
+    const int max_levels = 2 * (64 - __builtin_clzll((unsigned long long)std::max(maxM, sumN) + 1)) + 8;
+    while (n_cur > 0) {
+        if (levels >= max_levels) return DTW_EINTERNAL;
+        PlanArgs pa{cur, n_cur, d_pairs, mode, U, BR, d_sweeps, d_ctl, reinterpret_cast<int32_t*>(ws + L.progpool),
+                    L.cap_sweeps, L.cap_buf, L.cap_out, L.cap_prog};
+        e = launch_plan(pa, st);
+        SweepArgs sa{d_sweeps,
+                     d_ctl,
+                     ws + L.bufpool,
+                     reinterpret_cast<int32_t*>(ws + L.tagpool),
+                     ws + L.outpool,
+                     reinterpret_cast<int32_t*>(ws + L.progpool),
+                     d_sres,
+                     d,
+                     c.spin_limit,
+                     c.skip_publish};
+        cudaEvent_t s0 = nullptr, s1 = nullptr;
+        if (c.timing) s0 = T.mark();
+        if (e == cudaSuccess) e = launch_sweep(kind, d, mode == MODE_TAG, sa, c.num_sms, st);
+        launches += mode == MODE_COST ? 2 : 3;
+        if (c.timing) s1 = T.mark();
+        ++sweeps;
+        if (e == cudaSuccess && mode != MODE_COST) {
+            SplitArgs sp{cur,  n_cur, d_pairs, d_pres, mode,   kind,    d,  d_sweeps,   d_sres,
+                         ws + L.outpool, nxt, d_base, d_ctl, base_area, (int)L.cap_box, (int)L.cap_base};
+            e = launch_split(sp, st);
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return DTW_ECUDA;
+        if (c.timing) sweep_ms += elapsed(s0, s1);
+        ++levels;
+        if (hc.err != ERR_NONE) break;
+        if (mode == MODE_COST) break;
+        std::swap(cur, nxt);
+        n_cur = hc.n_next;
+    }
+    if (hc.err == ERR_NONE && mode == MODE_COST) {
+        std::vector<SweepRes> sr(B);
+        e = cudaMemcpyAsync(sr.data(), d_sres, sizeof(SweepRes) * B, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return DTW_ECUDA;
+        for (int b = 0; b < B; ++b) cost_out[b] = kind == KIND_ABS ? (double)sr[b].end_i : sr[b].end_f;
+    }
+    if (hc.err == ERR_NONE && want_path) {
+        BaseArgs ba{d_base, hc.n_base, d_pairs, d_pres, d_jlo, d_jhi, d_ctl, kind, d};
+        e = launch_base(ba, st);
+        AssembleArgs aa{d_pairs, B, (int)maxM, d_pres, d_jlo, d_jhi, d_off, d_ctl};
+        if (e == cudaSuccess) e = launch_assemble(aa, st);
+        launches += (hc.n_base > 0 ? 1 : 0) + 2;
+        std::vector<PairRes> pr(B);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(pr.data(), d_pres, sizeof(PairRes) * B, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return DTW_ECUDA;
+        if (hc.err == ERR_NONE) {
+            for (int b = 0; b < B && e == cudaSuccess; ++b) {
+                K_out[b] = pr[b].K;
+                cost_out[b] = kind == KIND_ABS ? (double)pr[b].cost_i : pr[b].cost_f;
+                if (!pdev[b])
+                    e = cudaMemcpyAsync(path_out[b], pd[b].path, sizeof(int32_t) * 2 * (size_t)pr[b].K,
+                                        cudaMemcpyDeviceToHost, st);
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return DTW_ECUDA;
+        }
+    }
+    double total_ms = 0;
+    if (c.timing) {
+        cudaEvent_t t_end = T.mark();
+        cudaEventSynchronize(t_end);
+        total_ms = elapsed(t_begin, t_end);
+    }
+    dtw_stats& s = c.stats;
+    s = dtw_stats{};
+    for (int b = 0; b < B; ++b) s.problem_cells += M[b] * N[b];
+    s.sweep_cells = (int64_t)hc.sweep_cells;
+    s.tag_cells = (int64_t)hc.tag_cells;
+    s.base_cells = (int64_t)hc.base_cells;
+    s.levels = levels;
+    s.sweep_launches = sweeps;
+    s.base_boxes = hc.n_base;
+    s.kernel_launches = launches;
+    s.sweep_ms = sweep_ms;
+    s.device_ms = total_ms;
+    return map_device_error(hc.err);
+}
+
+int run_plain(Ctx& c, const void* X, int64_t M, const void* Y, int64_t N, int d, int kind, int32_t* path_out,
+              int64_t* K_out, double* cost_out) {
+    const size_t esize = 4;
+    const bool xd = is_device_ptr(X), yd = is_device_ptr(Y), pdv = is_device_ptr(path_out);
+    const size_t fx = xd ? 0 : align_up((size_t)M * d * esize), fy = yd ? 0 : align_up((size_t)N * d * esize);
+    const size_t fp = pdv ? 0 : align_up(sizeof(int32_t) * 2 * (size_t)(M + N - 1));
+    const size_t wb = plain_workspace_bytes(M, N);
+    void* wsv = nullptr;
+    int rc = workspace(c, fx + fy + fp + wb, &wsv);
+    if (rc) return rc;
+    char* ws = static_cast<char*>(wsv);
+    cudaStream_t st = c.stream;
+    cudaError_t e = cudaSuccess;
+    PlainProblem pb{X, Y, M, N, d, kind};
+    if (!xd) {
+        e = cudaMemcpyAsync(ws, X, (size_t)M * d * esize, cudaMemcpyHostToDevice, st);
+        pb.X = ws;
+    }
+    if (e == cudaSuccess && !yd) {
+        e = cudaMemcpyAsync(ws + fx, Y, (size_t)N * d * esize, cudaMemcpyHostToDevice, st);
+        pb.Y = ws + fx;
+    }
+    if (e != cudaSuccess) return DTW_ECUDA;
+    int32_t* dpath = pdv ? path_out : reinterpret_cast<int32_t*>(ws + fx + fy);
+    Timer T{c.timing != 0, st, {}};
+    cudaEvent_t t0 = c.timing ? T.mark() : nullptr;
+    long long cells = 0;
+    rc = plain_align(pb, dpath, cost_out, K_out, ws + fx + fy + fp, wb, st, &cells);
+    if (rc) return rc;
+    if (!pdv) {
+        e = cudaMemcpyAsync(path_out, dpath, sizeof(int32_t) * 2 * (size_t)*K_out, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return DTW_ECUDA;
+    }
+    dtw_stats& s = c.stats;
+    s = dtw_stats{};
+    s.problem_cells = M * N;
+    s.sweep_cells = cells;
+    if (c.timing) {
+        cudaEvent_t t1 = T.mark();
+        cudaEventSynchronize(t1);
+        s.device_ms = elapsed(t0, t1);
+    }
+    return DTW_OK;
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+
+extern "C" {
+
+int64_t dtw_align(const void* X, int64_t M, const void* Y, int64_t N, int32_t d, int32_t cost_kind,
+                  int32_t* path_out, double* cost_out) {
+    int kind;
+    bool plain;
+    int rc = check_kind(cost_kind, d, &kind, &plain);
+    if (rc) return rc;
+    if (!X || !Y || !path_out || !cost_out || M < 1 || N < 1) return DTW_EINVAL;
+    Ctx& c = ctx();
+    std::lock_guard<std::mutex> g(c.mu);
+    rc = ensure_device(c);
+    if (rc) return rc;
+    int64_t K = 0;
+    if (plain) {
+        rc = run_plain(c, X, M, Y, N, d, kind, path_out, &K, cost_out);
+    } else {
+        const void* xs[1] = {X};
+        const void* ys[1] = {Y};
+        int32_t* ps[1] = {path_out};
+        rc = run_batch(c, 1, xs, &M, ys, &N, d, kind, true, ps, &K, cost_out);
+    }
+    return rc ? rc : K;
+}
+
+int dtw_cost(const void* X, int64_t M, const void* Y, int64_t N, int32_t d, int32_t cost_kind, double* cost_out) {
+    int kind;
+    bool plain;
+    int rc = check_kind(cost_kind, d, &kind, &plain);
+    if (rc) return rc;
+    if (plain || !X || !Y || !cost_out || M < 1 || N < 1) return DTW_EINVAL;
+    Ctx& c = ctx();
+    std::lock_guard<std::mutex> g(c.mu);
+    rc = ensure_device(c);
+    if (rc) return rc;
+    const void* xs[1] = {X};
+    const void* ys[1] = {Y};
+    return run_batch(c, 1, xs, &M, ys, &N, d, kind, false, nullptr, nullptr, cost_out);
+}
+
+int dtw_align_batch(int32_t B, const void* const* X, const int64_t* M, const void* const* Y, const int64_t* N,
+                    int32_t d, int32_t cost_kind, int32_t* const* path_out, int64_t* K_out, double* cost_out) {
+    int kind;
+    bool plain;
+    int rc = check_kind(cost_kind, d, &kind, &plain);
+    if (rc) return rc;
+    if (B < 1 || !X || !M || !Y || !N || !path_out || !K_out || !cost_out || plain) return DTW_EINVAL;
+    Ctx& c = ctx();
+    std::lock_guard<std::mutex> g(c.mu);
+    rc = ensure_device(c);
+    if (rc) return rc;
+    return run_batch(c, B, X, M, Y, N, d, kind, true, path_out, K_out, cost_out);
+}
+
+int64_t dtw_submit(const dtw_request* r) {
+    if (!r) return DTW_EINVAL;
+    double cost = 0;
+    const int64_t K = dtw_align(r->X, r->M, r->Y, r->N, r->d, r->cost_kind, r->path_out, &cost);
+    Ctx& c = ctx();
+    std::lock_guard<std::mutex> g(c.mu);
+    const long long t = c.next_ticket++;
+    c.done[t] = Ctx::Done{K < 0 ? (int)K : DTW_OK, K < 0 ? 0 : K, cost};
+    return t;
+}
+
+int dtw_poll(int64_t ticket, int64_t* K_out, double* cost_out) {
+    Ctx& c = ctx();
+    std::lock_guard<std::mutex> g(c.mu);
+    auto it = c.done.find(ticket);
+    if (it == c.done.end()) return DTW_EINVAL;
+    const Ctx::Done dn = it->second;
+    c.done.erase(it);
+    if (K_out) *K_out = dn.K;
+    if (cost_out) *cost_out = dn.cost;
+    return dn.status;
+}
+
+int dtw_set_stream(void* cuda_stream) {
+    Ctx& c = ctx();
+    std::lock_guard<std::mutex> g(c.mu);
+    c.stream = static_cast<cudaStream_t>(cuda_stream);
+    return DTW_OK;
+}
+
+int dtw_set_budget(uint64_t bytes) {
+    Ctx& c = ctx();
+    std::lock_guard<std::mutex> g(c.mu);
+    c.budget = bytes;
+    return DTW_OK;
+}
+
+int dtw_set_arena(void* device_ptr, uint64_t bytes) {
+    Ctx& c = ctx();
+    std::lock_guard<std::mutex> g(c.mu);
+    if (device_ptr && (reinterpret_cast<uintptr_t>(device_ptr) & 255)) return DTW_EINVAL;
+    c.arena = device_ptr;
+    c.arena_bytes = device_ptr ? bytes : 0;
+    return DTW_OK;
+}
+
+size_t dtw_footprint(int64_t M, int64_t N, int32_t d, int32_t cost_kind) {
+    if (M < 1 || N < 1 || d < 1) return 0;
+    if (cost_kind & DTW_PLAIN_F64) {
+        return align_up((size_t)(M + N) * d * 4) + 3 * 256 + align_up(8 * (size_t)(M + N)) +
+               plain_workspace_bytes(M, N);
+    }
+    const Layout L = make_layout(1, M, N, (long long)align_up((size_t)M * d * 4) + (long long)align_up((size_t)N * d * 4),
+                                 M + N - 1);
+    return L.total;
+}
+
+const char* dtw_strerror(int status) {
+    switch (status) {
+        case DTW_OK: return "ok";
+        case DTW_PENDING: return "pending";
+        case DTW_EINVAL: return "invalid argument";
+        case DTW_ENOMEM: return "out of device memory or over budget";
+        case DTW_ECUDA: return "CUDA runtime error";
+        case DTW_ETIMEOUT: return "device-side wait timed out";
+        case DTW_EOVERFLOW: return "integer accumulator range exceeded";
+        case DTW_EBUSY: return "queue full";
+        case DTW_EINTERNAL: return "internal consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+int dtw_get_stats(dtw_stats* out) {
+    if (!out) return DTW_EINVAL;
+    Ctx& c = ctx();
+    std::lock_guard<std::mutex> g(c.mu);
+    *out = c.stats;
+    return DTW_OK;
+}
+
+int dtw_set_option(int32_t key, int64_t value) {
+    Ctx& c = ctx();
+    std::lock_guard<std::mutex> g(c.mu);
+    switch (key) {
+        case DTW_OPT_TIMING: c.timing = value != 0; return DTW_OK;
+        case DTW_OPT_BASE_AREA:
+            if (value < 4 || value > kBaseAreaMax) return DTW_EINVAL;
+            c.base_area = value;
+            return DTW_OK;
+        case DTW_OPT_SPIN_LIMIT:
+            if (value < 1 || value > (1LL << 30)) return DTW_EINVAL;
+            c.spin_limit = (int)value;
+            return DTW_OK;
+        case DTW_OPT_SKIP_PUBLISH: c.skip_publish = value; return DTW_OK;
+        default: return DTW_EINVAL;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,221 @@
+// Device-side types and helpers shared by the kernels of the library.
+//
+// Frames (Section 2.1): pair b aligns X (M frames) with Y (N frames).  A "box" is
+// the sub-problem [i0, i0+H) x [j0, j0+W) of one pair whose first and last cells
+// are known to lie on the optimal path (Algorithm 2's recursion).  A box is swept
+// in a "frame" (p, q): p runs along the split axis (X rows when H >= W, else Y
+// rows), q along the other axis, and a backward sweep reverses both (the
+// reversed series X_R, Y_R of Algorithm 2, done by index arithmetic).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dtwb {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Cost kinds (low byte of the ABI's cost_kind).
+constexpr int KIND_EUC = 0;  // Euclidean distance of FP32 frames, FP64 accumulation
+constexpr int KIND_ABS = 1;  // |x - y| of int32 samples, exact int32 accumulation
+
+// "Infinity" of the int32 accumulator: above any reachable cost (the host
+// guarantees max C * (M+N-1) < 2^29) and far from overflow when C is added.
+constexpr int32_t kIntInf = 0x3FFFFFFF;
+
+// Device error codes (stored in LevelCtl::err; first error wins).
+constexpr int ERR_NONE = 0;
+constexpr int ERR_TIMEOUT = 1;     // a bounded wait gave up
+constexpr int ERR_CONSIST = 2;     // a box's swept cost differs from its known cost
+constexpr int ERR_PATH = 3;        // the assembled path is not a warping path
+constexpr int ERR_OVERFLOW = 4;    // integer accumulator range exceeded
+constexpr int ERR_CAPACITY = 5;    // a level needs more workspace than reserved
+
+struct PairDesc {
+    const void* X;      // M*d frames
+    const void* Y;      // N*d frames
+    int32_t M, N;
+    int32_t row_off;    // offset of the pair's rows in the per-row path arrays
+    int32_t flags;
+    int32_t* path;      // device path buffer, 2*(M+N-1) int32
+};
+
+struct PairRes {
+    long long cost_i;   // exact D* (KIND_ABS)
+    double cost_f;      // D* (KIND_EUC)
+    int32_t K;          // path length
+    int32_t pad;
+};
+
+constexpr int BOX_ROOT = 1;
+
+struct Box {
+    int32_t pair, i0, j0, H, W, flags;
+    long long known_i;  // optimal cost of the box if known (KIND_ABS), else -1
+    double known_f;     // optimal cost of the box (KIND_EUC), NaN if unknown
+};
+
+// One wavefront sweep over frame rows [0, rows) x frame columns [0, Q).
+struct Sweep {
+    const void* rowseq;  // features indexed by frame row p: rowseq[rbase + rstep*p]
+    const void* colseq;  // features indexed by frame column q: colseq[cbase + cstep*q]
+    int32_t rbase, rstep, cbase, cstep;
+    int32_t box;         // index in the level's box array
+    int32_t dir;         // 0 forward from the box's first cell, 1 backward from its last
+    int32_t axis;        // 0: p runs along X; 1: p runs along Y
+    int32_t rows;        // frame rows swept
+    int32_t Q;           // frame columns
+    int32_t nblk;        // column blocks of the sweep's kernel variant
+    int32_t out_row;     // frame row copied to the out pool (-1: none)
+    int32_t tag_row;     // frame row where split tags start (-1: untagged sweep)
+    int32_t nbands;
+    int32_t pad;
+    long long band_begin;  // first ticket of the sweep
+    long long buf_off;     // boundary-row pool offset (nblk*U entries)
+    long long out_off;     // out pool offset (Q entries, forward column order)
+    long long prog_off;    // progress-counter offset (nbands entries)
+};
+
+struct SweepRes {
+    long long end_i;  // accumulated cost at the sweep's last cell (KIND_ABS)
+    double end_f;     // (KIND_EUC)
+    int32_t end_tag;  // split tag carried to the last cell (tag sweeps)
+    int32_t pad;
+};
+
+// Control block of a call, in device memory.
+struct LevelCtl {
+    unsigned long long ticket;   // next band ticket of the current sweep launch
+    long long n_tickets;         // bands in the current level
+    int32_t n_sweeps;
+    int32_t n_next;              // boxes appended to the next level
+    int32_t n_base;              // boxes appended to the base list (all levels)
+    int32_t err;                 // first device error (ERR_*)
+    int32_t err_info;
+    int32_t pad;
+    unsigned long long sweep_cells;
+    unsigned long long tag_cells;
+    unsigned long long base_cells;
+    long long need_buf;          // pool entries the current level needs
+    long long need_prog;
+};
+
+// ---------------------------------------------------------------- memory order
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void set_error(LevelCtl* ctl, int code, int info) {
+    if (atomicCAS(&ctl->err, ERR_NONE, code) == ERR_NONE) ctl->err_info = info;
+}
+
+// ---------------------------------------------------------------- accumulators
+
+template <int KIND> struct AccOf;
+template <> struct AccOf<KIND_ABS> {
+    using T = int32_t;
+    static __device__ __forceinline__ T inf() { return kIntInf; }
+    static __device__ __forceinline__ T zero() { return 0; }
+};
+template <> struct AccOf<KIND_EUC> {
+    using T = double;
+    static __device__ __forceinline__ T inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+    static __device__ __forceinline__ T zero() { return 0.0; }
+};
+
+__device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return __vimin3_s32(a, b, c); }
+__device__ __forceinline__ double min3(double a, double b, double c) { return fmin(fmin(a, b), c); }
+
+// ---------------------------------------------------------------- frame features
+
+// A frame held in registers.  DIM > 0: compile-time dimension; the int kind has DIM 1.
+template <int KIND, int DIM> struct Frame;
+
+template <> struct Frame<KIND_ABS, 1> {
+    int32_t v;
+    __device__ __forceinline__ void load(const void* base, long long idx, int /*d*/) {
+        v = __ldg(static_cast<const int32_t*>(base) + idx);
+    }
+};
+
+template <int DIM> struct Frame<KIND_EUC, DIM> {
+    float v[DIM];
+    __device__ __forceinline__ void load(const void* base, long long idx, int /*d*/) {
+        const float* p = static_cast<const float*>(base) + idx * DIM;
+        if constexpr (DIM % 4 == 0) {
+            const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+            for (int e = 0; e < DIM / 4; ++e) {
+                float4 t = __ldg(p4 + e);
+                v[4 * e] = t.x;
+                v[4 * e + 1] = t.y;
+                v[4 * e + 2] = t.z;
+                v[4 * e + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < DIM; ++e) v[e] = __ldg(p + e);
+        }
+    }
+};
+
+// Runtime dimension: the frame stays in global memory (read through L1).
+template <> struct Frame<KIND_EUC, 0> {
+    const float* p;
+    int d;
+    __device__ __forceinline__ void load(const void* base, long long idx, int dd) {
+        d = dd;
+        p = static_cast<const float*>(base) + idx * dd;
+    }
+};
+
+// Frame cost C (Section 2.1): |x-y|, or the Euclidean distance (Section 4.1)
+// evaluated in FP32 (sum of squares with FMA, correctly rounded sqrt) and widened.
+__device__ __forceinline__ int32_t frame_cost(const Frame<KIND_ABS, 1>& a, const Frame<KIND_ABS, 1>& b) {
+    return abs(a.v - b.v);
+}
+
+template <int DIM>
+__device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, DIM>& a, const Frame<KIND_EUC, DIM>& b) {
+    float s = 0.f;
+#pragma unroll
+    for (int e = 0; e < DIM; ++e) {
+        float t = a.v[e] - b.v[e];
+        s = fmaf(t, t, s);
+    }
+    return (double)__fsqrt_rn(s);
+}
+
+__device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, 0>& a, const Frame<KIND_EUC, 0>& b) {
+    float s = 0.f;
+    for (int e = 0; e < a.d; ++e) {
+        float t = __ldg(a.p + e) - __ldg(b.p + e);
+        s = fmaf(t, t, s);
+    }
+    return (double)__fsqrt_rn(s);
+}
+
+// Cost of global cell (i, j) of a pair, for the split and checks.
+template <int KIND, int DIM>
+__device__ __forceinline__ typename AccOf<KIND>::T cell_cost(const PairDesc& pd, int i, int j, int d) {
+    Frame<KIND, DIM> a, b;
+    a.load(pd.X, i, d);
+    b.load(pd.Y, j, d);
+    return frame_cost(a, b);
+}
+
+}  // namespace dtwb

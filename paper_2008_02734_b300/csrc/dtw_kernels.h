@@ -1,0 +1,107 @@
+// Launchers of the library's kernels (host side).  Internal header.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dtw_b300.h"
+#include "dtw_common.cuh"
+
+namespace dtwb {
+
+struct SweepArgs {
+    const Sweep* sweeps;
+    LevelCtl* ctl;
+    void* bufpool;      // boundary rows (Acc)
+    int32_t* tagpool;   // boundary-row split tags, indexed like bufpool
+    void* outpool;      // split rows (Acc), forward column order
+    int32_t* progpool;  // per-band progress counters, indexed by ticket
+    SweepRes* res;      // per-sweep last-cell results
+    int d;
+    int spin_limit;
+    long long skip_ticket;  // test hook: this band never publishes (-1: none)
+};
+
+// Sweep variants
+int sweep_block_cols(int kind, int d);  // U
+int sweep_band_rows(int kind, int d);   // 32*R
+cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, cudaStream_t st);
+
+// Level planning modes
+constexpr int MODE_TAG = 0;   // one tagged forward sweep per box (canonical pivot)
+constexpr int MODE_FB = 1;    // forward half + backward half per box (F + B - C argmin)
+constexpr int MODE_COST = 2;  // one untagged forward sweep of the whole box, last cell only
+
+struct PlanArgs {
+    const Box* boxes;
+    int n_boxes;
+    const PairDesc* pairs;
+    int mode;
+    int U, BR;
+    Sweep* sweeps;
+    LevelCtl* ctl;
+    int32_t* progpool;
+    long long cap_sweeps, cap_buf, cap_out, cap_prog;
+};
+cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st);
+
+struct SplitArgs {
+    const Box* boxes;
+    int n_boxes;
+    const PairDesc* pairs;
+    PairRes* pres;
+    int mode;
+    int kind, d;
+    const Sweep* sweeps;
+    const SweepRes* res;
+    const void* outpool;
+    Box* next;
+    Box* base;
+    LevelCtl* ctl;
+    long long base_area;
+    int cap_next, cap_base;
+};
+cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
+
+struct BaseArgs {
+    const Box* base;
+    int n_base;
+    const PairDesc* pairs;
+    PairRes* pres;
+    int32_t* jlo;
+    int32_t* jhi;
+    LevelCtl* ctl;
+    int kind, d;
+};
+// Largest box (cells) the base-case kernel accepts.
+constexpr long long kBaseAreaMax = 32768;
+cudaError_t launch_base(const BaseArgs& a, cudaStream_t st);
+
+struct AssembleArgs {
+    const PairDesc* pairs;
+    int n_pairs;
+    int max_M;
+    PairRes* pres;
+    int32_t* jlo;
+    int32_t* jhi;
+    int32_t* off;
+    LevelCtl* ctl;
+};
+cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st);
+cudaError_t launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st);
+cudaError_t launch_int_range_check(const PairDesc* pairs, int n_pairs, LevelCtl* ctl, cudaStream_t st);
+
+// The paper's plain form (plain.cu)
+struct PlainProblem {
+    const void* X;
+    const void* Y;
+    int64_t M, N;
+    int d, kind;
+};
+// Runs the plain FP64 form on device-resident X, Y; writes the path (device,
+// 2*(M+N-1) int32) and returns K or a negative status through *K.
+int plain_align(const PlainProblem& pb, int32_t* d_path, double* cost, int64_t* K, void* work,
+                size_t work_bytes, cudaStream_t st, long long* cells);
+size_t plain_workspace_bytes(int64_t M, int64_t N);
+
+}  // namespace dtwb

@@ -1,0 +1,220 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer |x-y| inputs: cost and path must equal oracle 1's bit for bit (the path
+is the canonical DIAG > UP > LEFT backtrace).  Float inputs (FP32 frame cost,
+FP64 accumulation): cost within 1e-6 relative of the FP64 oracle optimum, and
+the returned path, re-scored by the oracle in FP64, within the same tolerance.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2008_02734_b300 as dtw
+from paper_2008_02734_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-6  # FP32 frame costs (relative error ~1e-7 each), FP64 sums
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def check_path_struct(path, M, N):
+    path = np.asarray(path)
+    assert tuple(path[0]) == (0, 0) and tuple(path[-1]) == (M - 1, N - 1)
+    st = np.diff(path, axis=0)
+    assert ((st == [0, 1]).all(1) | (st == [1, 0]).all(1) | (st == [1, 1]).all(1)).all()
+
+
+def check_int(X, Y, **kw):
+    path, cost = dtw.align(_cuda(X), _cuda(Y), **kw)
+    p_ref, c_ref = oracle.dtw(X, Y)
+    assert cost == c_ref
+    assert np.array_equal(path.cpu().numpy(), p_ref)
+
+
+def check_float(X, Y):
+    path, cost = dtw.align(_cuda(X), _cuda(Y))
+    p_ref, c_ref = oracle.dtw(X, Y)
+    p = path.cpu().numpy()
+    check_path_struct(p, len(X), len(Y))
+    assert cost == pytest.approx(c_ref, rel=REL_TOL, abs=1e-9)
+    assert oracle.path_cost(X, Y, p) == pytest.approx(c_ref, rel=REL_TOL, abs=1e-9)
+
+
+@pytest.fixture(autouse=True)
+def _defaults(cuda_device):
+    yield
+    dtw.set_option(dtw.OPT_BASE_AREA, 16384)
+    dtw.set_option(dtw.OPT_SPIN_LIMIT, 1 << 24)
+    dtw.set_option(dtw.OPT_SKIP_PUBLISH, -1)
+
+
+SHAPES = [(1, 1), (1, 9), (9, 1), (2, 2), (3, 7), (7, 13), (33, 65), (64, 64), (65, 63), (100, 37),
+          (129, 257), (257, 300), (500, 433), (1000, 1200)]
+
+
+@pytest.mark.parametrize("M,N", SHAPES)
+@pytest.mark.parametrize("base_area", [4, 64, 16384])
+def test_int_small_exact(M, N, base_area):
+    dtw.set_option(dtw.OPT_BASE_AREA, base_area)
+    X, Y = synth.int_pair(M * 7 + N, M, N)
+    check_int(X, Y)
+
+
+@pytest.mark.parametrize("alphabet", [2, 3])
+@pytest.mark.parametrize("M,N", [(40, 50), (301, 257), (2000, 1800)])
+def test_int_ties_canonical(alphabet, M, N):
+    """Small alphabets make most split rows tie; the path must still be the
+    canonical backtrace."""
+    rng = np.random.default_rng(M + N + alphabet)
+    X = rng.integers(0, alphabet, M).astype(np.int32)
+    Y = rng.integers(0, alphabet, N).astype(np.int32)
+    dtw.set_option(dtw.OPT_BASE_AREA, 64)
+    check_int(X, Y)
+    dtw.set_option(dtw.OPT_BASE_AREA, 16384)
+    check_int(X, Y)
+
+
+@pytest.mark.parametrize("M,N", [(1, 40000), (40000, 1), (2, 30000), (30000, 3), (5, 9000)])
+def test_int_degenerate_thin(M, N):
+    X, Y = synth.int_pair(M + 3 * N, M, N)
+    check_int(X, Y)
+
+
+@pytest.mark.parametrize("M,N,d", [(1, 1, 12), (5, 3, 12), (64, 80, 12), (300, 257, 12), (1000, 1300, 12),
+                                   (70, 90, 3), (257, 129, 5), (33, 2000, 12)])
+@pytest.mark.parametrize("base_area", [4, 16384])
+def test_float_small(M, N, d, base_area):
+    dtw.set_option(dtw.OPT_BASE_AREA, base_area)
+    if d == 12:
+        X, Y = synth.chroma_pair(M + N, M, N)
+    else:
+        rng = np.random.default_rng(M * N)
+        X = rng.standard_normal((M, d)).astype(np.float32)
+        Y = rng.standard_normal((N, d)).astype(np.float32)
+    check_float(X, Y)
+
+
+def test_plain_float_config_full():
+    """2000 x 12-d chroma vs its 2500-frame warp (the plain float workload)."""
+    X, Y = synth.workload_plain_float()
+    check_float(X, Y)
+
+
+def test_int_pair_full_size():
+    """M=20000, N=24000 int32: path and cost bit-exact against oracle 1."""
+    X, Y = synth.workload_int_pair()
+    check_int(X, Y)
+    s = dtw.get_stats()
+    M, N = len(X), len(Y)
+    processed = s["sweep_cells"] + s["base_cells"]
+    assert processed <= 2 * M * N + (M + N) * np.log2(M + N)
+    assert processed / (M * N) > 1.5
+
+
+def test_cost_only():
+    X, Y = synth.int_pair(5, 3000, 3500)
+    assert dtw.cost(_cuda(X), _cuda(Y)) == oracle.dtw(X, Y)[1]
+    Xf, Yf = synth.chroma_pair(6, 900, 1000)
+    assert dtw.cost(_cuda(Xf), _cuda(Yf)) == pytest.approx(oracle.dtw(Xf, Yf)[1], rel=REL_TOL)
+
+
+def test_host_buffers_match_device():
+    X, Y = synth.int_pair(8, 1500, 1700)
+    p_dev, c_dev = dtw.align(_cuda(X), _cuda(Y))
+    p_host, c_host = dtw.align(X, Y)  # numpy inputs: staged by the library
+    assert c_dev == c_host
+    assert np.array_equal(p_dev.cpu().numpy(), p_host.numpy())
+
+
+def test_batch_matches_single():
+    pairs = [synth.int_pair(40 + k, m, n) for k, (m, n) in enumerate([(700, 900), (1500, 1200), (3, 2000),
+                                                                         (1, 1), (4000, 3900)])]
+    res = dtw.align_batch([_cuda(x) for x, _ in pairs], [_cuda(y) for _, y in pairs])
+    for (X, Y), (path, cost) in zip(pairs, res):
+        p_ref, c_ref = oracle.dtw(X, Y)
+        assert cost == c_ref
+        assert np.array_equal(path.cpu().numpy(), p_ref)
+
+
+def test_batch_float():
+    pairs = [synth.chroma_pair(60 + k, m, n) for k, (m, n) in enumerate([(500, 600), (800, 700), (40, 30)])]
+    res = dtw.align_batch([_cuda(x) for x, _ in pairs], [_cuda(y) for _, y in pairs])
+    for (X, Y), (path, cost) in zip(pairs, res):
+        c_ref = oracle.dtw(X, Y)[1]
+        assert cost == pytest.approx(c_ref, rel=REL_TOL)
+        assert oracle.path_cost(X, Y, path.cpu().numpy()) == pytest.approx(c_ref, rel=REL_TOL)
+
+
+def test_submit_poll():
+    X, Y = synth.int_pair(9, 800, 900)
+    t, path, keep = dtw.submit(_cuda(X), _cuda(Y))
+    rc, K, c = dtw.poll(t)
+    assert rc == dtw.OK
+    p_ref, c_ref = oracle.dtw(X, Y)
+    assert c == c_ref and np.array_equal(path[:K].cpu().numpy(), p_ref)
+
+
+@pytest.mark.parametrize("kind", ["int", "float"])
+def test_plain_form(kind):
+    """The paper's plain FP64 form (one launch per anti-diagonal) is optimal too."""
+    if kind == "int":
+        X, Y = synth.int_pair(11, 1200, 1000)
+    else:
+        X, Y = synth.chroma_pair(12, 1100, 1300)
+    path, cost = dtw.align(_cuda(X), _cuda(Y), plain=True)
+    p = path.cpu().numpy()
+    check_path_struct(p, len(X), len(Y))
+    c_ref = oracle.dtw(X, Y)[1]
+    if kind == "int":
+        assert cost == c_ref and oracle.path_cost(X, Y, p) == c_ref
+    else:
+        assert cost == pytest.approx(c_ref, rel=1e-12)
+        assert oracle.path_cost(X, Y, p) == pytest.approx(c_ref, rel=1e-12)
+
+
+def test_wait_timeout_reports_status():
+    """A band that never publishes makes the band below give up after a bounded
+    number of polls; the call returns DTW_ETIMEOUT and the library stays usable."""
+    X, Y = synth.int_pair(13, 3000, 3000)
+    dtw.set_option(dtw.OPT_SPIN_LIMIT, 2000)
+    dtw.set_option(dtw.OPT_SKIP_PUBLISH, 0)
+    with pytest.raises(dtw.DTWError) as ei:
+        dtw.align(_cuda(X), _cuda(Y))
+    assert ei.value.status == dtw.ETIMEOUT
+    dtw.set_option(dtw.OPT_SKIP_PUBLISH, -1)
+    dtw.set_option(dtw.OPT_SPIN_LIMIT, 1 << 24)
+    check_int(X, Y)
+
+
+def test_integer_range_guard():
+    X = np.array([0, 2 ** 30], np.int32)
+    Y = np.array([-2 ** 30, 5, 7], np.int32)
+    with pytest.raises(dtw.DTWError) as ei:
+        dtw.align(_cuda(X), _cuda(Y))
+    assert ei.value.status == dtw.EOVERFLOW
+
+
+def test_budget_admission():
+    X, Y = synth.int_pair(14, 5000, 5000)
+    dtw.set_budget(1024)
+    try:
+        with pytest.raises(dtw.DTWError) as ei:
+            dtw.align(_cuda(X), _cuda(Y))
+        assert ei.value.status == dtw.ENOMEM
+    finally:
+        dtw.set_budget(0)
+
+
+def test_arena():
+    X, Y = synth.int_pair(15, 2500, 2000)
+    arena = torch.empty(dtw.footprint(2500, 2000) + (1 << 20), dtype=torch.uint8, device="cuda")
+    dtw.set_arena(arena)
+    try:
+        check_int(X, Y)
+    finally:
+        dtw.set_arena(None)
