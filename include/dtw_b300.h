@@ -156,6 +156,34 @@ DTW_API size_t dtw_footprint(int64_t M, int64_t N, int32_t d, int32_t cost_kind)
 
 DTW_API const char* dtw_strerror(int status);
 
+/*
+ * dtw_cost_noalloc -- D* of one pair, like dtw_cost, without allocating any
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- a process whose device memory is fully
+ * reserved up front (a serving loop, a host application that owns the memory
+ * budget of plug-ins it loads), or code that must not risk the implicit device
+ * synchronisation and the latency of an allocation in the middle of its work.
+ *
+ * All scratch state lives in one fixed device array inside the library (about
+ * 3.4 MB), which every GPU that loads the library keeps until the process
+ * exits.  Limits: min(M, N) <= DTW_NOALLOC_MAX_SHORT and max(M, N) <=
+ * DTW_NOALLOC_MAX_LONG; larger inputs are rejected with DTW_ENOMEM.
+ *   X, Y       DEVICE pointers (host pointers are rejected with DTW_EINVAL)
+ *   cost_kind  DTW_EUCLID_F32 or DTW_ABS_I32 (no form flags)
+ *   cost_out   host double; receives D*
+ *   cuda_stream  stream for the work (a cudaStream_t; NULL = legacy default)
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * reuses the same array and clears what has to start from zero; calls whose GPU
+ * work overlaps (several streams or several threads at once) race on it, so
+ * calls from several host threads are serialised and callers must not run two
+ * on different streams concurrently.  Blocks until *cost_out is written.
+ */
+#define DTW_NOALLOC_MAX_SHORT 262144
+#define DTW_NOALLOC_MAX_LONG 4194304
+DTW_API int dtw_cost_noalloc(const void* X, int64_t M, const void* Y, int64_t N, int32_t d, int32_t cost_kind,
+                             double* cost_out, void* cuda_stream);
+
 /* Counters of the most recent dtw_align / dtw_cost / dtw_align_batch call. */
 typedef struct dtw_stats {
     int64_t problem_cells;   /* sum of M*N over the pairs */

@@ -70,6 +70,7 @@ def _load():
         "dtw_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "dtw_get_stats": (ctypes.c_int, [vp]),
         "dtw_set_option": (ctypes.c_int, [i32, i64]),
+        "dtw_cost_noalloc": (ctypes.c_int, [vp, i64, vp, i64, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -98,7 +99,7 @@ def __getattr__(name):
 # exported names of the C ABI, for the symbol check
 ABI_FUNCTIONS = ("dtw_align", "dtw_cost", "dtw_align_batch", "dtw_submit", "dtw_poll", "dtw_set_stream",
                  "dtw_set_budget", "dtw_set_arena", "dtw_footprint", "dtw_strerror", "dtw_get_stats",
-                 "dtw_set_option")
+                 "dtw_set_option", "dtw_cost_noalloc")
 
 
 def _strerror(status: int) -> str:
@@ -195,6 +196,20 @@ def cost(X, Y):
         _sync_stream(cu)
     c = ctypes.c_double()
     _check(_get_lib().dtw_cost(xp, M, yp, N, d, kind, ctypes.byref(c)), "dtw_cost")
+    return int(c.value) if kind == ABS_I32 else c.value
+
+
+def cost_noalloc(X, Y):
+    """D* through the entry point that allocates no device memory (CUDA inputs only);
+    see dtw_cost_noalloc in include/dtw_b300.h for its size limits."""
+    keep, xp, M, yp, N, d, kind, on_cuda, cu = _prep_pair(X, Y)
+    if cu is None:
+        raise ValueError("dtw_cost_noalloc needs CUDA inputs")
+    import torch
+    torch.cuda.set_device(cu.device)
+    c = ctypes.c_double()
+    st = ctypes.c_void_p(torch.cuda.current_stream(cu.device).cuda_stream)
+    _check(_get_lib().dtw_cost_noalloc(xp, M, yp, N, d, kind, ctypes.byref(c), st), "dtw_cost_noalloc")
     return int(c.value) if kind == ABS_I32 else c.value
 
 
