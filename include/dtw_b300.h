@@ -165,7 +165,7 @@ DTW_API const char* dtw_strerror(int status);
  * synchronisation and the latency of an allocation in the middle of its work.
  *
  * All scratch state lives in one fixed device array inside the library (about
- * 3.4 MB), which every GPU that loads the library keeps until the process
+ * 4.2 MB), which every GPU that loads the library keeps until the process
  * exits.  Limits: min(M, N) <= DTW_NOALLOC_MAX_SHORT and max(M, N) <=
  * DTW_NOALLOC_MAX_LONG; larger inputs are rejected with DTW_ENOMEM.
  *   X, Y       DEVICE pointers (host pointers are rejected with DTW_EINVAL)
@@ -194,6 +194,10 @@ typedef struct dtw_stats {
     int32_t sweep_launches;  /* sweep kernel launches */
     int32_t base_boxes;      /* boxes finished by the base-case kernel */
     int32_t kernel_launches; /* CUDA kernels the call launched */
+    int32_t retagged_boxes;  /* integer boxes whose split window tied and were re-swept with tags */
+    int32_t pad;
+    int64_t resyncs;         /* boundary prefetch refills (a band waited for the band above) */
+    int64_t polls;           /* failed polls of boundary words while waiting */
     double sweep_ms;         /* summed device time of the sweep launches (timing on) */
     double device_ms;        /* device time of the whole call (timing on) */
 } dtw_stats;

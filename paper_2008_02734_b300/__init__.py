@@ -40,10 +40,12 @@ class Stats(ctypes.Structure):
                 ("tag_cells", ctypes.c_int64), ("base_cells", ctypes.c_int64),
                 ("levels", ctypes.c_int32), ("sweep_launches", ctypes.c_int32),
                 ("base_boxes", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("retagged_boxes", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("resyncs", ctypes.c_int64), ("polls", ctypes.c_int64),
                 ("sweep_ms", ctypes.c_double), ("device_ms", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class Request(ctypes.Structure):

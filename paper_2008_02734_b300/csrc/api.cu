@@ -27,8 +27,9 @@ struct Ctx {
     size_t ws_bytes = 0;
     int timing = 0;
     long long base_area = 16384;
-    int spin_limit = 1 << 24;
+    int spin_limit = 1 << 22;
     long long skip_publish = -1;
+    uint32_t epoch = 1;  // next boundary-word epoch; increases across calls
     int num_sms = 0;
     int device = -1;
     dtw_stats stats = {};
@@ -92,6 +93,8 @@ int workspace(Ctx& c, size_t bytes, void** out) {
             cudaGetLastError();
             return DTW_ENOMEM;
         }
+        // boundary words must not carry a future epoch by accident
+        if (cudaMemsetAsync(c.ws, 0, want, c.stream) != cudaSuccess) return DTW_ECUDA;
         c.ws_bytes = want;
     }
     *out = c.ws;
@@ -102,9 +105,9 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte layout of the workspace for a batch (every size linear in sum(M+N)).
 struct Layout {
-    size_t feat, pairs, pres, boxA, boxB, base, sweeps, sres, bufpool, tagpool, outpool, progpool, jlo, jhi, off,
-        path, ctl, total;
-    long long cap_box, cap_base, cap_sweeps, cap_buf, cap_out, cap_prog;
+    size_t feat, pairs, pres, boxA, boxB, base, sweeps, sres, bufpool, outpool, minmax, jlo, jhi, off, path, ctl,
+        total;
+    long long cap_box, cap_base, cap_sweeps, cap_buf, cap_out;
 };
 
 Layout make_layout(int B, long long sumM, long long sumN, long long feat_bytes, long long path_pairs) {
@@ -113,9 +116,9 @@ Layout make_layout(int B, long long sumM, long long sumN, long long feat_bytes, 
     L.cap_box = S / 2 + B + 16;
     L.cap_base = S + B + 16;
     L.cap_sweeps = 2 * L.cap_box;
-    L.cap_buf = 2 * (S + 2 * L.cap_box) + 2 * L.cap_box * 8;
-    L.cap_out = 2 * (S + 2 * L.cap_box);
-    L.cap_prog = S + 3 * L.cap_box;
+    // two 64-bit words per column per sweep (columns padded to 8)
+    L.cap_buf = 4 * (S + 2 * L.cap_box) + 2 * L.cap_box * 16;
+    L.cap_out = 2 * kSplitRowsMax * (S + 2 * L.cap_box);
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t r = o;
@@ -131,9 +134,8 @@ Layout make_layout(int B, long long sumM, long long sumN, long long feat_bytes, 
     L.sweeps = take(sizeof(Sweep) * L.cap_sweeps);
     L.sres = take(sizeof(SweepRes) * L.cap_sweeps);
     L.bufpool = take(8 * (size_t)L.cap_buf);
-    L.tagpool = take(4 * (size_t)L.cap_buf);
     L.outpool = take(8 * (size_t)L.cap_out);
-    L.progpool = take(4 * (size_t)L.cap_prog);
+    L.minmax = take(16 * (size_t)B);
     L.jlo = take(4 * (size_t)sumM);
     L.jhi = take(4 * (size_t)sumM);
     L.off = take(4 * (size_t)sumM);
@@ -190,14 +192,16 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void* const* Y, const int64_t* N, int d,
               int kind, bool want_path, int32_t* const* path_out, int64_t* K_out, double* cost_out) {
     const size_t esize = 4;  // float or int32
-    long long sumM = 0, sumN = 0, feat_bytes = 0, path_pairs = 0, maxM = 0;
+    long long sumM = 0, sumN = 0, feat_bytes = 0, path_pairs = 0, maxM = 0, maxN = 0;
     std::vector<char> xdev(B), ydev(B), pdev(B);
     for (int b = 0; b < B; ++b) {
         if (!X[b] || !Y[b] || M[b] < 1 || N[b] < 1 || M[b] > (1LL << 30) || N[b] > (1LL << 30)) return DTW_EINVAL;
+        if (B > 65535) return DTW_EINVAL;
         if (want_path && !path_out[b]) return DTW_EINVAL;
         sumM += M[b];
         sumN += N[b];
         maxM = std::max<long long>(maxM, M[b]);
+        maxN = std::max<long long>(maxN, N[b]);
         xdev[b] = is_device_ptr(X[b]);
         ydev[b] = is_device_ptr(Y[b]);
         if (!xdev[b]) feat_bytes += align_up((size_t)M[b] * d * esize);
@@ -290,6 +294,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     }
     LevelCtl ctl0{};
     ctl0.n_base = (int32_t)base_roots.size();
+    ctl0.epoch_base = c.epoch;
     e = cudaMemcpyAsync(d_pairs, pd.data(), sizeof(PairDesc) * B, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !roots.empty())
         e = cudaMemcpyAsync(boxA, roots.data(), sizeof(Box) * roots.size(), cudaMemcpyHostToDevice, st);
@@ -297,15 +302,20 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         e = cudaMemcpyAsync(d_base, base_roots.data(), sizeof(Box) * base_roots.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_ctl, &ctl0, sizeof(LevelCtl), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_pres, 0, sizeof(PairRes) * B, st);
+    // only this call's boundary words may bear this call's epochs
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.bufpool, 0, 8 * (size_t)L.cap_buf, st);
     if (e == cudaSuccess && want_path) {
         e = launch_fill_i32(d_jlo, sumM, INT32_MAX, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_jhi, 0xff, 4 * (size_t)sumM, st);
     }
-    if (e == cudaSuccess && kind == KIND_ABS) e = launch_int_range_check(d_pairs, B, d_ctl, st);
+    if (e == cudaSuccess && kind == KIND_ABS)
+        e = launch_int_range_check(d_pairs, B, (int)std::max(maxM, maxN), reinterpret_cast<int32_t*>(ws + L.minmax),
+                                   d_ctl, st);
     if (e != cudaSuccess) return DTW_ECUDA;
 
     // ---- the level loop (Algorithm 2, breadth first: all boxes of a level together)
-    const int mode = !want_path ? MODE_COST : (kind == KIND_ABS ? MODE_TAG : MODE_FB);
+    const int mode = want_path ? MODE_ALIGN : MODE_COST;
+    const int halo = kind == KIND_ABS ? kSplitHalo : 0;
     const int U = sweep_block_cols(kind, d);
     const int BR = sweep_band_rows(kind, d);
     Box* cur = boxA;
@@ -316,37 +326,31 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     LevelCtl hc = ctl0;
     // every level shrinks each box's longer side to at most about half, so the
     // depth is bounded by twice the bits of the longest sequence
-    int launches = (want_path ? 1 : 0) + (kind == KIND_ABS ? 1 : 0);
+    int launches = (want_path ? 1 : 0) + (kind == KIND_ABS ? 3 : 0);
     const int max_levels = 2 * (64 - __builtin_clzll((unsigned long long)std::max(maxM, sumN) + 1)) + 8;
     while (n_cur > 0) {
         if (levels >= max_levels) return DTW_EINTERNAL;
-        PlanArgs pa{cur, n_cur, d_pairs, mode, U, BR, d_sweeps, d_ctl, reinterpret_cast<int32_t*>(ws + L.progpool),
-                    L.cap_sweeps, L.cap_buf, L.cap_out, L.cap_prog};
+        PlanArgs pa{cur, n_cur, d_pairs, mode, kind, halo, U, BR, d_sweeps, d_ctl, L.cap_sweeps, L.cap_buf, L.cap_out};
         e = launch_plan(pa, st);
-        SweepArgs sa{d_sweeps,
-                     d_ctl,
-                     ws + L.bufpool,
-                     reinterpret_cast<int32_t*>(ws + L.tagpool),
-                     ws + L.outpool,
-                     reinterpret_cast<int32_t*>(ws + L.progpool),
-                     d_sres,
-                     d,
-                     c.spin_limit,
-                     c.skip_publish};
+        SweepArgs sa{d_sweeps, d_ctl,        reinterpret_cast<unsigned long long*>(ws + L.bufpool),
+                     ws + L.outpool, d_sres, d, c.spin_limit, c.skip_publish};
         cudaEvent_t s0 = nullptr, s1 = nullptr;
         if (c.timing) s0 = T.mark();
-        if (e == cudaSuccess) e = launch_sweep(kind, d, mode == MODE_TAG, sa, c.num_sms, st);
+        // integer levels may mix tagged and untagged boxes
+        if (e == cudaSuccess) e = launch_sweep(kind, d, mode == MODE_ALIGN && kind == KIND_ABS, sa, c.num_sms, st);
         launches += mode == MODE_COST ? 2 : 3;
         if (c.timing) s1 = T.mark();
         ++sweeps;
         if (e == cudaSuccess && mode != MODE_COST) {
-            SplitArgs sp{cur,  n_cur, d_pairs, d_pres, mode,   kind,    d,  d_sweeps,   d_sres,
-                         ws + L.outpool, nxt, d_base, d_ctl, base_area, (int)L.cap_box, (int)L.cap_base};
+            SplitArgs sp{cur,    n_cur,          d_pairs, d_pres, kind,      d,
+                         halo,   d_sweeps,       d_sres,  ws + L.outpool, nxt, d_base,
+                         d_ctl,  base_area,      (int)L.cap_box, (int)L.cap_base};
             e = launch_split(sp, st);
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return DTW_ECUDA;
+        c.epoch = hc.epoch_base;
         if (c.timing) sweep_ms += elapsed(s0, s1);
         ++levels;
         if (hc.err != ERR_NONE) break;
@@ -400,6 +404,9 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     s.sweep_launches = sweeps;
     s.base_boxes = hc.n_base;
     s.kernel_launches = launches;
+    s.retagged_boxes = (int32_t)hc.retag;
+    s.resyncs = (int64_t)hc.resyncs;
+    s.polls = (int64_t)hc.polls;
     s.sweep_ms = sweep_ms;
     s.device_ms = total_ms;
     return map_device_error(hc.err);
@@ -552,6 +559,8 @@ int dtw_set_arena(void* device_ptr, uint64_t bytes) {
     if (device_ptr && (reinterpret_cast<uintptr_t>(device_ptr) & 255)) return DTW_EINVAL;
     c.arena = device_ptr;
     c.arena_bytes = device_ptr ? bytes : 0;
+    // boundary words must not carry a future epoch by accident
+    if (device_ptr && cudaMemsetAsync(device_ptr, 0, bytes, c.stream) != cudaSuccess) return DTW_ECUDA;
     return DTW_OK;
 }
 

@@ -48,13 +48,19 @@ struct PairRes {
     int32_t pad;
 };
 
-constexpr int BOX_ROOT = 1;
+constexpr int BOX_ROOT = 1;  // the pair's whole problem: its result is the pair's D*
+constexpr int BOX_TAG = 2;   // integer box whose split rows all tied: use a tagged sweep
 
 struct Box {
     int32_t pair, i0, j0, H, W, flags;
     long long known_i;  // optimal cost of the box if known (KIND_ABS), else -1
     double known_f;     // optimal cost of the box (KIND_EUC), NaN if unknown
 };
+
+// Half-width of the window of split rows written by forward/backward sweeps of
+// integer boxes: rows r-kSplitHalo .. r+kSplitHalo around the middle row r.
+constexpr int kSplitHalo = 4;
+constexpr int kSplitRowsMax = 2 * kSplitHalo + 1;
 
 // One wavefront sweep over frame rows [0, rows) x frame columns [0, Q).
 struct Sweep {
@@ -64,17 +70,18 @@ struct Sweep {
     int32_t box;         // index in the level's box array
     int32_t dir;         // 0 forward from the box's first cell, 1 backward from its last
     int32_t axis;        // 0: p runs along X; 1: p runs along Y
-    int32_t rows;        // frame rows swept
+    int32_t rows;        // frame rows swept (0: empty slot)
     int32_t Q;           // frame columns
     int32_t nblk;        // column blocks of the sweep's kernel variant
-    int32_t out_row;     // frame row copied to the out pool (-1: none)
+    int32_t out_row0;    // first frame row copied to the out pool
+    int32_t nout;        // rows copied (0: none)
     int32_t tag_row;     // frame row where split tags start (-1: untagged sweep)
     int32_t nbands;
+    uint32_t epoch0;     // band b stamps its boundary words with epoch0 + b + 1
     int32_t pad;
     long long band_begin;  // first ticket of the sweep
-    long long buf_off;     // boundary-row pool offset (nblk*U entries)
-    long long out_off;     // out pool offset (Q entries, forward column order)
-    long long prog_off;    // progress-counter offset (nbands entries)
+    long long buf_off;     // boundary-row pool offset, in 64-bit words (2 per column)
+    long long out_off;     // out pool offset (nout rows of Q values, forward row and column order)
 };
 
 struct SweepRes {
@@ -93,31 +100,42 @@ struct LevelCtl {
     int32_t n_base;              // boxes appended to the base list (all levels)
     int32_t err;                 // first device error (ERR_*)
     int32_t err_info;
-    int32_t pad;
+    uint32_t epoch_base;         // next unused boundary-word epoch (never reused)
     unsigned long long sweep_cells;
     unsigned long long tag_cells;
     unsigned long long base_cells;
-    long long need_buf;          // pool entries the current level needs
-    long long need_prog;
+    long long need_buf;          // pool words the current level needs
+    long long retag;             // boxes sent back for a tagged sweep
+    unsigned long long resyncs;  // prefetch-ring refills in the sweeps
+    unsigned long long polls;    // failed polls of boundary words
 };
 
 // ---------------------------------------------------------------- memory order
-
-__device__ __forceinline__ int ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(int* p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 __device__ __forceinline__ int ld_relaxed(const int* p) {
     int v;
     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+
+// Boundary words: a 64-bit word carries a 32-bit payload (low half) and the
+// epoch of the band that wrote it (high half).  A single aligned 64-bit relaxed
+// access is single-copy atomic, so a reader that sees the expected epoch holds
+// that band's payload -- no fence or flag is needed, and stale words from earlier
+// bands, levels or calls (smaller epochs) are simply not accepted.
+__device__ __forceinline__ void st_word(unsigned long long* p, uint32_t payload, uint32_t epoch) {
+    const unsigned long long w = ((unsigned long long)epoch << 32) | payload;
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long* p) {
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    return w;
+}
+
+__device__ __forceinline__ uint32_t word_epoch(unsigned long long w) { return (uint32_t)(w >> 32); }
+__device__ __forceinline__ uint32_t word_payload(unsigned long long w) { return (uint32_t)w; }
 
 __device__ __forceinline__ void set_error(LevelCtl* ctl, int code, int info) {
     if (atomicCAS(&ctl->err, ERR_NONE, code) == ERR_NONE) ctl->err_info = info;
@@ -150,6 +168,7 @@ template <> struct Frame<KIND_ABS, 1> {
     __device__ __forceinline__ void load(const void* base, long long idx, int /*d*/) {
         v = __ldg(static_cast<const int32_t*>(base) + idx);
     }
+    __device__ __forceinline__ void load_shared(const void* p) { v = *static_cast<const int32_t*>(p); }
 };
 
 template <int DIM> struct Frame<KIND_EUC, DIM> {
@@ -171,6 +190,22 @@ template <int DIM> struct Frame<KIND_EUC, DIM> {
             for (int e = 0; e < DIM; ++e) v[e] = __ldg(p + e);
         }
     }
+    __device__ __forceinline__ void load_shared(const void* ps) {
+        const float* p = static_cast<const float*>(ps);
+        if constexpr (DIM % 4 == 0) {
+#pragma unroll
+            for (int e = 0; e < DIM / 4; ++e) {
+                const float4 t = reinterpret_cast<const float4*>(p)[e];
+                v[4 * e] = t.x;
+                v[4 * e + 1] = t.y;
+                v[4 * e + 2] = t.z;
+                v[4 * e + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < DIM; ++e) v[e] = p[e];
+        }
+    }
 };
 
 // Runtime dimension: the frame stays in global memory (read through L1).
@@ -181,6 +216,7 @@ template <> struct Frame<KIND_EUC, 0> {
         d = dd;
         p = static_cast<const float*>(base) + idx * dd;
     }
+    __device__ __forceinline__ void load_shared(const void*) {}
 };
 
 // Frame cost C (Section 2.1): |x-y|, or the Euclidean distance (Section 4.1)

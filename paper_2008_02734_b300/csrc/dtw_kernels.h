@@ -12,11 +12,9 @@ namespace dtwb {
 struct SweepArgs {
     const Sweep* sweeps;
     LevelCtl* ctl;
-    void* bufpool;      // boundary rows (Acc)
-    int32_t* tagpool;   // boundary-row split tags, indexed like bufpool
-    void* outpool;      // split rows (Acc), forward column order
-    int32_t* progpool;  // per-band progress counters, indexed by ticket
-    SweepRes* res;      // per-sweep last-cell results
+    unsigned long long* bufpool;  // boundary rows: 2 epoch-stamped words per column
+    void* outpool;                // split rows (Acc), forward row and column order
+    SweepRes* res;                // per-sweep last-cell results
     int d;
     int spin_limit;
     long long skip_ticket;  // test hook: this band never publishes (-1: none)
@@ -28,20 +26,20 @@ int sweep_band_rows(int kind, int d);   // 32*R
 cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, cudaStream_t st);
 
 // Level planning modes
-constexpr int MODE_TAG = 0;   // one tagged forward sweep per box (canonical pivot)
-constexpr int MODE_FB = 1;    // forward half + backward half per box (F + B - C argmin)
-constexpr int MODE_COST = 2;  // one untagged forward sweep of the whole box, last cell only
+constexpr int MODE_ALIGN = 0;  // per box: two half sweeps, or one tagged sweep (BOX_TAG)
+constexpr int MODE_COST = 2;   // one untagged forward sweep of the whole box, last cell only
 
 struct PlanArgs {
     const Box* boxes;
     int n_boxes;
     const PairDesc* pairs;
     int mode;
+    int kind;
+    int halo;  // split rows each side of the middle row written by half sweeps
     int U, BR;
     Sweep* sweeps;
     LevelCtl* ctl;
-    int32_t* progpool;
-    long long cap_sweeps, cap_buf, cap_out, cap_prog;
+    long long cap_sweeps, cap_buf, cap_out;
 };
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st);
 
@@ -50,8 +48,8 @@ struct SplitArgs {
     int n_boxes;
     const PairDesc* pairs;
     PairRes* pres;
-    int mode;
     int kind, d;
+    int halo;
     const Sweep* sweeps;
     const SweepRes* res;
     const void* outpool;
@@ -89,7 +87,9 @@ struct AssembleArgs {
 };
 cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st);
 cudaError_t launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st);
-cudaError_t launch_int_range_check(const PairDesc* pairs, int n_pairs, LevelCtl* ctl, cudaStream_t st);
+// minmax: 4 int32 per pair of scratch (min X, max X, min Y, max Y)
+cudaError_t launch_int_range_check(const PairDesc* pairs, int n_pairs, int max_len, int32_t* minmax, LevelCtl* ctl,
+                                   cudaStream_t st);
 
 // The paper's plain form (plain.cu)
 struct PlainProblem {

@@ -4,6 +4,7 @@
 // share the pivot, finishing small boxes with a full-table DP and backtrace
 // (Section 2.1), and assembling the per-pair warping paths.
 #include <climits>
+#include <type_traits>
 
 #include "dtw_common.cuh"
 #include "dtw_kernels.h"
@@ -70,24 +71,30 @@ __device__ long long block_excl_scan(long long v, long long* total) {
 
 // ---------------------------------------------------------------- plan
 
-// One block of 1024 threads.  For every box of the level: its sweeps (one
-// tagged forward sweep, or a forward half and a backward half, or one full
-// forward sweep), their band tickets and pool offsets; then the level counters.
+// One block of 1024 threads.  Every box owns two sweep slots.  An aligned box
+// gets a forward half sweep (frame rows 0..r+h) and a backward half sweep
+// (rows r-h..P-1 of the reversed box), both ending on the window of split rows
+// r-h..r+h; a box flagged BOX_TAG gets one tagged forward sweep of the whole box
+// (second slot empty); in cost mode the single slot sweeps the whole box.
+// Then band tickets, pool offsets, epochs and the level counters.
 __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
     __shared__ long long carry[3];
     __shared__ unsigned long long cells_sh[2];
-    const int nsw = a.mode == MODE_FB ? 2 : 1;
+    __shared__ uint32_t ep_base;
+    const int nslot = a.mode == MODE_COST ? 1 : 2;
     if (threadIdx.x < 3) carry[threadIdx.x] = 0;
     if (threadIdx.x < 2) cells_sh[threadIdx.x] = 0;
+    if (threadIdx.x == 0) ep_base = a.ctl->epoch_base;
     __syncthreads();
     unsigned long long my_cells = 0, my_tag = 0;
-    for (int base = 0; base < a.n_boxes * nsw; base += blockDim.x) {
+    const int nsw = a.n_boxes * nslot;
+    for (int base = 0; base < nsw; base += blockDim.x) {
         const int s = base + threadIdx.x;
-        const bool valid = s < a.n_boxes * nsw;
+        const bool valid = s < nsw;
         Sweep sw = {};
         long long nb = 0, nbuf = 0, nout = 0;
         if (valid) {
-            const int bi = s / nsw, dir = s % nsw;
+            const int bi = s / nslot, dir = s % nslot;
             const Box b = a.boxes[bi];
             const PairDesc pd = a.pairs[b.pair];
             const Geom g = geom_of(b);
@@ -95,21 +102,26 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             sw.dir = dir;
             sw.axis = g.axis;
             sw.Q = g.Q;
-            sw.nblk = (g.Q + a.U - 1) / a.U;
-            if (a.mode == MODE_TAG) {
+            sw.tag_row = -1;
+            sw.nout = 0;
+            sw.out_row0 = 0;
+            if (a.mode == MODE_COST) {
                 sw.rows = g.P;
-                sw.out_row = g.r;
+            } else if (b.flags & BOX_TAG) {
+                sw.rows = dir == 0 ? g.P : 0;
+                sw.out_row0 = g.r;
+                sw.nout = dir == 0 ? 1 : 0;
                 sw.tag_row = g.r;
-            } else if (a.mode == MODE_FB) {
-                sw.rows = dir == 0 ? g.r + 1 : g.P - g.r;
-                sw.out_row = sw.rows - 1;  // both halves end on the split row
-                sw.tag_row = -1;
             } else {
-                sw.rows = g.P;
-                sw.out_row = -1;
-                sw.tag_row = -1;
+                // the window stays inside rows 1..P-2, so both children are
+                // strictly shorter than the box along the cut side
+                const int h = max(0, min(a.halo, min(g.r - 1, g.P - 2 - g.r)));
+                sw.rows = dir == 0 ? g.r + h + 1 : g.P - g.r + h;
+                sw.nout = 2 * h + 1;  // both halves end on rows r-h..r+h
+                sw.out_row0 = sw.rows - sw.nout;
             }
-            sw.nbands = (sw.rows + a.BR - 1) / a.BR;
+            sw.nblk = sw.rows > 0 ? (g.Q + a.U - 1) / a.U : 0;
+            sw.nbands = sw.rows > 0 ? (sw.rows + a.BR - 1) / a.BR : 0;
             sw.rowseq = g.axis ? pd.Y : pd.X;
             sw.colseq = g.axis ? pd.X : pd.Y;
             const int rb0 = g.axis ? b.j0 : b.i0, rlen = g.axis ? b.W : b.H;
@@ -126,8 +138,10 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
                 sw.cstep = -1;
             }
             nb = sw.nbands;
-            nbuf = (long long)sw.nblk * a.U;
-            nout = a.mode == MODE_COST ? 0 : g.Q;
+            // boundary words per column: one for an untagged integer sweep, two otherwise
+            const int nw = (a.kind == KIND_ABS && sw.tag_row < 0) ? 1 : 2;
+            nbuf = (long long)nw * sw.nblk * a.U;
+            nout = (long long)sw.nout * g.Q;
             my_cells += (unsigned long long)sw.rows * (unsigned long long)g.Q;
             if (sw.tag_row >= 0) my_tag += (unsigned long long)(sw.rows - sw.tag_row) * g.Q;
         }
@@ -137,7 +151,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         const long long e2 = block_excl_scan(nout, &t2);
         if (valid) {
             sw.band_begin = carry[0] + e0;
-            sw.prog_off = carry[0] + e0;
+            sw.epoch0 = ep_base + (uint32_t)(carry[0] + e0);
             sw.buf_off = carry[1] + e1;
             sw.out_off = carry[2] + e2;
             if (s < a.cap_sweeps) a.sweeps[s] = sw;
@@ -153,18 +167,16 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
     atomicAdd(&cells_sh[0], my_cells);
     atomicAdd(&cells_sh[1], my_tag);
     __syncthreads();
-    const long long total_bands = carry[0];
-    const bool fits = (long long)a.n_boxes * nsw <= a.cap_sweeps && carry[1] <= a.cap_buf &&
-                      carry[2] <= a.cap_out && total_bands <= a.cap_prog;
-    for (long long k = threadIdx.x; k < (fits ? total_bands : 0); k += blockDim.x) a.progpool[k] = 0;
     if (threadIdx.x == 0) {
+        const long long total_bands = carry[0];
+        const bool fits = (long long)nsw <= a.cap_sweeps && carry[1] <= a.cap_buf && carry[2] <= a.cap_out;
         LevelCtl* c = a.ctl;
         c->ticket = 0;
         c->n_next = 0;
         c->need_buf = carry[1];
-        c->need_prog = total_bands;
+        c->epoch_base = ep_base + (uint32_t)total_bands + 1u;
         if (fits) {
-            c->n_sweeps = a.n_boxes * nsw;
+            c->n_sweeps = nsw;
             c->n_tickets = total_bands;
             c->sweep_cells += cells_sh[0];
             c->tag_cells += cells_sh[1];
@@ -185,7 +197,7 @@ cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st) {
 
 __device__ __forceinline__ void emit_child(const SplitArgs& a, const Box& c) {
     const long long area = (long long)c.H * c.W;
-    if (area <= a.base_area) {
+    if (area <= a.base_area && !(c.flags & BOX_TAG)) {
         const int k = atomicAdd(&a.ctl->n_base, 1);
         if (k < a.cap_base) a.base[k] = c;
         else set_error(a.ctl, ERR_CAPACITY, 1);
@@ -196,23 +208,38 @@ __device__ __forceinline__ void emit_child(const SplitArgs& a, const Box& c) {
     }
 }
 
+// (min, number of columns attaining it, lowest such column) of one split row
+template <typename V>
+struct RowMin {
+    V v;
+    int n, q;
+};
+
+template <typename V>
+__device__ __forceinline__ RowMin<V> merge(RowMin<V> x, RowMin<V> y) {
+    if (y.v < x.v) return y;
+    if (x.v < y.v) return x;
+    return RowMin<V>{x.v, x.n + y.n, min(x.q, y.q)};
+}
+
 template <int KIND, int DIM>
 __device__ void split_box(const SplitArgs& a, int bi) {
     using Acc = typename AccOf<KIND>::T;
-    __shared__ double s_val[32];
-    __shared__ long long s_ival[32];
-    __shared__ int s_q[32];
+    using V = typename std::conditional<KIND == KIND_ABS, long long, double>::type;
+    __shared__ RowMin<V> s_part[kSplitRowsMax][32];
+    __shared__ int s_choice;
     const Box b = a.boxes[bi];
     const PairDesc pd = a.pairs[b.pair];
     const Geom g = geom_of(b);
-    int qs = 0;
+    int row = g.r, qs = 0;
     long long known_l = 0, known_r = 0, total_i = 0;
     double kl_f = 0, kr_f = 0, total_f = 0;
-    if (a.mode == MODE_TAG) {
+    bool retag = false;
+    if (b.flags & BOX_TAG) {
         // canonical pivot: the tag that reached the box's last cell
         if (threadIdx.x == 0) {
-            const Sweep& sw = a.sweeps[bi];
-            const SweepRes rr = a.res[bi];
+            const Sweep& sw = a.sweeps[2 * bi];
+            const SweepRes rr = a.res[2 * bi];
             qs = rr.end_tag;
             const Acc* out = static_cast<const Acc*>(a.outpool) + sw.out_off;
             if (qs < 0 || qs >= g.Q) {
@@ -234,74 +261,83 @@ __device__ void split_box(const SplitArgs& a, int bi) {
             }
         }
     } else {
-        // F + B - C over the split row (Lemma 2); argmin, ties to the lowest column
+        // S = F + B - C on the window of split rows (Lemma 2): per row, its
+        // minimum, how many columns attain it and the lowest of them
         const Sweep& fw = a.sweeps[2 * bi];
         const Sweep& bw = a.sweeps[2 * bi + 1];
+        const int nr = fw.nout, h = nr / 2;
         const Acc* F = static_cast<const Acc*>(a.outpool) + fw.out_off;
         const Acc* B = static_cast<const Acc*>(a.outpool) + bw.out_off;
-        double best_f = __longlong_as_double(0x7ff0000000000000LL);
-        long long best_i = LLONG_MAX;
-        int best_q = INT_MAX;
+        RowMin<V> part[kSplitRowsMax];
+        for (int m = 0; m < kSplitRowsMax; ++m) part[m] = RowMin<V>{(V)0, 0, INT_MAX};
+        bool first = true;
         for (int q = threadIdx.x; q < g.Q; q += blockDim.x) {
-            int i, j;
-            frame_to_global(b, g.axis, g.r, q, i, j);
-            const Acc c = cell_cost<KIND, DIM>(pd, i, j, a.d);
-            if constexpr (KIND == KIND_ABS) {
-                const long long S = (long long)F[q] + (long long)B[q] - (long long)c;
-                if (S < best_i) {
-                    best_i = S;
-                    best_q = q;
-                }
-            } else {
-                const double S = F[q] + B[q] - c;
-                if (S < best_f) {
-                    best_f = S;
-                    best_q = q;
-                }
-            }
-        }
-        // block argmin (value, then lowest column)
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const double of = __shfl_down_sync(kFull, best_f, o);
-            const long long oi = __shfl_down_sync(kFull, best_i, o);
-            const int oq = __shfl_down_sync(kFull, best_q, o);
-            const bool take = (KIND == KIND_ABS) ? (oi < best_i || (oi == best_i && oq < best_q))
-                                                 : (of < best_f || (of == best_f && oq < best_q));
-            if (take) {
-                best_f = of;
-                best_i = oi;
-                best_q = oq;
+            for (int m = 0; m < kSplitRowsMax; ++m) {
+                if (m < nr) {
+                    int i, j;
+                    frame_to_global(b, g.axis, g.r - h + m, q, i, j);
+                    const V c = (V)cell_cost<KIND, DIM>(pd, i, j, a.d);
+                    const V S = (V)F[(size_t)m * g.Q + q] + (V)B[(size_t)m * g.Q + q] - c;
+                    const RowMin<V> x{S, 1, q};
+                    part[m] = first ? x : merge(part[m], x);
+                }
             }
+            first = false;
         }
-        if (lane == 0) {
-            s_val[wid] = best_f;
-            s_ival[wid] = best_i;
-            s_q[wid] = best_q;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int m = 0; m < nr; ++m) {
+            RowMin<V> x = part[m];
+            for (int o = 16; o; o >>= 1) {
+                RowMin<V> y;
+                y.v = __shfl_down_sync(kFull, x.v, o);
+                y.n = __shfl_down_sync(kFull, x.n, o);
+                y.q = __shfl_down_sync(kFull, x.q, o);
+                if (lane + o < 32) x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
+            }
+            if (lane == 0) s_part[m][wid] = x;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-                const bool take = (KIND == KIND_ABS)
-                                      ? (s_ival[w] < best_i || (s_ival[w] == best_i && s_q[w] < best_q))
-                                      : (s_val[w] < best_f || (s_val[w] == best_f && s_q[w] < best_q));
-                if (take) {
-                    best_f = s_val[w];
-                    best_i = s_ival[w];
-                    best_q = s_q[w];
+            RowMin<V> rm[kSplitRowsMax];
+            for (int m = 0; m < nr; ++m) {
+                RowMin<V> x = s_part[m][0];
+                for (int w = 1; w < nw; ++w) {
+                    const RowMin<V> y = s_part[m][w];
+                    x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
                 }
+                rm[m] = x;
             }
-            qs = best_q;
+            // every split row's minimum is the box's optimal cost (Lemma 2)
+            int pick = -1;
             if constexpr (KIND == KIND_ABS) {
-                total_i = best_i;
-                if (b.known_i >= 0 && b.known_i != total_i) set_error(a.ctl, ERR_CONSIST, 12);
-                known_l = F[qs];
-                known_r = B[qs];
+                for (int m = 0; m < nr; ++m) {
+                    if (rm[m].v != rm[h].v) set_error(a.ctl, ERR_CONSIST, 12);
+                    if (b.known_i >= 0 && rm[m].v != b.known_i) set_error(a.ctl, ERR_CONSIST, 13);
+                }
+                // a row whose minimum is attained once: that cell is on every
+                // optimal path, hence on the canonical one; nearest the middle first
+                for (int k = 0; k <= h && pick < 0; ++k) {
+                    if (rm[h - k].n == 1) pick = h - k;
+                    else if (rm[h + k].n == 1) pick = h + k;
+                }
+                total_i = rm[h].v;
             } else {
-                total_f = best_f;
-                kl_f = F[qs];
-                kr_f = B[qs];
+                pick = h;  // any minimiser gives an optimal path (float kind)
+                total_f = rm[h].v;
+            }
+            if (pick < 0) {
+                retag = true;
+            } else {
+                row = g.r - h + pick;
+                qs = rm[pick].q;
+                if constexpr (KIND == KIND_ABS) {
+                    known_l = F[(size_t)pick * g.Q + qs];
+                    known_r = B[(size_t)pick * g.Q + qs];
+                } else {
+                    kl_f = F[(size_t)pick * g.Q + qs];
+                    kr_f = B[(size_t)pick * g.Q + qs];
+                }
             }
         }
     }
@@ -310,30 +346,38 @@ __device__ void split_box(const SplitArgs& a, int bi) {
             a.pres[b.pair].cost_i = total_i;
             a.pres[b.pair].cost_f = total_f;
         }
-        Box L = b, Rb = b;
-        L.flags = 0;
-        Rb.flags = 0;
-        if (g.axis == 0) {
-            L.H = g.r + 1;
-            L.W = qs + 1;
-            Rb.i0 = b.i0 + g.r;
-            Rb.j0 = b.j0 + qs;
-            Rb.H = b.H - g.r;
-            Rb.W = b.W - qs;
+        if (retag) {  // every split row tied: sweep this box again with split tags
+            Box t = b;
+            t.flags = BOX_TAG;
+            t.known_i = total_i;
+            atomicAdd((unsigned long long*)&a.ctl->retag, 1ULL);
+            emit_child(a, t);
         } else {
-            L.H = qs + 1;
-            L.W = g.r + 1;
-            Rb.i0 = b.i0 + qs;
-            Rb.j0 = b.j0 + g.r;
-            Rb.H = b.H - qs;
-            Rb.W = b.W - g.r;
+            Box L = b, Rb = b;
+            L.flags = 0;
+            Rb.flags = 0;
+            if (g.axis == 0) {
+                L.H = row + 1;
+                L.W = qs + 1;
+                Rb.i0 = b.i0 + row;
+                Rb.j0 = b.j0 + qs;
+                Rb.H = b.H - row;
+                Rb.W = b.W - qs;
+            } else {
+                L.H = qs + 1;
+                L.W = row + 1;
+                Rb.i0 = b.i0 + qs;
+                Rb.j0 = b.j0 + row;
+                Rb.H = b.H - qs;
+                Rb.W = b.W - row;
+            }
+            L.known_i = known_l;
+            Rb.known_i = known_r;
+            L.known_f = kl_f;
+            Rb.known_f = kr_f;
+            emit_child(a, L);
+            emit_child(a, Rb);
         }
-        L.known_i = known_l;
-        Rb.known_i = known_r;
-        L.known_f = kl_f;
-        Rb.known_f = kr_f;
-        emit_child(a, L);
-        emit_child(a, Rb);
     }
 }
 
@@ -565,44 +609,62 @@ cudaError_t launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st)
 }
 
 // Exactness guard of the int32 accumulator: every accumulated cost is at most
-// max|x - y| * (M + N - 1), which must stay below 2^29.
-__global__ void int_range_kernel(const PairDesc* pairs, int n_pairs, LevelCtl* ctl) {
-    __shared__ int smin[2], smax[2];
-    for (int pb = blockIdx.x; pb < n_pairs; pb += gridDim.x) {
-        const PairDesc pd = pairs[pb];
-        if (threadIdx.x < 2) {
-            smin[threadIdx.x] = INT_MAX;
-            smax[threadIdx.x] = INT_MIN;
-        }
-        __syncthreads();
-        int mn[2] = {INT_MAX, INT_MAX}, mx[2] = {INT_MIN, INT_MIN};
-        for (int i = threadIdx.x; i < pd.M; i += blockDim.x) {
+// max|x - y| * (M + N - 1), which must stay below 2^29.  Blocks of a 2-D grid
+// (chunk, pair) reduce min and max of X and Y into minmax[4*pair..4*pair+3].
+__global__ void int_range_kernel(const PairDesc* pairs, int32_t* minmax) {
+    const PairDesc pd = pairs[blockIdx.y];
+    int mn[2] = {INT_MAX, INT_MAX}, mx[2] = {INT_MIN, INT_MIN};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(pd.M, pd.N); i += gridDim.x * blockDim.x) {
+        if (i < pd.M) {
             const int v = static_cast<const int32_t*>(pd.X)[i];
             mn[0] = min(mn[0], v);
             mx[0] = max(mx[0], v);
         }
-        for (int j = threadIdx.x; j < pd.N; j += blockDim.x) {
-            const int v = static_cast<const int32_t*>(pd.Y)[j];
+        if (i < pd.N) {
+            const int v = static_cast<const int32_t*>(pd.Y)[i];
             mn[1] = min(mn[1], v);
             mx[1] = max(mx[1], v);
         }
+    }
+    for (int o = 16; o; o >>= 1) {
         for (int t = 0; t < 2; ++t) {
-            atomicMin(&smin[t], mn[t]);
-            atomicMax(&smax[t], mx[t]);
+            mn[t] = min(mn[t], __shfl_down_sync(kFull, mn[t], o));
+            mx[t] = max(mx[t], __shfl_down_sync(kFull, mx[t], o));
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const long long c1 = (long long)smax[0] - smin[1], c2 = (long long)smax[1] - smin[0];
-            const long long cmax = c1 > c2 ? c1 : c2;
-            if (cmax * ((long long)pd.M + pd.N - 1) >= (1LL << 29)) set_error(ctl, ERR_OVERFLOW, pb);
-        }
-        __syncthreads();
+    }
+    if ((threadIdx.x & 31) == 0) {
+        int32_t* r = minmax + 4 * blockIdx.y;
+        atomicMin(r + 0, mn[0]);
+        atomicMax(r + 1, mx[0]);
+        atomicMin(r + 2, mn[1]);
+        atomicMax(r + 3, mx[1]);
     }
 }
 
-cudaError_t launch_int_range_check(const PairDesc* pairs, int n_pairs, LevelCtl* ctl, cudaStream_t st) {
-    int g = n_pairs < 1024 ? n_pairs : 1024;
-    int_range_kernel<<<g, 256, 0, st>>>(pairs, n_pairs, ctl);
+__global__ void int_range_finish_kernel(const PairDesc* pairs, int n_pairs, const int32_t* minmax, LevelCtl* ctl) {
+    for (int pb = blockIdx.x * blockDim.x + threadIdx.x; pb < n_pairs; pb += gridDim.x * blockDim.x) {
+        const int32_t* r = minmax + 4 * pb;
+        const long long c1 = (long long)r[1] - r[2], c2 = (long long)r[3] - r[0];
+        const long long cmax = c1 > c2 ? c1 : c2;
+        if (cmax * ((long long)pairs[pb].M + pairs[pb].N - 1) >= (1LL << 29)) set_error(ctl, ERR_OVERFLOW, pb);
+    }
+}
+
+__global__ void minmax_init_kernel(int32_t* minmax, int n_pairs) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 4 * n_pairs; k += gridDim.x * blockDim.x)
+        minmax[k] = (k & 1) ? INT_MIN : INT_MAX;
+}
+
+cudaError_t launch_int_range_check(const PairDesc* pairs, int n_pairs, int max_len, int32_t* minmax, LevelCtl* ctl,
+                                   cudaStream_t st) {
+    const int g0 = (4 * n_pairs + 255) / 256;
+    minmax_init_kernel<<<g0 < 1024 ? g0 : 1024, 256, 0, st>>>(minmax, n_pairs);
+    int gx = (max_len + 1023) / 1024;
+    if (gx > 64) gx = 64;
+    dim3 grid(gx < 1 ? 1 : gx, n_pairs);
+    int_range_kernel<<<grid, 256, 0, st>>>(pairs, minmax);
+    const int g1 = (n_pairs + 255) / 256;
+    int_range_finish_kernel<<<g1 < 1024 ? g1 : 1024, 256, 0, st>>>(pairs, n_pairs, minmax, ctl);
     return cudaGetLastError();
 }
 

@@ -3,8 +3,8 @@
 //
 // Everything the sweep needs besides its inputs and its output -- the pair and
 // box descriptors, the sweep descriptor and result, the control block, the
-// boundary row between bands and the per-band progress counters -- lives in one
-// fixed device array defined in this file.  The array is part of the library's
+// integer range scratch and the boundary row between bands -- lives in one fixed
+// device array defined in this file.  The array is part of the library's
 // device image: every GPU that loads the library holds it until the process
 // exits, and every call on a device reuses the same bytes.
 #include <mutex>
@@ -20,7 +20,6 @@ namespace {
 constexpr long long kShortMax = DTW_NOALLOC_MAX_SHORT;  // max min(M, N)
 constexpr long long kLongMax = DTW_NOALLOC_MAX_LONG;    // max max(M, N)
 constexpr long long kPadCols = 64;                      // column padding of the widest kernel variant
-constexpr long long kBandRowsMin = 64;                  // rows per band of every sweep variant
 
 constexpr size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -30,12 +29,10 @@ constexpr size_t kOffBox = kOffPair + up256(sizeof(PairDesc));
 constexpr size_t kOffSweep = kOffBox + up256(sizeof(Box));
 constexpr size_t kOffRes = kOffSweep + up256(sizeof(Sweep));
 constexpr size_t kOffCtl = kOffRes + up256(sizeof(SweepRes));
-constexpr long long kBufEntries = kShortMax + kPadCols;
-constexpr size_t kOffBuf = kOffCtl + up256(sizeof(LevelCtl));
-constexpr size_t kOffTag = kOffBuf + up256(8 * (size_t)kBufEntries);
-constexpr long long kProgEntries = kLongMax / kBandRowsMin + 2;
-constexpr size_t kOffProg = kOffTag + up256(4 * (size_t)kBufEntries);
-constexpr size_t kScratchBytes = kOffProg + up256(4 * (size_t)kProgEntries);
+constexpr size_t kOffMinMax = kOffCtl + up256(sizeof(LevelCtl));
+constexpr long long kBufWords = 2 * (kShortMax + kPadCols);  // two epoch-stamped words per column
+constexpr size_t kOffBuf = kOffMinMax + 256;
+constexpr size_t kScratchBytes = kOffBuf + up256(8 * (size_t)kBufWords);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -45,7 +42,8 @@ void* g_addr[kMaxDevices] = {};  // device address of the scratch array, per dev
 int g_sms[kMaxDevices] = {};
 
 // Writes the pair, the root box and a zeroed control block for this call (the
-// previous call's contents are still there).
+// previous call's contents are still there).  The boundary-word epoch counter
+// is carried over, so that words left by earlier calls are never accepted.
 __global__ void noalloc_init_kernel(const void* X, int M, const void* Y, int N) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     PairDesc* pd = reinterpret_cast<PairDesc*>(g_noalloc_scratch + kOffPair);
@@ -66,7 +64,9 @@ __global__ void noalloc_init_kernel(const void* X, int M, const void* Y, int N) 
     b->known_i = -1;
     b->known_f = 0.0;
     LevelCtl* c = reinterpret_cast<LevelCtl*>(g_noalloc_scratch + kOffCtl);
+    const uint32_t ep = c->epoch_base;
     *c = LevelCtl{};
+    c->epoch_base = ep == 0 ? 1u : ep;
     SweepRes* r = reinterpret_cast<SweepRes*>(g_noalloc_scratch + kOffRes);
     *r = SweepRes{};
 }
@@ -129,17 +129,16 @@ extern "C" int dtw_cost_noalloc(const void* X, int64_t M, const void* Y, int64_t
     Sweep* sweep = reinterpret_cast<Sweep*>(base + kOffSweep);
     SweepRes* res = reinterpret_cast<SweepRes*>(base + kOffRes);
     LevelCtl* ctl = reinterpret_cast<LevelCtl*>(base + kOffCtl);
-    int32_t* prog = reinterpret_cast<int32_t*>(base + kOffProg);
+    int32_t* minmax = reinterpret_cast<int32_t*>(base + kOffMinMax);
 
     noalloc_init_kernel<<<1, 32, 0, st>>>(X, (int)M, Y, (int)N);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && kind == KIND_ABS) e = launch_int_range_check(pairs, 1, ctl, st);
-    // the plan zeroes the progress counters and the ticket before the sweep
-    PlanArgs pa{box, 1, pairs, MODE_COST, sweep_block_cols(kind, d), sweep_band_rows(kind, d), sweep, ctl, prog,
-                1, kBufEntries, 0, kProgEntries};
+    if (e == cudaSuccess && kind == KIND_ABS) e = launch_int_range_check(pairs, 1, (int)hi, minmax, ctl, st);
+    // the plan resets the band ticket and assigns this call's epochs
+    PlanArgs pa{box, 1, pairs, MODE_COST, kind, 0, sweep_block_cols(kind, d), sweep_band_rows(kind, d), sweep, ctl,
+                1, kBufWords, 0};
     if (e == cudaSuccess) e = launch_plan(pa, st);
-    SweepArgs sa{sweep, ctl, base + kOffBuf, reinterpret_cast<int32_t*>(base + kOffTag), nullptr, prog, res, d,
-                 1 << 24, -1};
+    SweepArgs sa{sweep, ctl, reinterpret_cast<unsigned long long*>(base + kOffBuf), nullptr, res, d, 1 << 22, -1};
     if (e == cudaSuccess) e = launch_sweep(kind, d, false, sa, sms, st);
     SweepRes hr{};
     LevelCtl hc{};

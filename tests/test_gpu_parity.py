@@ -49,7 +49,7 @@ def check_float(X, Y):
 def _defaults(cuda_device):
     yield
     dtw.set_option(dtw.OPT_BASE_AREA, 16384)
-    dtw.set_option(dtw.OPT_SPIN_LIMIT, 1 << 24)
+    dtw.set_option(dtw.OPT_SPIN_LIMIT, 1 << 22)
     dtw.set_option(dtw.OPT_SKIP_PUBLISH, -1)
 
 
@@ -77,6 +77,17 @@ def test_int_ties_canonical(alphabet, M, N):
     check_int(X, Y)
     dtw.set_option(dtw.OPT_BASE_AREA, 16384)
     check_int(X, Y)
+
+
+@pytest.mark.parametrize("a,b", [(3, 3), (1, 4)])
+@pytest.mark.parametrize("M,N", [(700, 900), (2000, 1500)])
+def test_int_constant_series_all_rows_tie(a, b, M, N):
+    """Constant series: every cell of every split row ties, so every box falls
+    back to the tagged sweep; the path must still be the canonical one."""
+    X = np.full(M, a, np.int32)
+    Y = np.full(N, b, np.int32)
+    check_int(X, Y)
+    assert dtw.get_stats()["retagged_boxes"] > 0
 
 
 @pytest.mark.parametrize("M,N", [(1, 40000), (40000, 1), (2, 30000), (30000, 3), (5, 9000)])
@@ -187,7 +198,7 @@ def test_wait_timeout_reports_status():
         dtw.align(_cuda(X), _cuda(Y))
     assert ei.value.status == dtw.ETIMEOUT
     dtw.set_option(dtw.OPT_SKIP_PUBLISH, -1)
-    dtw.set_option(dtw.OPT_SPIN_LIMIT, 1 << 24)
+    dtw.set_option(dtw.OPT_SPIN_LIMIT, 1 << 22)
     check_int(X, Y)
 
 
