@@ -330,7 +330,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     const int max_levels = 2 * (64 - __builtin_clzll((unsigned long long)std::max(maxM, sumN) + 1)) + 8;
     while (n_cur > 0) {
         if (levels >= max_levels) return DTW_EINTERNAL;
-        PlanArgs pa{cur, n_cur, d_pairs, mode, kind, halo, U, BR, d_sweeps, d_ctl, L.cap_sweeps, L.cap_buf, L.cap_out};
+        PlanArgs pa{cur, n_cur, d_pairs, mode, kind, halo, U, BR, sweep_group_bands(), d_sweeps, d_ctl, L.cap_sweeps, L.cap_buf, L.cap_out};
         e = launch_plan(pa, st);
         SweepArgs sa{d_sweeps, d_ctl,        reinterpret_cast<unsigned long long*>(ws + L.bufpool),
                      ws + L.outpool, d_sres, d, c.spin_limit, c.skip_publish};

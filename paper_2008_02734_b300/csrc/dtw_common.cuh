@@ -79,8 +79,8 @@ struct Sweep {
     int32_t nbands;
     uint32_t epoch0;     // band b stamps its boundary words with epoch0 + b + 1
     int32_t pad;
-    long long band_begin;  // first ticket of the sweep
-    long long buf_off;     // boundary-row pool offset, in 64-bit words (2 per column)
+    long long band_begin;  // level band number of the sweep's first band
+    long long buf_off;     // boundary-row pool offset, in 64-bit words (1 or 2 per column)
     long long out_off;     // out pool offset (nout rows of Q values, forward row and column order)
 };
 
@@ -93,8 +93,9 @@ struct SweepRes {
 
 // Control block of a call, in device memory.
 struct LevelCtl {
-    unsigned long long ticket;   // next band ticket of the current sweep launch
-    long long n_tickets;         // bands in the current level
+    unsigned long long ticket;   // next ticket (a group of consecutive bands) of the current sweep launch
+    long long n_tickets;         // tickets in the current level
+    long long n_bands;           // bands in the current level
     int32_t n_sweeps;
     int32_t n_next;              // boxes appended to the next level
     int32_t n_base;              // boxes appended to the base list (all levels)

@@ -12,17 +12,18 @@ namespace dtwb {
 struct SweepArgs {
     const Sweep* sweeps;
     LevelCtl* ctl;
-    unsigned long long* bufpool;  // boundary rows: 2 epoch-stamped words per column
+    unsigned long long* bufpool;  // boundary rows: 1 or 2 epoch-stamped words per column
     void* outpool;                // split rows (Acc), forward row and column order
     SweepRes* res;                // per-sweep last-cell results
     int d;
     int spin_limit;
-    long long skip_ticket;  // test hook: this band never publishes (-1: none)
+    long long skip_ticket;  // test hook: this level band never publishes (-1: none)
 };
 
 // Sweep variants
 int sweep_block_cols(int kind, int d);  // U
 int sweep_band_rows(int kind, int d);   // 32*R
+int sweep_group_bands();                // bands per ticket (compute warps per block)
 cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, cudaStream_t st);
 
 // Level planning modes
@@ -36,7 +37,7 @@ struct PlanArgs {
     int mode;
     int kind;
     int halo;  // split rows each side of the middle row written by half sweeps
-    int U, BR;
+    int U, BR, G;  // columns per block, rows per band, bands per ticket
     Sweep* sweeps;
     LevelCtl* ctl;
     long long cap_sweeps, cap_buf, cap_out;

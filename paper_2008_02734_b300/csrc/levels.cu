@@ -177,11 +177,13 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         c->epoch_base = ep_base + (uint32_t)total_bands + 1u;
         if (fits) {
             c->n_sweeps = nsw;
-            c->n_tickets = total_bands;
+            c->n_bands = total_bands;
+            c->n_tickets = (total_bands + a.G - 1) / a.G;
             c->sweep_cells += cells_sh[0];
             c->tag_cells += cells_sh[1];
         } else {
             c->n_sweeps = 0;
+            c->n_bands = 0;
             c->n_tickets = 0;
             set_error(c, ERR_CAPACITY, 0);
         }
