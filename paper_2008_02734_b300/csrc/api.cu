@@ -118,7 +118,8 @@ Layout make_layout(int B, long long sumM, long long sumN, long long feat_bytes, 
     L.cap_sweeps = 2 * L.cap_box;
     // two 64-bit words per column per sweep (columns padded to 8)
     L.cap_buf = 4 * (S + 2 * L.cap_box) + 2 * L.cap_box * 16;
-    L.cap_out = 2 * kSplitRowsMax * (S + 2 * L.cap_box);
+    // out rows: per sweep nout <= kSplitRowsMax rows of its columns padded to whole blocks (<= 8 columns)
+    L.cap_out = kSplitRowsMax * (S + 2 * L.cap_box * 8);
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t r = o;
@@ -314,13 +315,16 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     if (e != cudaSuccess) return DTW_ECUDA;
 
     // ---- the level loop (Algorithm 2, breadth first: all boxes of a level together)
+    // Per level: sweep -> split -> plan of the next level, then one read-back of
+    // the control block (errors, the next level's box and ticket counts, which
+    // size the next sweep's grid).
     const int mode = want_path ? MODE_ALIGN : MODE_COST;
     const int halo = kind == KIND_ABS ? kSplitHalo : 0;
     const int U = sweep_block_cols(kind, d);
     const int BR = sweep_band_rows(kind, d);
+    const int G = sweep_group_bands();
     Box* cur = boxA;
     Box* nxt = boxB;
-    int n_cur = (int)roots.size();
     int levels = 0, sweeps = 0;
     double sweep_ms = 0;
     LevelCtl hc = ctl0;
@@ -328,17 +332,28 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     // depth is bounded by twice the bits of the longest sequence
     int launches = (want_path ? 1 : 0) + (kind == KIND_ABS ? 3 : 0);
     const int max_levels = 2 * (64 - __builtin_clzll((unsigned long long)std::max(maxM, sumN) + 1)) + 8;
-    while (n_cur > 0) {
-        if (levels >= max_levels) return DTW_EINTERNAL;
-        PlanArgs pa{cur, n_cur, d_pairs, mode, kind, halo, U, BR, sweep_group_bands(), d_sweeps, d_ctl, L.cap_sweeps, L.cap_buf, L.cap_out};
+    if (!roots.empty()) {
+        PlanArgs pa{cur, (int)roots.size(), d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
+                    L.cap_sweeps, L.cap_buf, L.cap_out};
         e = launch_plan(pa, st);
+        ++launches;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return DTW_ECUDA;
+        c.epoch = hc.epoch_base;
+    } else {
+        hc.n_cur = 0;
+    }
+    while (hc.err == ERR_NONE && hc.n_cur > 0) {
+        if (levels >= max_levels) return DTW_EINTERNAL;
+        const int n_cur = hc.n_cur;
         SweepArgs sa{d_sweeps, d_ctl,        reinterpret_cast<unsigned long long*>(ws + L.bufpool),
                      ws + L.outpool, d_sres, d, c.spin_limit, c.skip_publish};
         cudaEvent_t s0 = nullptr, s1 = nullptr;
         if (c.timing) s0 = T.mark();
         // integer levels may mix tagged and untagged boxes
-        if (e == cudaSuccess) e = launch_sweep(kind, d, mode == MODE_ALIGN && kind == KIND_ABS, sa, c.num_sms, st);
-        launches += mode == MODE_COST ? 2 : 3;
+        e = launch_sweep(kind, d, mode == MODE_ALIGN && kind == KIND_ABS, sa, c.num_sms, hc.n_tickets, st);
+        ++launches;
         if (c.timing) s1 = T.mark();
         ++sweeps;
         if (e == cudaSuccess && mode != MODE_COST) {
@@ -346,6 +361,12 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
                          halo,   d_sweeps,       d_sres,  ws + L.outpool, nxt, d_base,
                          d_ctl,  base_area,      (int)L.cap_box, (int)L.cap_base};
             e = launch_split(sp, st);
+            ++launches;
+            // plan the next level from the boxes the split appended (count read on the device)
+            PlanArgs pa{nxt, -1, d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
+                        L.cap_sweeps, L.cap_buf, L.cap_out};
+            if (e == cudaSuccess) e = launch_plan(pa, st);
+            ++launches;
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -353,10 +374,8 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         c.epoch = hc.epoch_base;
         if (c.timing) sweep_ms += elapsed(s0, s1);
         ++levels;
-        if (hc.err != ERR_NONE) break;
         if (mode == MODE_COST) break;
         std::swap(cur, nxt);
-        n_cur = hc.n_next;
     }
     if (hc.err == ERR_NONE && mode == MODE_COST) {
         std::vector<SweepRes> sr(B);

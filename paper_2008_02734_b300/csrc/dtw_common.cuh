@@ -78,10 +78,10 @@ struct Sweep {
     int32_t tag_row;     // frame row where split tags start (-1: untagged sweep)
     int32_t nbands;
     uint32_t epoch0;     // band b stamps its boundary words with epoch0 + b + 1
-    int32_t pad;
+    int32_t ostride;     // out-row stride (columns padded to whole blocks)
     long long band_begin;  // level band number of the sweep's first band
     long long buf_off;     // boundary-row pool offset, in 64-bit words (1 or 2 per column)
-    long long out_off;     // out pool offset (nout rows of Q values, forward row and column order)
+    long long out_off;     // out pool offset: nout rows of ostride values, in the sweep's own frame order
 };
 
 struct SweepRes {
@@ -96,6 +96,8 @@ struct LevelCtl {
     unsigned long long ticket;   // next ticket (a group of consecutive bands) of the current sweep launch
     long long n_tickets;         // tickets in the current level
     long long n_bands;           // bands in the current level
+    int32_t n_cur;               // boxes of the current level (set by the plan)
+    int32_t pad0;
     int32_t n_sweeps;
     int32_t n_next;              // boxes appended to the next level
     int32_t n_base;              // boxes appended to the base list (all levels)

@@ -24,7 +24,9 @@ struct SweepArgs {
 int sweep_block_cols(int kind, int d);  // U
 int sweep_band_rows(int kind, int d);   // 32*R
 int sweep_group_bands();                // bands per ticket (compute warps per block)
-cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, cudaStream_t st);
+// max_blocks > 0 caps the grid (one block per ticket suffices); 0: a full persistent grid.
+cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, long long max_blocks,
+                         cudaStream_t st);
 
 // Level planning modes
 constexpr int MODE_ALIGN = 0;  // per box: two half sweeps, or one tagged sweep (BOX_TAG)
@@ -32,7 +34,7 @@ constexpr int MODE_COST = 2;   // one untagged forward sweep of the whole box, l
 
 struct PlanArgs {
     const Box* boxes;
-    int n_boxes;
+    int n_boxes;  // < 0: the count the split kernel left in ctl->n_next
     const PairDesc* pairs;
     int mode;
     int kind;

@@ -84,10 +84,15 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
     const int nslot = a.mode == MODE_COST ? 1 : 2;
     if (threadIdx.x < 3) carry[threadIdx.x] = 0;
     if (threadIdx.x < 2) cells_sh[threadIdx.x] = 0;
-    if (threadIdx.x == 0) ep_base = a.ctl->epoch_base;
+    __shared__ int nbox_sh;
+    if (threadIdx.x == 0) {
+        ep_base = a.ctl->epoch_base;
+        nbox_sh = a.n_boxes >= 0 ? a.n_boxes : a.ctl->n_next;
+    }
     __syncthreads();
+    const int n_boxes = nbox_sh;
     unsigned long long my_cells = 0, my_tag = 0;
-    const int nsw = a.n_boxes * nslot;
+    const int nsw = n_boxes * nslot;
     for (int base = 0; base < nsw; base += blockDim.x) {
         const int s = base + threadIdx.x;
         const bool valid = s < nsw;
@@ -121,6 +126,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
                 sw.out_row0 = sw.rows - sw.nout;
             }
             sw.nblk = sw.rows > 0 ? (g.Q + a.U - 1) / a.U : 0;
+            sw.ostride = sw.nblk * a.U;
             sw.nbands = sw.rows > 0 ? (sw.rows + a.BR - 1) / a.BR : 0;
             sw.rowseq = g.axis ? pd.Y : pd.X;
             sw.colseq = g.axis ? pd.X : pd.Y;
@@ -141,7 +147,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             // boundary words per column: one for an untagged integer sweep, two otherwise
             const int nw = (a.kind == KIND_ABS && sw.tag_row < 0) ? 1 : 2;
             nbuf = (long long)nw * sw.nblk * a.U;
-            nout = (long long)sw.nout * g.Q;
+            nout = (long long)sw.nout * sw.ostride;
             my_cells += (unsigned long long)sw.rows * (unsigned long long)g.Q;
             if (sw.tag_row >= 0) my_tag += (unsigned long long)(sw.rows - sw.tag_row) * g.Q;
         }
@@ -173,6 +179,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         LevelCtl* c = a.ctl;
         c->ticket = 0;
         c->n_next = 0;
+        c->n_cur = n_boxes;
         c->need_buf = carry[1];
         c->epoch_base = ep_base + (uint32_t)total_bands + 1u;
         if (fits) {
@@ -267,9 +274,12 @@ __device__ void split_box(const SplitArgs& a, int bi) {
         // minimum, how many columns attain it and the lowest of them
         const Sweep& fw = a.sweeps[2 * bi];
         const Sweep& bw = a.sweeps[2 * bi + 1];
+        // out rows are stored in each sweep's frame order: the backward sweep's
+        // rows and columns run the other way
         const int nr = fw.nout, h = nr / 2;
+        const int fs = fw.ostride, bs = bw.ostride;
         const Acc* F = static_cast<const Acc*>(a.outpool) + fw.out_off;
-        const Acc* B = static_cast<const Acc*>(a.outpool) + bw.out_off;
+        const Acc* B = static_cast<const Acc*>(a.outpool) + bw.out_off + (size_t)(nr - 1) * bs + (g.Q - 1);
         RowMin<V> part[kSplitRowsMax];
         for (int m = 0; m < kSplitRowsMax; ++m) part[m] = RowMin<V>{(V)0, 0, INT_MAX};
         bool first = true;
@@ -280,7 +290,7 @@ __device__ void split_box(const SplitArgs& a, int bi) {
                     int i, j;
                     frame_to_global(b, g.axis, g.r - h + m, q, i, j);
                     const V c = (V)cell_cost<KIND, DIM>(pd, i, j, a.d);
-                    const V S = (V)F[(size_t)m * g.Q + q] + (V)B[(size_t)m * g.Q + q] - c;
+                    const V S = (V)F[(size_t)m * fs + q] + (V)B[-(long long)m * bs - q] - c;
                     const RowMin<V> x{S, 1, q};
                     part[m] = first ? x : merge(part[m], x);
                 }
@@ -334,11 +344,11 @@ __device__ void split_box(const SplitArgs& a, int bi) {
                 row = g.r - h + pick;
                 qs = rm[pick].q;
                 if constexpr (KIND == KIND_ABS) {
-                    known_l = F[(size_t)pick * g.Q + qs];
-                    known_r = B[(size_t)pick * g.Q + qs];
+                    known_l = F[(size_t)pick * fs + qs];
+                    known_r = B[-(long long)pick * bs - qs];
                 } else {
-                    kl_f = F[(size_t)pick * g.Q + qs];
-                    kr_f = B[(size_t)pick * g.Q + qs];
+                    kl_f = F[(size_t)pick * fs + qs];
+                    kr_f = B[-(long long)pick * bs - qs];
                 }
             }
         }

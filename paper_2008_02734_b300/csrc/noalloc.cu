@@ -140,7 +140,7 @@ extern "C" int dtw_cost_noalloc(const void* X, int64_t M, const void* Y, int64_t
                 1, kBufWords, 0};
     if (e == cudaSuccess) e = launch_plan(pa, st);
     SweepArgs sa{sweep, ctl, reinterpret_cast<unsigned long long*>(base + kOffBuf), nullptr, res, d, 1 << 22, -1};
-    if (e == cudaSuccess) e = launch_sweep(kind, d, false, sa, sms, st);
+    if (e == cudaSuccess) e = launch_sweep(kind, d, false, sa, sms, 0, st);
     SweepRes hr{};
     LevelCtl hc{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hr, res, sizeof(hr), cudaMemcpyDeviceToHost, st);

@@ -39,6 +39,8 @@
 // cell copies the tag of its backpointer (first minimum in the order DIAG, UP,
 // LEFT).  The tag reaching the last cell names the column where the canonical
 // backtrace meets the split row, so that cell lies on the canonical path.
+#include <type_traits>
+
 #include "dtw_common.cuh"
 #include "dtw_kernels.h"
 
@@ -54,11 +56,11 @@ namespace dtwb {
 
 namespace {
 
-constexpr int kG = 4;                  // compute warps (bands) per block
+constexpr int kG = 4;                    // compute warps (bands) per block
 constexpr int kThreads = 32 * (kG + 1);  // + the loader warp
-constexpr int RS = 64;                 // ring slots (column blocks) per warp boundary
-constexpr int KP = 8;                  // progress counters are published every KP blocks
-constexpr int kQuickPolls = 8;         // polls before a waiting warp starts to sleep
+constexpr int URS = 64;                  // slots (column blocks) of a row ring
+constexpr int KC = 8;                    // steps per group: rings are synchronised once per group
+constexpr int CHB = 16;                  // column blocks per loader round of column frames
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ int ld_acquire_cta(const int* p) {
@@ -75,8 +77,14 @@ __device__ __forceinline__ void st_words2(unsigned long long* p, unsigned long l
 __device__ __forceinline__ unsigned long long mkword(uint32_t payload, uint32_t epoch) {
     return ((unsigned long long)epoch << 32) | payload;
 }
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 // Stores / loads n 32-bit words at a shared address aligned to 4*n bytes (n <= 4)
@@ -119,25 +127,47 @@ __device__ __forceinline__ void ld_shared_words(const uint32_t* p, uint32_t* w) 
     }
 }
 
+// Stores U consecutive accumulators (an out row's cells of one column block).
+template <typename T, int U>
+__device__ __forceinline__ void store_row(T* p, const T* v) {
+    if constexpr (sizeof(T) == 4 && U % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < U; i += 4)
+            *reinterpret_cast<int4*>(p + i) = make_int4((int)v[i], (int)v[i + 1], (int)v[i + 2], (int)v[i + 3]);
+    } else if constexpr (sizeof(T) == 8 && U % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < U; i += 2) {
+            double2 t;
+            t.x = (double)v[i];
+            t.y = (double)v[i + 1];
+            *reinterpret_cast<double2*>(p + i) = t;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < U; ++i) p[i] = v[i];
+    }
+}
+
 // Per-warp wait statistics, flushed once per band.
 struct WaitStats {
     unsigned long long waits = 0, polls = 0;
 };
 
 // Spins until *ctr >= target (a shared progress counter; warp-uniform call).
-// Bounded: on expiry records ERR_TIMEOUT and returns the last value seen.
+// The writer is another warp of the same block, on another scheduler, so the
+// wait spins without sleeping.  Bounded: on expiry records ERR_TIMEOUT and
+// returns the last value seen.
 __device__ __forceinline__ int wait_counter(const int* ctr, int target, LevelCtl* ctl, int spin_limit, int info,
                                             bool& gave_up, WaitStats& ws) {
     int v = ld_acquire_cta(ctr);
     if (v >= target || gave_up) return v;
     ++ws.waits;
     for (int it = 1;; ++it) {
-        if (it >= spin_limit || ((it & 63) == 0 && ld_relaxed(&ctl->err) != ERR_NONE)) {
+        if (it >= spin_limit || ((it & 255) == 0 && ld_relaxed(&ctl->err) != ERR_NONE)) {
             set_error(ctl, ERR_TIMEOUT, info);
             gave_up = true;
             return v;
         }
-        if (it > kQuickPolls) __nanosleep(32);
         v = ld_acquire_cta(ctr);
         ++ws.polls;
         if (v >= target) return v;
@@ -168,52 +198,90 @@ __device__ __forceinline__ void unpack(const uint32_t* w, typename AccOf<KIND>::
 
 }  // namespace
 
-// Shared memory of a block: one ring per compute warp (ring g feeds warp g; the
-// loader writes ring 0, warp g-1 writes ring g).
-template <int U, int NWMAX>
+// 32-bit words of one column frame in a frame ring (0: frames are read from
+// global memory by every lane, the runtime-dimension variant).
+template <int KIND, int DIM>
+struct FrameWords {
+    static constexpr int v = KIND == KIND_ABS ? 1 : DIM;
+};
+
+// Shared memory of a block.  Row ring g carries the last row of the band above
+// warp g's band (written by warp g-1, or by the loader from global memory for
+// warp 0); frame ring g carries the column frames of warp g's sweep (written by
+// the loader).  Counters: blocks written (prog) and blocks released by the
+// reader (cons).
+template <int U, int NWMAX, int YW>
 struct StripSmem {
-    static constexpr int SLOT = U * NWMAX;  // words per ring slot
-    __align__(16) uint32_t ring[kG][RS * SLOT];
-    int prog[kG];  // column blocks written into ring g
-    int cons[kG];  // column blocks consumed from ring g
+    static constexpr int YRS = (U * YW <= 4) ? 128 : 64;  // frame ring slots (column blocks)
+    __align__(16) uint32_t uring[kG][URS * U * NWMAX];
+    __align__(16) uint32_t yring[kG][YW > 0 ? YRS * U * YW : 4];
+    int uprog[kG], ucons[kG], yprog[kG], ycons[kG];
     long long ticket;
     int stop;
 };
-
-// Where a band's last row goes.
-constexpr int OUT_NONE = 0;    // last band of its sweep
-constexpr int OUT_RING = 1;    // to the next warp of the block
-constexpr int OUT_GLOBAL = 2;  // to the block holding the band below (boundary row in global memory)
 
 // One band.  TAGM: 0 untagged rows, 1 every row of the band tagged, 2 the band
 // holds tag_row.  VF: the vertical frame move (p-1, q) precedes the horizontal
 // one (p, q-1) in the backpointer order (true when frame rows run along X).
 // NW: payload words per column (1: integer value; 2: value and tag, or the two
 // halves of a double).  SPECIAL: the band holds an out row or the sweep's last row.
+// to_ring / to_global: the band's last row goes to warp g+1 / to the block
+// holding the next band (neither for the last band of a sweep).
+//
+// The step loop runs in groups of KC steps.  All waiting and publishing happens
+// once per group, in warp-uniform code at the group's start; inside a group a
+// step only reads the two rings (its inputs were loaded one step earlier),
+// shuffles, evaluates its R x U cells and lets lane 31 store its last row.
+// Groups in which every lane has a block (the band's steady state) run without
+// per-lane activity tests.
 template <int KIND, int R, int U, int DIM, int NWMAX, int NW, int TAGM, bool VF, bool SPECIAL>
-__device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_idx, int band, int out_mode,
-                                      const SweepArgs& A, uint32_t* rin, int* prog_in, int* cons_in, uint32_t* rout,
-                                      int* prog_out, const int* cons_out) {
+__device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_idx, int band, bool to_ring,
+                                      bool to_global, const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>& sm,
+                                      int g) {
     using Acc = typename AccOf<KIND>::T;
+    using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>;
+    constexpr int YW = FrameWords<KIND, DIM>::v;
+    constexpr int YRS = SM::YRS;
     constexpr bool TAG = TAGM != 0;
-    constexpr int SLOT = U * NWMAX;  // ring slot stride (words)
+    constexpr int SLOT = U * NWMAX;  // row ring slot stride (words)
     constexpr int BW = U * NW;       // payload words per block
     static_assert(BW % 2 == 0, "boundary blocks are written as 16-byte pairs");
     const int lane = threadIdx.x & 31;
     const Acc INF = AccOf<KIND>::inf();
 
-    const int rows = sp->rows, Q = sp->Q, nblk = sp->nblk, rev = sp->dir;
+    const int rows = sp->rows, Q = sp->Q, nblk = sp->nblk;
     const int rbase = sp->rbase, rstep = sp->rstep;
-    const long long cbase = sp->cbase;
-    const int cstep = sp->cstep;
     const void* rowseq = sp->rowseq;
-    const void* colseq = sp->colseq;
-    const int out_row0 = sp->out_row0, nout = sp->nout, tag_row = sp->tag_row;
+    const int out_row0 = sp->out_row0, nout = sp->nout, tag_row = sp->tag_row, ostride = sp->ostride;
     const uint32_t ep_out = sp->epoch0 + (uint32_t)band + 1u;
     unsigned long long* buf = A.bufpool + sp->buf_off;
     Acc* outp = static_cast<Acc*>(A.outpool) + sp->out_off;
     const int p0 = band * (32 * R) + lane * R;
     const int end_k = rows - 1 - p0;
+    const int end_u = (Q - 1) % U;  // the last cell's column within the last block
+    const bool has_above = band > 0;
+    // out rows of this lane: row k goes to orow_ptr[k] (null: not an out row),
+    // U columns per step with one vector store
+    Acc* orow_ptr[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int orow = p0 + k - out_row0;
+        orow_ptr[k] = (SPECIAL && (unsigned)orow < (unsigned)nout) ? outp + (size_t)orow * ostride : nullptr;
+    }
+
+    uint32_t* rin = sm.uring[g];
+    uint32_t* rout = sm.uring[g + 1 < kG ? g + 1 : g];
+    const uint32_t* yr = sm.yring[g];
+    if (!has_above) {
+        // the row above the sweep: D(-1, q) = infinity (Eq. "dtwboundary")
+        uint32_t w[NW];
+        pack<KIND, NW>(INF, 0, w);
+        for (int i = lane; i < URS * U; i += 32) {
+#pragma unroll
+            for (int k = 0; k < NW; ++k) rin[(i / U) * SLOT + (i % U) * NW + k] = w[k];
+        }
+        __syncwarp();
+    }
 
     Frame<KIND, DIM> xr[R];
 #pragma unroll
@@ -241,65 +309,90 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         bott[u] = 0;
     }
 
-    // column frames of the lane's next block (lane l starts at block -l: clamped)
-    auto load_cols = [&](Frame<KIND, DIM>* y, int cb) {
+    // inputs of the next step: the row ring slot of block s (lane 0's row
+    // above; every lane reads the same slot) and the frames of block s - lane
+    uint32_t nwd[BW];
+    Frame<KIND, DIM> ny[U];
+    auto fetch = [&](int s) {
+        ld_shared_words<BW>(rin + (s & (URS - 1)) * SLOT, nwd);
+        const int cb = s - lane;
+        if constexpr (KIND == KIND_ABS && U % 4 == 0) {
+            uint32_t w[U];
+            ld_shared_words<U>(yr + (cb & (YRS - 1)) * U, w);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int q = min(max(cb * U + u, 0), Q - 1);
-            y[u].load(colseq, cbase + (long long)cstep * q, A.d);
+            for (int u = 0; u < U; ++u) ny[u].v = (int32_t)w[u];
+        } else if constexpr (YW > 0) {
+            const uint32_t* ys = yr + (cb & (YRS - 1)) * (U * YW);
+#pragma unroll
+            for (int u = 0; u < U; ++u) ny[u].load_shared(ys + u * YW);
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = min(max(cb * U + u, 0), Q - 1);
+                ny[u].load(sp->colseq, sp->cbase + (long long)sp->cstep * q, A.d);
+            }
         }
     };
-    Frame<KIND, DIM> yn[U];
-    load_cols(yn, -lane);
 
-    const long long fbytes = KIND == KIND_ABS ? 4 : 4LL * (DIM > 0 ? DIM : A.d);  // bytes per column frame
-    const bool has_above = band > 0;
-    Acc end_v = INF;
-    int end_t = -1;
     bool gave_up = false;
     WaitStats ws;
-    int avail = 0;  // blocks known to be in rin
-    int room = RS;  // blocks that may be written to rout
+    Acc end_v = INF;
+    int end_t = -1;
+    int uroom = URS;  // this warp may write blocks < uroom into rout
     const int nsteps = nblk + 31;
-    for (int s = 0; s < nsteps; ++s) {
-        const int cb = s - lane;
-        const bool active = cb >= 0 && cb < nblk;
+
+    // warp-uniform: release what the previous groups read and wrote, wait for
+    // the blocks this group reads, and for room for the blocks it writes
+    auto sync_group = [&](int s0) {
+        if (s0 > 0) {
+            __syncwarp();
+            if (lane == 0) {
+                if (has_above) st_release_cta(&sm.ucons[g], min(s0 + 1, nblk));
+                if (YW > 0 && s0 > 31) st_release_cta(&sm.ycons[g], min(s0 - 30, nblk));
+            }
+            if (to_ring && lane == 31 && s0 > 31) st_release_cta(&sm.uprog[g + 1], min(s0 - 31, nblk));
+        }
+        if (s0 < nblk) {  // lane 0 reads blocks up to s0 + KC (the last one ahead of time)
+            const int need = min(s0 + KC + 1, nblk);
+            if (has_above) wait_counter(&sm.uprog[g], need, A.ctl, A.spin_limit, band, gave_up, ws);
+            if constexpr (YW > 0) wait_counter(&sm.yprog[g], need, A.ctl, A.spin_limit, band, gave_up, ws);
+        }
+        if (to_ring) {  // this group writes blocks up to s0 + KC - 32
+            const int last = s0 + KC - 32;
+            if (last >= uroom)
+                uroom = wait_counter(&sm.ucons[g + 1], last + 1 - URS, A.ctl, A.spin_limit, band, gave_up, ws) + URS;
+        }
+    };
+
+    auto step = [&](int s, auto checked) {
+        constexpr bool CHECK = decltype(checked)::value;
+        uint32_t cw[BW];
+#pragma unroll
+        for (int i = 0; i < BW; ++i) cw[i] = nwd[i];
         Frame<KIND, DIM> yc[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) yc[u] = yn[u];
-        if (lane == 0 && s + 16 < nblk) {
-            const int q = min((s + 16) * U, Q - 1);
-            prefetch_l1(static_cast<const char*>(colseq) + (cbase + (long long)cstep * q) * fbytes);
-        }
-        load_cols(yn, cb + 1);
-
+        for (int u = 0; u < U; ++u) yc[u] = ny[u];
+        fetch(s + 1);
+        const int cb = s - lane;
+        // the row above: lane 0 from the ring, the other lanes by shuffle
         Acc upv[U];
         int upt[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            upv[u] = __shfl_up_sync(kFull, bot[u], 1);
-            if constexpr (TAG) upt[u] = __shfl_up_sync(kFull, bott[u], 1);
-            else upt[u] = 0;
-        }
-        // lane 0: the band above's last row over block s
-        if (has_above) {
-            if (s < nblk && s >= avail) avail = wait_counter(prog_in, s + 1, A.ctl, A.spin_limit, band, gave_up, ws);
-            if (lane == 0 && s < nblk) {
-                uint32_t w[BW];
-                ld_shared_words<BW>(rin + (s % RS) * SLOT, w);
-#pragma unroll
-                for (int u = 0; u < U; ++u) unpack<KIND, NW>(w + u * NW, upv[u], upt[u]);
-            }
-            if (lane == 0 && s < nblk && ((s + 1) % KP == 0 || s == nblk - 1)) st_release_cta(cons_in, s + 1);
-        } else if (lane == 0) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                upv[u] = INF;
+            Acc rv;
+            int rt;
+            unpack<KIND, NW>(cw + u * NW, rv, rt);
+            const Acc sv = __shfl_up_sync(kFull, bot[u], 1);
+            upv[u] = lane == 0 ? rv : sv;
+            if constexpr (TAG) {
+                const int st = __shfl_up_sync(kFull, bott[u], 1);
+                upt[u] = lane == 0 ? rt : st;
+            } else {
                 upt[u] = 0;
             }
         }
-
-        if (active) {
+        if (!CHECK || (unsigned)cb < (unsigned)nblk) {
+            Acc rowv[SPECIAL ? R : 1][U];  // the block's cells, for out rows and the last cell
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int q = cb * U + u;
@@ -325,10 +418,9 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                         LT[k] = t;
                     }
                     if constexpr (SPECIAL) {
-                        const int orow = p0 + k - out_row0;
-                        if ((unsigned)orow < (unsigned)nout && q < Q)
-                            outp[(size_t)(rev ? nout - 1 - orow : orow) * Q + (rev ? Q - 1 - q : q)] = nv;
-                        if (k == end_k && q == Q - 1) {
+                        rowv[k][u] = nv;
+                        // the sweep's last cell lies in the lane's last block (a checked group)
+                        if (CHECK && k == end_k && u == end_u && cb == nblk - 1) {
                             end_v = nv;
                             end_t = t;
                         }
@@ -342,28 +434,43 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
             }
             dprev = upv[U - 1];
             dprevt = upt[U - 1];
+            if constexpr (SPECIAL) {
+#pragma unroll
+                for (int k = 0; k < R; ++k)
+                    if (orow_ptr[k]) store_row<Acc, U>(orow_ptr[k] + (size_t)cb * U, rowv[k]);
+            }
         }
-
         // lane 31: the band's last row over block s-31, for the band below
         const int ob = s - 31;
-        if (out_mode == OUT_RING && ob >= 0) {
-            if (ob >= room) room = wait_counter(cons_out, ob + 1 - RS, A.ctl, A.spin_limit, band, gave_up, ws) + RS;
-            if (lane == 31) {
-                uint32_t w[BW];
-#pragma unroll
-                for (int u = 0; u < U; ++u) pack<KIND, NW>(bot[u], bott[u], w + u * NW);
-                st_shared_words<BW>(rout + (ob % RS) * SLOT, w);
-                if ((ob + 1) % KP == 0 || ob == nblk - 1) st_release_cta(prog_out, ob + 1);
-            }
-        } else if (out_mode == OUT_GLOBAL && ob >= 0 && lane == 31) {
+        if (!CHECK || ob >= 0) {
             uint32_t w[BW];
 #pragma unroll
             for (int u = 0; u < U; ++u) pack<KIND, NW>(bot[u], bott[u], w + u * NW);
-            unsigned long long* dst = buf + (size_t)ob * BW;
+            if (to_ring && lane == 31) {
+                st_shared_words<BW>(rout + (ob & (URS - 1)) * SLOT, w);
+            } else if (to_global && lane == 31) {
+                unsigned long long* dst = buf + (size_t)ob * BW;
 #pragma unroll
-            for (int i = 0; i < BW / 2; ++i) st_words2(dst + 2 * i, mkword(w[2 * i], ep_out), mkword(w[2 * i + 1], ep_out));
+                for (int i = 0; i < BW / 2; ++i)
+                    st_words2(dst + 2 * i, mkword(w[2 * i], ep_out), mkword(w[2 * i + 1], ep_out));
+            }
+        }
+    };
+
+    sync_group(0);
+    fetch(0);
+    for (int s0 = 0; s0 < nsteps; s0 += KC) {
+        if (s0 > 0) sync_group(s0);
+        if (s0 >= 31 && s0 + KC < nblk) {
+#pragma unroll
+            for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{});
+        } else {
+#pragma unroll
+            for (int i = 0; i < KC; ++i)
+                if (s0 + i < nsteps) step(s0 + i, std::true_type{});
         }
     }
+    if (to_ring && lane == 31) st_release_cta(&sm.uprog[g + 1], nblk);
     if constexpr (SPECIAL) {
         if (end_k >= 0 && end_k < R) {
             SweepRes* r = A.res + sweep_idx;
@@ -378,53 +485,137 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     }
 }
 
-// The loader warp: copies the boundary row written by the block above (global
-// memory, epoch-stamped words) into ring 0, 32 columns per round.
-template <int U, int NWMAX, int NW>
-__device__ __noinline__ void run_loader(const Sweep* __restrict__ sp, int band, const SweepArgs& A, uint32_t* ring,
-                                        int* prog, const int* cons) {
+// The loader warp.  Round after round it (a) stages, for every compute warp,
+// the next CHB column blocks of its sweep's column frames into its frame ring
+// (cp.async, all warps' copies in flight together), and (b) for warp 0, when
+// its band continues a band of an earlier block, copies the next 32 columns of
+// that band's boundary row from global memory into row ring 0 once every word
+// bears the expected epoch.  Neither step blocks: a round that can do nothing
+// sleeps briefly, and a bounded number of idle rounds ends in ERR_TIMEOUT.
+template <int KIND, int U, int DIM, int NWMAX, int NW>
+__device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>& sm,
+                                        const int* sweep_of, const int* band_of) {
+    using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>;
+    constexpr int YW = FrameWords<KIND, DIM>::v;
+    constexpr int YRS = SM::YRS;
     constexpr int SLOT = U * NWMAX;
-    static_assert(32 % U == 0, "a round of 32 columns covers whole blocks");
+    constexpr int FB = 4 * YW;  // bytes per frame
+    static_assert(32 % U == 0, "a round of 32 boundary columns covers whole blocks");
     const int lane = threadIdx.x & 31;
-    const unsigned long long* buf = A.bufpool + sp->buf_off;
-    const uint32_t ep = sp->epoch0 + (uint32_t)band;  // epoch of the band above
-    const int nblk = sp->nblk;
-    const int ncol = nblk * U;
+    int ynext[kG], yend[kG];  // frame columns staged so far / to stage
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+        ynext[g] = 0;
+        yend[g] = (YW > 0 && sweep_of[g] >= 0) ? A.sweeps[sweep_of[g]].nblk * U : 0;
+    }
+    // boundary row for warp 0
+    const Sweep* s0 = sweep_of[0] >= 0 ? A.sweeps + sweep_of[0] : nullptr;
+    const int uband = s0 ? band_of[0] : 0;
+    const int uend = (s0 && uband > 0) ? s0->nblk * U : 0;
+    const unsigned long long* ubuf = s0 ? A.bufpool + s0->buf_off : nullptr;
+    const uint32_t uep = s0 ? s0->epoch0 + (uint32_t)uband : 0u;  // epoch of the band above
+    int unext = 0;
     bool gave_up = false;
     WaitStats ws;
-    int room = RS;
-    for (int c0 = 0; c0 < ncol; c0 += 32) {
-        const int b1 = min((c0 + 32) / U, nblk);
-        if (b1 > room) room = wait_counter(cons, b1 - RS, A.ctl, A.spin_limit, band, gave_up, ws) + RS;
-        const int col = c0 + lane;
-        unsigned long long w[NW];
-        bool ok = col >= ncol;
-        for (int it = 0;; ++it) {
-            if (!ok) {
+    for (int idle = 0;;) {
+        bool work_left = false, progress = false;
+        if constexpr (YW > 0) {
+            int issued[kG];
+            bool any = false;
 #pragma unroll
-                for (int i = 0; i < NW; ++i) w[i] = ld_word(buf + (size_t)col * NW + i);
-                ok = true;
+            for (int g = 0; g < kG; ++g) {
+                issued[g] = 0;
+                if (ynext[g] < yend[g]) {
+                    work_left = true;
+                    const Sweep* sp = A.sweeps + sweep_of[g];
+                    const int nblk = yend[g] / U;
+                    const int b1 = min(ynext[g] / U + CHB, nblk);
+                    if (b1 <= ld_acquire_cta(&sm.ycons[g]) + YRS) {
+                        const int Q = sp->Q, cstep = sp->cstep;
+                        const long long cbase = sp->cbase;
+                        const char* cols = static_cast<const char*>(sp->colseq);
+                        uint32_t* yr = sm.yring[g];
+                        for (int c = ynext[g] + lane; c < b1 * U; c += 32) {
+                            const char* src = cols + (cbase + (long long)cstep * min(c, Q - 1)) * FB;
+                            uint32_t* dst = yr + (c % (YRS * U)) * YW;
+                            if constexpr (FB == 4) {
+                                cp_async4(dst, src);
+                            } else {
 #pragma unroll
-                for (int i = 0; i < NW; ++i) ok = ok && word_epoch(w[i]) == ep;
+                                for (int e = 0; e < FB / 16; ++e) cp_async16(dst + 4 * e, src + 16 * e);
+                            }
+                        }
+                        issued[g] = b1;
+                        any = true;
+                    }
+                }
             }
-            if (__all_sync(kFull, ok) || gave_up) break;
-            if (it == 0) ++ws.waits;
-            ++ws.polls;
-            if (it >= A.spin_limit || ((it & 63) == 63 && ld_relaxed(&A.ctl->err) != ERR_NONE)) {
-                set_error(A.ctl, ERR_TIMEOUT, band);
+            if (any) {
+                cp_async_commit_wait_all();
+                __threadfence_block();
+                __syncwarp();
+#pragma unroll
+                for (int g = 0; g < kG; ++g) {
+                    if (issued[g] > 0) {
+                        if (lane == 0) st_release_cta(&sm.yprog[g], issued[g]);
+                        ynext[g] = issued[g] * U;
+                    }
+                }
+                progress = true;
+            }
+        }
+        if (unext < uend) {
+            work_left = true;
+            const int nblk = uend / U;
+            const int b1 = min((unext + 32) / U, nblk);
+            if (b1 <= ld_acquire_cta(&sm.ucons[0]) + URS) {
+                const int col = unext + lane;
+                unsigned long long w[NW];
+                bool ok = col >= uend;
+                if (!ok) {
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) w[i] = ld_word(ubuf + (size_t)col * NW + i);
+                    ok = true;
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) ok = ok && word_epoch(w[i]) == uep;
+                }
+                if (__all_sync(kFull, ok) || gave_up) {
+                    if (col < uend) {
+                        uint32_t* dst = sm.uring[0] + ((col / U) & (URS - 1)) * SLOT + (col % U) * NW;
+#pragma unroll
+                        for (int i = 0; i < NW; ++i) dst[i] = word_payload(w[i]);
+                    }
+                    __threadfence_block();
+                    __syncwarp();
+                    if (lane == 0) st_release_cta(&sm.uprog[0], b1);
+                    unext += 32;
+                    progress = true;
+                } else {
+                    ++ws.polls;
+                }
+            }
+        }
+        if (!work_left) break;
+        if (progress) {
+            idle = 0;
+        } else {
+            if (idle == 0) ++ws.waits;
+            if (++idle >= A.spin_limit || ((idle & 63) == 0 && ld_relaxed(&A.ctl->err) != ERR_NONE)) {
+                if (!gave_up) set_error(A.ctl, ERR_TIMEOUT, uband);
                 gave_up = true;
+                idle = 0;
+                // release every ring so that the compute warps finish (on garbage)
+                if (lane == 0) {
+#pragma unroll
+                    for (int g = 0; g < kG; ++g) {
+                        st_release_cta(&sm.yprog[g], 1 << 30);
+                        if (g == 0) st_release_cta(&sm.uprog[0], 1 << 30);
+                    }
+                }
                 break;
             }
             __nanosleep(64);
         }
-        if (col < ncol) {
-            uint32_t* dst = ring + ((col / U) % RS) * SLOT + (col % U) * NW;
-#pragma unroll
-            for (int i = 0; i < NW; ++i) dst[i] = word_payload(w[i]);
-        }
-        __threadfence_block();
-        __syncwarp();
-        if (lane == 0) st_release_cta(prog, b1);
     }
     if (lane == 0 && ws.waits) {
         atomicAdd(&A.ctl->resyncs, ws.waits);
@@ -433,11 +624,11 @@ __device__ __noinline__ void run_loader(const Sweep* __restrict__ sp, int band, 
 }
 
 template <int KIND, int R, int U, int DIM, int NWMAX, int NW, int TAGM, bool VF>
-__device__ __forceinline__ void run_band_s(bool special, const Sweep* sp, int si, int band, int om,
-                                           const SweepArgs& A, uint32_t* rin, int* pin, int* cin, uint32_t* rout,
-                                           int* pout, const int* cout) {
-    if (special) run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, true>(sp, si, band, om, A, rin, pin, cin, rout, pout, cout);
-    else run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, false>(sp, si, band, om, A, rin, pin, cin, rout, pout, cout);
+__device__ __forceinline__ void run_band_s(bool special, const Sweep* sp, int si, int band, bool to_ring,
+                                           bool to_global, const SweepArgs& A,
+                                           StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>& sm, int g) {
+    if (special) run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, true>(sp, si, band, to_ring, to_global, A, sm, g);
+    else run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, false>(sp, si, band, to_ring, to_global, A, sm, g);
 }
 
 // Index of the sweep holding level band gb: the last sweep whose band_begin is
@@ -457,7 +648,8 @@ __device__ __forceinline__ int find_sweep(const Sweep* sweeps, int n_sweeps, lon
 template <int KIND, int R, int U, int DIM, bool TAGS>
 __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__ SweepArgs A) {
     constexpr int NWMAX = (KIND == KIND_EUC || TAGS) ? 2 : 1;
-    __shared__ StripSmem<U, NWMAX> sm;
+    __shared__ StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v> sm;
+    __shared__ int sweep_of[kG], band_of[kG];
     const int warp = threadIdx.x >> 5;
     const int n_sweeps = A.ctl->n_sweeps;
     const long long n_tickets = A.ctl->n_tickets;
@@ -468,74 +660,76 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
             sm.stop = ld_relaxed(&A.ctl->err) != ERR_NONE;
         }
         if (threadIdx.x < kG) {
-            sm.prog[threadIdx.x] = 0;
-            sm.cons[threadIdx.x] = 0;
+            sm.uprog[threadIdx.x] = 0;
+            sm.ucons[threadIdx.x] = 0;
+            sm.yprog[threadIdx.x] = 0;
+            sm.ycons[threadIdx.x] = 0;
         }
         __syncthreads();
         const long long t = sm.ticket;
         if (t >= n_tickets || sm.stop) break;
         if (warp < kG) {
+            // the warp's band and sweep, also published for the loader
             const long long gb = t * kG + warp;
+            int si = -1, band = 0;
             if (gb < n_bands) {
-                const int si = find_sweep(A.sweeps, n_sweeps, gb);
+                si = find_sweep(A.sweeps, n_sweeps, gb);
+                band = (int)(gb - A.sweeps[si].band_begin);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                sweep_of[warp] = si;
+                band_of[warp] = band;
+            }
+        }
+        __syncthreads();
+        if (warp < kG) {
+            const int si = sweep_of[warp];
+            if (si >= 0) {
+                const long long gb = t * kG + warp;
                 const Sweep* sp = A.sweeps + si;
-                const int band = (int)(gb - sp->band_begin);
+                const int band = band_of[warp];
                 const int nbands = sp->nbands, rows = sp->rows, tag_row = sp->tag_row;
-                int om = band + 1 < nbands ? (warp + 1 < kG ? OUT_RING : OUT_GLOBAL) : OUT_NONE;
-                if (gb == A.skip_ticket) om = OUT_NONE;
+                const bool below = band + 1 < nbands && gb != A.skip_ticket;
+                const bool to_ring = below && warp + 1 < kG;
+                const bool to_global = below && warp + 1 == kG;
                 const int BR = 32 * R;
                 const int b_lo = band * BR, b_hi = b_lo + BR;  // band rows [b_lo, b_hi)
                 const bool special =
                     (sp->nout > 0 && sp->out_row0 < b_hi && sp->out_row0 + sp->nout > b_lo) || (rows - 1 < b_hi);
-                uint32_t* rin = sm.ring[warp];
-                int* pin = &sm.prog[warp];
-                int* cin = &sm.cons[warp];
-                const int wn = warp + 1 < kG ? warp + 1 : warp;  // unused when om != OUT_RING
-                uint32_t* rout = sm.ring[wn];
-                int* pout = &sm.prog[wn];
-                const int* cout = &sm.cons[wn];
                 if constexpr (KIND == KIND_EUC) {
-                    run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true>(special, sp, si, band, om, A, rin, pin, cin, rout,
-                                                                   pout, cout);
+                    run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true>(special, sp, si, band, to_ring, to_global, A, sm,
+                                                                   warp);
                 } else if (!TAGS || tag_row < 0) {
-                    run_band_s<KIND, R, U, DIM, NWMAX, 1, 0, true>(special, sp, si, band, om, A, rin, pin, cin, rout,
-                                                                   pout, cout);
+                    run_band_s<KIND, R, U, DIM, NWMAX, 1, 0, true>(special, sp, si, band, to_ring, to_global, A, sm,
+                                                                   warp);
                 } else if constexpr (TAGS) {
                     const bool vf = sp->axis == 0;
                     if (b_hi <= tag_row) {
-                        run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true>(special, sp, si, band, om, A, rin, pin, cin,
-                                                                       rout, pout, cout);
+                        run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true>(special, sp, si, band, to_ring, to_global, A,
+                                                                       sm, warp);
                     } else if (b_lo > tag_row) {
                         if (vf)
-                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 1, true>(special, sp, si, band, om, A, rin, pin, cin,
-                                                                           rout, pout, cout);
+                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 1, true>(special, sp, si, band, to_ring, to_global,
+                                                                           A, sm, warp);
                         else
-                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 1, false>(special, sp, si, band, om, A, rin, pin,
-                                                                            cin, rout, pout, cout);
+                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 1, false>(special, sp, si, band, to_ring, to_global,
+                                                                            A, sm, warp);
                     } else {
                         if (vf)
-                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 2, true>(special, sp, si, band, om, A, rin, pin, cin,
-                                                                           rout, pout, cout);
+                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 2, true>(special, sp, si, band, to_ring, to_global,
+                                                                           A, sm, warp);
                         else
-                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 2, false>(special, sp, si, band, om, A, rin, pin,
-                                                                            cin, rout, pout, cout);
+                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 2, false>(special, sp, si, band, to_ring, to_global,
+                                                                            A, sm, warp);
                     }
                 }
             }
         } else {
-            // the loader serves warp 0 when its band continues a band of an earlier block
-            const long long gb = t * kG;
-            if (gb < n_bands) {
-                const int si = find_sweep(A.sweeps, n_sweeps, gb);
-                const Sweep* sp = A.sweeps + si;
-                const int band = (int)(gb - sp->band_begin);
-                if (band > 0) {
-                    if (KIND == KIND_EUC || (TAGS && sp->tag_row >= 0))
-                        run_loader<U, NWMAX, 2>(sp, band, A, sm.ring[0], &sm.prog[0], &sm.cons[0]);
-                    else
-                        run_loader<U, NWMAX, 1>(sp, band, A, sm.ring[0], &sm.prog[0], &sm.cons[0]);
-                }
-            }
+            const int si0 = sweep_of[0];
+            if (KIND == KIND_EUC || (TAGS && si0 >= 0 && A.sweeps[si0].tag_row >= 0))
+                run_loader<KIND, U, DIM, NWMAX, 2>(A, sm, sweep_of, band_of);
+            else
+                run_loader<KIND, U, DIM, NWMAX, 1>(A, sm, sweep_of, band_of);
         }
         __syncthreads();
     }
@@ -543,14 +737,20 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
 
 // ---------------------------------------------------------------- launchers
 
+// Grid: one block per ticket up to a full persistent grid.  With fewer tickets
+// than SMs every block gets an SM of its own, so a level with few bands spreads
+// its warps over the schedulers of the whole GPU.
 template <int KIND, int R, int U, int DIM, bool TAGS>
-static cudaError_t launch_one(const SweepArgs& A, int num_sms, cudaStream_t st) {
+static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blocks, cudaStream_t st) {
     static int nb = 0;
     if (nb == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<KIND, R, U, DIM, TAGS>, kThreads, 0);
         if (nb < 1) nb = 1;
     }
-    sweep_kernel<KIND, R, U, DIM, TAGS><<<num_sms * nb, kThreads, 0, st>>>(A);
+    long long grid = (long long)num_sms * nb;
+    if (max_blocks > 0 && max_blocks < grid) grid = max_blocks;
+    if (max_blocks < 0 || grid < 1) grid = 1;
+    sweep_kernel<KIND, R, U, DIM, TAGS><<<(unsigned)grid, kThreads, 0, st>>>(A);
     return cudaGetLastError();
 }
 
@@ -564,13 +764,14 @@ int sweep_block_cols(int kind, int d) { return kind == KIND_ABS ? kIntU : 2; }
 int sweep_band_rows(int kind, int d) { return kind == KIND_ABS ? 32 * kIntR : 64; }
 int sweep_group_bands() { return kG; }
 
-cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, cudaStream_t st) {
+cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, long long max_blocks,
+                         cudaStream_t st) {
     if (kind == KIND_ABS) {
-        if (tags) return launch_one<KIND_ABS, kIntR, kIntU, 1, true>(A, num_sms, st);
-        return launch_one<KIND_ABS, kIntR, kIntU, 1, false>(A, num_sms, st);
+        if (tags) return launch_one<KIND_ABS, kIntR, kIntU, 1, true>(A, num_sms, max_blocks, st);
+        return launch_one<KIND_ABS, kIntR, kIntU, 1, false>(A, num_sms, max_blocks, st);
     }
-    if (d == 12) return launch_one<KIND_EUC, 2, 2, 12, false>(A, num_sms, st);
-    return launch_one<KIND_EUC, 2, 2, 0, false>(A, num_sms, st);
+    if (d == 12) return launch_one<KIND_EUC, 2, 2, 12, false>(A, num_sms, max_blocks, st);
+    return launch_one<KIND_EUC, 2, 2, 0, false>(A, num_sms, max_blocks, st);
 }
 
 }  // namespace dtwb
