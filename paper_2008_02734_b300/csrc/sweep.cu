@@ -59,8 +59,15 @@ namespace {
 constexpr int kG = 4;                    // compute warps (bands) per block
 constexpr int kThreads = 32 * (kG + 1);  // + the loader warp
 constexpr int URS = 64;                  // slots (column blocks) of a row ring
-constexpr int KC = 8;                    // steps per group: rings are synchronised once per group
-constexpr int CHB = 16;                  // column blocks per loader round of column frames
+#ifndef DTW_SWEEP_KC
+#define DTW_SWEEP_KC 8
+#endif
+#ifndef DTW_SWEEP_UNROLL
+#define DTW_SWEEP_UNROLL 2
+#endif
+constexpr int KC = DTW_SWEEP_KC;         // steps per group: rings are synchronised once per group
+constexpr int kGroupUnroll = DTW_SWEEP_UNROLL;
+constexpr int CHB = 32;                  // column blocks per loader round of a frame stream
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ int ld_acquire_cta(const int* p) {
@@ -210,12 +217,18 @@ struct FrameWords {
 // warp 0); frame ring g carries the column frames of warp g's sweep (written by
 // the loader).  Counters: blocks written (prog) and blocks released by the
 // reader (cons).
+//
+// Warps of a block that belong to the same sweep read one frame stream: the
+// ring of the first of them (ystream[g]).  The ring must span the lag between
+// the stream's first and last reader (a few dozen steps per warp) plus the
+// loader's lead, hence YRS slots.
 template <int U, int NWMAX, int YW>
 struct StripSmem {
-    static constexpr int YRS = (U * YW <= 4) ? 128 : 64;  // frame ring slots (column blocks)
+    static constexpr int YRS = 256;  // frame ring slots (column blocks)
     __align__(16) uint32_t uring[kG][URS * U * NWMAX];
     __align__(16) uint32_t yring[kG][YW > 0 ? YRS * U * YW : 4];
     int uprog[kG], ucons[kG], yprog[kG], ycons[kG];
+    int sweep_of[kG], band_of[kG], ystream[kG];
     long long ticket;
     int stop;
 };
@@ -271,7 +284,8 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
 
     uint32_t* rin = sm.uring[g];
     uint32_t* rout = sm.uring[g + 1 < kG ? g + 1 : g];
-    const uint32_t* yr = sm.yring[g];
+    const int ys = sm.ystream[g];
+    const uint32_t* yr = sm.yring[ys];
     if (!has_above) {
         // the row above the sweep: D(-1, q) = infinity (Eq. "dtwboundary")
         uint32_t w[NW];
@@ -355,7 +369,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         if (s0 < nblk) {  // lane 0 reads blocks up to s0 + KC (the last one ahead of time)
             const int need = min(s0 + KC + 1, nblk);
             if (has_above) wait_counter(&sm.uprog[g], need, A.ctl, A.spin_limit, band, gave_up, ws);
-            if constexpr (YW > 0) wait_counter(&sm.yprog[g], need, A.ctl, A.spin_limit, band, gave_up, ws);
+            if constexpr (YW > 0) wait_counter(&sm.yprog[ys], need, A.ctl, A.spin_limit, band, gave_up, ws);
         }
         if (to_ring) {  // this group writes blocks up to s0 + KC - 32
             const int last = s0 + KC - 32;
@@ -364,6 +378,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         }
     };
 
+    const bool w31_ring = to_ring && lane == 31, w31_global = to_global && lane == 31;
     auto step = [&](int s, auto checked) {
         constexpr bool CHECK = decltype(checked)::value;
         uint32_t cw[BW];
@@ -446,9 +461,8 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
             uint32_t w[BW];
 #pragma unroll
             for (int u = 0; u < U; ++u) pack<KIND, NW>(bot[u], bott[u], w + u * NW);
-            if (to_ring && lane == 31) {
-                st_shared_words<BW>(rout + (ob & (URS - 1)) * SLOT, w);
-            } else if (to_global && lane == 31) {
+            if (w31_ring) st_shared_words<BW>(rout + (ob & (URS - 1)) * SLOT, w);
+            if (w31_global) {
                 unsigned long long* dst = buf + (size_t)ob * BW;
 #pragma unroll
                 for (int i = 0; i < BW / 2; ++i)
@@ -462,7 +476,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     for (int s0 = 0; s0 < nsteps; s0 += KC) {
         if (s0 > 0) sync_group(s0);
         if (s0 >= 31 && s0 + KC < nblk) {
-#pragma unroll
+#pragma unroll kGroupUnroll
             for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{});
         } else {
 #pragma unroll
@@ -485,16 +499,17 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     }
 }
 
-// The loader warp.  Round after round it (a) stages, for every compute warp,
-// the next CHB column blocks of its sweep's column frames into its frame ring
-// (cp.async, all warps' copies in flight together), and (b) for warp 0, when
-// its band continues a band of an earlier block, copies the next 32 columns of
-// that band's boundary row from global memory into row ring 0 once every word
-// bears the expected epoch.  Neither step blocks: a round that can do nothing
-// sleeps briefly, and a bounded number of idle rounds ends in ERR_TIMEOUT.
+// The loader warp.  Round after round it (a) issues, for every frame stream
+// with room in its ring, cp.async copies of the next CHB column blocks of the
+// sweep's column frames, (b) for warp 0, when its band continues a band of an
+// earlier block, polls the next 32 columns of that band's boundary row in
+// global memory and, once every word bears the expected epoch, copies the
+// payloads into row ring 0, and (c) waits for the previous round's copies and
+// publishes them (copies stay one round in flight).  Nothing blocks on another
+// warp: a round that can do nothing sleeps briefly, and a bounded number of
+// idle rounds ends in ERR_TIMEOUT.
 template <int KIND, int U, int DIM, int NWMAX, int NW>
-__device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>& sm,
-                                        const int* sweep_of, const int* band_of) {
+__device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>& sm) {
     using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>;
     constexpr int YW = FrameWords<KIND, DIM>::v;
     constexpr int YRS = SM::YRS;
@@ -502,40 +517,46 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
     constexpr int FB = 4 * YW;  // bytes per frame
     static_assert(32 % U == 0, "a round of 32 boundary columns covers whole blocks");
     const int lane = threadIdx.x & 31;
-    int ynext[kG], yend[kG];  // frame columns staged so far / to stage
+    int ynext[kG], yend[kG], ypend[kG];  // blocks issued, to issue, issued in the round in flight
 #pragma unroll
-    for (int g = 0; g < kG; ++g) {
-        ynext[g] = 0;
-        yend[g] = (YW > 0 && sweep_of[g] >= 0) ? A.sweeps[sweep_of[g]].nblk * U : 0;
+    for (int j = 0; j < kG; ++j) {
+        const bool head = sm.sweep_of[j] >= 0 && sm.ystream[j] == j;
+        ynext[j] = 0;
+        ypend[j] = 0;
+        yend[j] = (YW > 0 && head) ? A.sweeps[sm.sweep_of[j]].nblk : 0;
     }
     // boundary row for warp 0
-    const Sweep* s0 = sweep_of[0] >= 0 ? A.sweeps + sweep_of[0] : nullptr;
-    const int uband = s0 ? band_of[0] : 0;
+    const int si0 = sm.sweep_of[0];
+    const Sweep* s0 = si0 >= 0 ? A.sweeps + si0 : nullptr;
+    const int uband = s0 ? sm.band_of[0] : 0;
     const int uend = (s0 && uband > 0) ? s0->nblk * U : 0;
     const unsigned long long* ubuf = s0 ? A.bufpool + s0->buf_off : nullptr;
     const uint32_t uep = s0 ? s0->epoch0 + (uint32_t)uband : 0u;  // epoch of the band above
     int unext = 0;
-    bool gave_up = false;
+    bool gave_up = false, inflight = false;
     WaitStats ws;
     for (int idle = 0;;) {
-        bool work_left = false, progress = false;
+        bool work_left = inflight, progress = false;
+        int issued[kG];
         if constexpr (YW > 0) {
-            int issued[kG];
-            bool any = false;
 #pragma unroll
-            for (int g = 0; g < kG; ++g) {
-                issued[g] = 0;
-                if (ynext[g] < yend[g]) {
+            for (int j = 0; j < kG; ++j) {
+                issued[j] = 0;
+                if (ynext[j] < yend[j]) {
                     work_left = true;
-                    const Sweep* sp = A.sweeps + sweep_of[g];
-                    const int nblk = yend[g] / U;
-                    const int b1 = min(ynext[g] / U + CHB, nblk);
-                    if (b1 <= ld_acquire_cta(&sm.ycons[g]) + YRS) {
+                    const int b1 = min(ynext[j] + CHB, yend[j]);
+                    // room: the slowest reader of the stream
+                    int rc = 1 << 30;
+#pragma unroll
+                    for (int g = 0; g < kG; ++g)
+                        if (sm.ystream[g] == j && sm.sweep_of[g] >= 0) rc = min(rc, ld_acquire_cta(&sm.ycons[g]));
+                    if (b1 <= rc + YRS) {
+                        const Sweep* sp = A.sweeps + sm.sweep_of[j];
                         const int Q = sp->Q, cstep = sp->cstep;
                         const long long cbase = sp->cbase;
                         const char* cols = static_cast<const char*>(sp->colseq);
-                        uint32_t* yr = sm.yring[g];
-                        for (int c = ynext[g] + lane; c < b1 * U; c += 32) {
+                        uint32_t* yr = sm.yring[j];
+                        for (int c = ynext[j] * U + lane; c < b1 * U; c += 32) {
                             const char* src = cols + (cbase + (long long)cstep * min(c, Q - 1)) * FB;
                             uint32_t* dst = yr + (c % (YRS * U)) * YW;
                             if constexpr (FB == 4) {
@@ -545,24 +566,13 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
                                 for (int e = 0; e < FB / 16; ++e) cp_async16(dst + 4 * e, src + 16 * e);
                             }
                         }
-                        issued[g] = b1;
-                        any = true;
+                        issued[j] = b1;
+                        ynext[j] = b1;
+                        progress = true;
                     }
                 }
             }
-            if (any) {
-                cp_async_commit_wait_all();
-                __threadfence_block();
-                __syncwarp();
-#pragma unroll
-                for (int g = 0; g < kG; ++g) {
-                    if (issued[g] > 0) {
-                        if (lane == 0) st_release_cta(&sm.yprog[g], issued[g]);
-                        ynext[g] = issued[g] * U;
-                    }
-                }
-                progress = true;
-            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
         }
         if (unext < uend) {
             work_left = true;
@@ -595,22 +605,33 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
                 }
             }
         }
+        if constexpr (YW > 0) {
+            // the previous round's copies are complete: publish them
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            __threadfence_block();
+            __syncwarp();
+            inflight = false;
+#pragma unroll
+            for (int j = 0; j < kG; ++j) {
+                if (ypend[j] > 0 && lane == 0) st_release_cta(&sm.yprog[j], ypend[j]);
+                ypend[j] = issued[j];
+                inflight = inflight || issued[j] > 0;
+            }
+        }
         if (!work_left) break;
         if (progress) {
             idle = 0;
-        } else {
+        } else if (!inflight) {
             if (idle == 0) ++ws.waits;
             if (++idle >= A.spin_limit || ((idle & 63) == 0 && ld_relaxed(&A.ctl->err) != ERR_NONE)) {
                 if (!gave_up) set_error(A.ctl, ERR_TIMEOUT, uband);
                 gave_up = true;
-                idle = 0;
                 // release every ring so that the compute warps finish (on garbage)
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
                 if (lane == 0) {
 #pragma unroll
-                    for (int g = 0; g < kG; ++g) {
-                        st_release_cta(&sm.yprog[g], 1 << 30);
-                        if (g == 0) st_release_cta(&sm.uprog[0], 1 << 30);
-                    }
+                    for (int j = 0; j < kG; ++j) st_release_cta(&sm.yprog[j], 1 << 30);
+                    st_release_cta(&sm.uprog[0], 1 << 30);
                 }
                 break;
             }
@@ -648,8 +669,11 @@ __device__ __forceinline__ int find_sweep(const Sweep* sweeps, int n_sweeps, lon
 template <int KIND, int R, int U, int DIM, bool TAGS>
 __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__ SweepArgs A) {
     constexpr int NWMAX = (KIND == KIND_EUC || TAGS) ? 2 : 1;
-    __shared__ StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v> sm;
-    __shared__ int sweep_of[kG], band_of[kG];
+    using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SM& sm = *reinterpret_cast<SM*>(smem_raw);
+    int* sweep_of = sm.sweep_of;
+    int* band_of = sm.band_of;
     const int warp = threadIdx.x >> 5;
     const int n_sweeps = A.ctl->n_sweeps;
     const long long n_tickets = A.ctl->n_tickets;
@@ -680,6 +704,12 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
                 sweep_of[warp] = si;
                 band_of[warp] = band;
             }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // frame streams: warps of one sweep share the first one's ring
+            for (int g = 0; g < kG; ++g)
+                sm.ystream[g] = (g > 0 && sweep_of[g] >= 0 && sweep_of[g] == sweep_of[g - 1]) ? sm.ystream[g - 1] : g;
         }
         __syncthreads();
         if (warp < kG) {
@@ -727,9 +757,9 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
         } else {
             const int si0 = sweep_of[0];
             if (KIND == KIND_EUC || (TAGS && si0 >= 0 && A.sweeps[si0].tag_row >= 0))
-                run_loader<KIND, U, DIM, NWMAX, 2>(A, sm, sweep_of, band_of);
+                run_loader<KIND, U, DIM, NWMAX, 2>(A, sm);
             else
-                run_loader<KIND, U, DIM, NWMAX, 1>(A, sm, sweep_of, band_of);
+                run_loader<KIND, U, DIM, NWMAX, 1>(A, sm);
         }
         __syncthreads();
     }
@@ -742,15 +772,20 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
 // its warps over the schedulers of the whole GPU.
 template <int KIND, int R, int U, int DIM, bool TAGS>
 static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blocks, cudaStream_t st) {
+    constexpr int NWMAX = (KIND == KIND_EUC || TAGS) ? 2 : 1;
+    constexpr size_t smem = sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>);
     static int nb = 0;
     if (nb == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<KIND, R, U, DIM, TAGS>, kThreads, 0);
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<KIND, R, U, DIM, TAGS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<KIND, R, U, DIM, TAGS>, kThreads, smem);
         if (nb < 1) nb = 1;
     }
     long long grid = (long long)num_sms * nb;
     if (max_blocks > 0 && max_blocks < grid) grid = max_blocks;
     if (max_blocks < 0 || grid < 1) grid = 1;
-    sweep_kernel<KIND, R, U, DIM, TAGS><<<(unsigned)grid, kThreads, 0, st>>>(A);
+    sweep_kernel<KIND, R, U, DIM, TAGS><<<(unsigned)grid, kThreads, smem, st>>>(A);
     return cudaGetLastError();
 }
 
