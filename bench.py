@@ -63,6 +63,26 @@ def measured_peaks():
     return {"sm_max_mhz": 2032.0, "hbm_gbs": 6400.0}, "fallback"
 
 
+SWEEP_SRC = os.path.join(ROOT, "paper_2008_02734_b300", "csrc", "sweep.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_kernel_int_pair_traffic.json")
+
+
+def sweep_traffic():
+    """DRAM bytes per sweep launch from the committed ncu capture, or None when
+    the capture is missing or the sweep kernel's source changed since it was taken."""
+    import hashlib
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+        with open(SWEEP_SRC, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError):
+        return None, "no capture"
+    if rec.get("source_sha256") != sha:
+        return None, "kernel changed since the capture"
+    return rec.get("dram_bytes_per_launch"), rec.get("command", "")
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -270,8 +290,11 @@ def run_ours(args):
     clk_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     peak_gops = sms * 4 * 32 * clk_mhz * 1e6 / 1e9  # one 32-lane instruction per SMSP per cycle
     achieved = ops / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
+    traffic, traffic_src = sweep_traffic()
     roofline = {"bound": "alu", "kernel": "sweep_kernel", "achieved": achieved, "peak": peak_gops,
-                "unit": "Gop/s", "frac": (achieved / peak_gops) if achieved else None, "traffic": None,
+                "unit": "Gop/s", "frac": (achieved / peak_gops) if achieved else None, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over "
+                                "the sweep launches of one alignment)", "traffic_source": traffic_src,
                 "peak_source": f"{sms} SMs x 4 schedulers x 32 lanes x {clk_mhz:.0f} MHz ({src} max SM clock); "
                                "op = one 32-bit lane instruction of the per-cell count (5 per cell, 7 tagged)",
                 "sweep_ms_per_step": sweep_ms / args.steps, "sweep_launches_per_step": sweep_launches / args.steps,
