@@ -105,9 +105,9 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte layout of the workspace for a batch (every size linear in sum(M+N)).
 struct Layout {
-    size_t feat, pairs, pres, boxA, boxB, base, sweeps, sres, bufpool, outpool, minmax, jlo, jhi, off, path, ctl,
-        total;
-    long long cap_box, cap_base, cap_sweeps, cap_buf, cap_out;
+    size_t feat, pairs, pres, boxA, boxB, base, sweeps, sres, bufpool, outpool, boxdone, partials, minmax, jlo, jhi,
+        off, path, ctl, total;
+    long long cap_box, cap_base, cap_sweeps, cap_buf, cap_out, cap_items;
 };
 
 Layout make_layout(int B, long long sumM, long long sumN, long long feat_bytes, long long path_pairs) {
@@ -120,6 +120,8 @@ Layout make_layout(int B, long long sumM, long long sumN, long long feat_bytes, 
     L.cap_buf = 4 * (S + 2 * L.cap_box) + 2 * L.cap_box * 16;
     // out rows: per sweep nout <= kSplitRowsMax rows of its columns padded to whole blocks (<= 8 columns)
     L.cap_out = kSplitRowsMax * (S + 2 * L.cap_box * 8);
+    // split work items: column chunks of every box's split rows
+    L.cap_items = S / kSplitChunk + L.cap_box + 16;
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t r = o;
@@ -136,6 +138,8 @@ Layout make_layout(int B, long long sumM, long long sumN, long long feat_bytes, 
     L.sres = take(sizeof(SweepRes) * L.cap_sweeps);
     L.bufpool = take(8 * (size_t)L.cap_buf);
     L.outpool = take(8 * (size_t)L.cap_out);
+    L.boxdone = take(4 * (size_t)L.cap_box);
+    L.partials = take(16 * (size_t)kSplitRowsMax * (size_t)L.cap_items);
     L.minmax = take(16 * (size_t)B);
     L.jlo = take(4 * (size_t)sumM);
     L.jhi = take(4 * (size_t)sumM);
@@ -332,9 +336,10 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     // depth is bounded by twice the bits of the longest sequence
     int launches = (want_path ? 1 : 0) + (kind == KIND_ABS ? 3 : 0);
     const int max_levels = 2 * (64 - __builtin_clzll((unsigned long long)std::max(maxM, sumN) + 1)) + 8;
+    int* d_boxdone = reinterpret_cast<int*>(ws + L.boxdone);
     if (!roots.empty()) {
         PlanArgs pa{cur, (int)roots.size(), d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
-                    L.cap_sweeps, L.cap_buf, L.cap_out};
+                    L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items};
         e = launch_plan(pa, st);
         ++launches;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
@@ -359,12 +364,13 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         if (e == cudaSuccess && mode != MODE_COST) {
             SplitArgs sp{cur,    n_cur,          d_pairs, d_pres, kind,      d,
                          halo,   d_sweeps,       d_sres,  ws + L.outpool, nxt, d_base,
-                         d_ctl,  base_area,      (int)L.cap_box, (int)L.cap_base};
+                         d_ctl,  base_area,      (int)L.cap_box, (int)L.cap_base,
+                         d_boxdone, ws + L.partials, hc.n_items, c.num_sms};
             e = launch_split(sp, st);
             ++launches;
             // plan the next level from the boxes the split appended (count read on the device)
             PlanArgs pa{nxt, -1, d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
-                        L.cap_sweeps, L.cap_buf, L.cap_out};
+                        L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items};
             if (e == cudaSuccess) e = launch_plan(pa, st);
             ++launches;
         }

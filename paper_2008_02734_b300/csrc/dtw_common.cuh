@@ -57,6 +57,9 @@ struct Box {
     double known_f;     // optimal cost of the box (KIND_EUC), NaN if unknown
 };
 
+// Columns of a split row handled by one split work item (one 256-thread block).
+constexpr int kSplitChunk = 1024;
+
 // Half-width of the window of split rows written by forward/backward sweeps of
 // integer boxes: rows r-kSplitHalo .. r+kSplitHalo around the middle row r.
 constexpr int kSplitHalo = 4;
@@ -79,6 +82,8 @@ struct Sweep {
     int32_t nbands;
     uint32_t epoch0;     // band b stamps its boundary words with epoch0 + b + 1
     int32_t ostride;     // out-row stride (columns padded to whole blocks)
+    int32_t item0;       // first split work item of the box (forward slot only)
+    int32_t nitems;      // split work items of the box: column chunks of its split rows (forward slot only)
     long long band_begin;  // level band number of the sweep's first band
     long long buf_off;     // boundary-row pool offset, in 64-bit words (1 or 2 per column)
     long long out_off;     // out pool offset: nout rows of ostride values, in the sweep's own frame order
@@ -97,7 +102,7 @@ struct LevelCtl {
     long long n_tickets;         // tickets in the current level
     long long n_bands;           // bands in the current level
     int32_t n_cur;               // boxes of the current level (set by the plan)
-    int32_t pad0;
+    int32_t n_items;             // split work items of the current level
     int32_t n_sweeps;
     int32_t n_next;              // boxes appended to the next level
     int32_t n_base;              // boxes appended to the base list (all levels)

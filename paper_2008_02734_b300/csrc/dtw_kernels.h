@@ -43,6 +43,8 @@ struct PlanArgs {
     Sweep* sweeps;
     LevelCtl* ctl;
     long long cap_sweeps, cap_buf, cap_out;
+    int* box_done;  // per-box split completion counters (reset here; MODE_ALIGN)
+    long long cap_items;
 };
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st);
 
@@ -61,6 +63,10 @@ struct SplitArgs {
     LevelCtl* ctl;
     long long base_area;
     int cap_next, cap_base;
+    int* box_done;    // per-box count of finished work items
+    void* partials;   // per work item: kSplitRowsMax partial row minima (16 B each)
+    int n_items;      // work items of the level (as planned)
+    int num_sms;
 };
 cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
 

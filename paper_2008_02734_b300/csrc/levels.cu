@@ -78,11 +78,11 @@ __device__ long long block_excl_scan(long long v, long long* total) {
 // (second slot empty); in cost mode the single slot sweeps the whole box.
 // Then band tickets, pool offsets, epochs and the level counters.
 __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
-    __shared__ long long carry[3];
+    __shared__ long long carry[4];
     __shared__ unsigned long long cells_sh[2];
     __shared__ uint32_t ep_base;
     const int nslot = a.mode == MODE_COST ? 1 : 2;
-    if (threadIdx.x < 3) carry[threadIdx.x] = 0;
+    if (threadIdx.x < 4) carry[threadIdx.x] = 0;
     if (threadIdx.x < 2) cells_sh[threadIdx.x] = 0;
     __shared__ int nbox_sh;
     if (threadIdx.x == 0) {
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         const int s = base + threadIdx.x;
         const bool valid = s < nsw;
         Sweep sw = {};
-        long long nb = 0, nbuf = 0, nout = 0;
+        long long nb = 0, nbuf = 0, nout = 0, nit = 0;
         if (valid) {
             const int bi = s / nslot, dir = s % nslot;
             const Box b = a.boxes[bi];
@@ -148,18 +148,26 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             const int nw = (a.kind == KIND_ABS && sw.tag_row < 0) ? 1 : 2;
             nbuf = (long long)nw * sw.nblk * a.U;
             nout = (long long)sw.nout * sw.ostride;
+            // split work: the forward slot of an aligned box owns the box's column chunks
+            if (a.mode != MODE_COST && dir == 0) {
+                nit = (b.flags & BOX_TAG) ? 1 : (g.Q + kSplitChunk - 1) / kSplitChunk;
+                if (a.box_done) a.box_done[bi] = 0;
+            }
+            sw.nitems = (int)nit;
             my_cells += (unsigned long long)sw.rows * (unsigned long long)g.Q;
             if (sw.tag_row >= 0) my_tag += (unsigned long long)(sw.rows - sw.tag_row) * g.Q;
         }
-        long long t0, t1, t2;
+        long long t0, t1, t2, t3;
         const long long e0 = block_excl_scan(nb, &t0);
         const long long e1 = block_excl_scan(nbuf, &t1);
         const long long e2 = block_excl_scan(nout, &t2);
+        const long long e3 = block_excl_scan(nit, &t3);
         if (valid) {
             sw.band_begin = carry[0] + e0;
             sw.epoch0 = ep_base + (uint32_t)(carry[0] + e0);
             sw.buf_off = carry[1] + e1;
             sw.out_off = carry[2] + e2;
+            sw.item0 = (int)(carry[3] + e3);
             if (s < a.cap_sweeps) a.sweeps[s] = sw;
         }
         __syncthreads();
@@ -167,6 +175,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             carry[0] += t0;
             carry[1] += t1;
             carry[2] += t2;
+            carry[3] += t3;
         }
         __syncthreads();
     }
@@ -175,7 +184,8 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const long long total_bands = carry[0];
-        const bool fits = (long long)nsw <= a.cap_sweeps && carry[1] <= a.cap_buf && carry[2] <= a.cap_out;
+        const bool fits = (long long)nsw <= a.cap_sweeps && carry[1] <= a.cap_buf && carry[2] <= a.cap_out &&
+                          (a.mode == MODE_COST || carry[3] <= a.cap_items);
         LevelCtl* c = a.ctl;
         c->ticket = 0;
         c->n_next = 0;
@@ -184,12 +194,14 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         c->epoch_base = ep_base + (uint32_t)total_bands + 1u;
         if (fits) {
             c->n_sweeps = nsw;
+            c->n_items = (int)carry[3];
             c->n_bands = total_bands;
             c->n_tickets = (total_bands + a.G - 1) / a.G;
             c->sweep_cells += cells_sh[0];
             c->tag_cells += cells_sh[1];
         } else {
             c->n_sweeps = 0;
+            c->n_items = 0;
             c->n_bands = 0;
             c->n_tickets = 0;
             set_error(c, ERR_CAPACITY, 0);
@@ -231,186 +243,244 @@ __device__ __forceinline__ RowMin<V> merge(RowMin<V> x, RowMin<V> y) {
     return RowMin<V>{x.v, x.n + y.n, min(x.q, y.q)};
 }
 
-template <int KIND, int DIM>
-__device__ void split_box(const SplitArgs& a, int bi) {
+// Partial minima of the window of split rows over one chunk of columns: for
+// every row m, S = F + B - C (Lemma 2) minimised over the chunk, with the number
+// of columns attaining the minimum and the lowest of them.  Block of 256 threads;
+// thread 0 ends up with the merged values in rm[].
+template <int KIND, int DIM, typename V>
+__device__ void chunk_minima(const SplitArgs& a, const Box& b, const PairDesc& pd, const Geom& g, const Sweep& fw,
+                             const Sweep& bw, int q0, int q1, RowMin<V>* rm) {
     using Acc = typename AccOf<KIND>::T;
-    using V = typename std::conditional<KIND == KIND_ABS, long long, double>::type;
-    __shared__ RowMin<V> s_part[kSplitRowsMax][32];
-    __shared__ int s_choice;
-    const Box b = a.boxes[bi];
-    const PairDesc pd = a.pairs[b.pair];
-    const Geom g = geom_of(b);
+    __shared__ RowMin<V> s_part[kSplitRowsMax][8];
+    // out rows are stored in each sweep's frame order: the backward sweep's
+    // rows and columns run the other way
+    const int nr = fw.nout, h = nr / 2;
+    const int fs = fw.ostride, bs = bw.ostride;
+    const Acc* F = static_cast<const Acc*>(a.outpool) + fw.out_off;
+    const Acc* B = static_cast<const Acc*>(a.outpool) + bw.out_off + (size_t)(nr - 1) * bs + (g.Q - 1);
+    RowMin<V> part[kSplitRowsMax];
+#pragma unroll
+    for (int m = 0; m < kSplitRowsMax; ++m) part[m] = RowMin<V>{(V)0, 0, INT_MAX};
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+#pragma unroll
+        for (int m = 0; m < kSplitRowsMax; ++m) {
+            if (m < nr) {
+                int i, j;
+                frame_to_global(b, g.axis, g.r - h + m, q, i, j);
+                const V c = (V)cell_cost<KIND, DIM>(pd, i, j, a.d);
+                const V S = (V)F[(size_t)m * fs + q] + (V)B[-(long long)m * bs - q] - c;
+                const RowMin<V> x{S, 1, q};
+                part[m] = part[m].n == 0 ? x : merge(part[m], x);
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int m = 0; m < nr; ++m) {
+        RowMin<V> x = part[m];
+        for (int o = 16; o; o >>= 1) {
+            RowMin<V> y;
+            y.v = __shfl_down_sync(kFull, x.v, o);
+            y.n = __shfl_down_sync(kFull, x.n, o);
+            y.q = __shfl_down_sync(kFull, x.q, o);
+            if (lane + o < 32) x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
+        }
+        if (lane == 0) s_part[m][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int m = 0; m < nr; ++m) {
+            RowMin<V> x = s_part[m][0];
+            for (int w = 1; w < nw; ++w) {
+                const RowMin<V> y = s_part[m][w];
+                x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
+            }
+            rm[m] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// The box's pivot from the minima of its split rows (thread 0 only), then its
+// two children (or, when every split row tied on an integer box, the box itself
+// again with split tags).
+template <int KIND, int DIM, typename V>
+__device__ void finish_box(const SplitArgs& a, const Box& b, const PairDesc& pd, const Geom& g, const Sweep& fw,
+                           const Sweep& bw, int bi, const RowMin<V>* rm) {
+    using Acc = typename AccOf<KIND>::T;
     int row = g.r, qs = 0;
     long long known_l = 0, known_r = 0, total_i = 0;
     double kl_f = 0, kr_f = 0, total_f = 0;
     bool retag = false;
     if (b.flags & BOX_TAG) {
         // canonical pivot: the tag that reached the box's last cell
-        if (threadIdx.x == 0) {
-            const Sweep& sw = a.sweeps[2 * bi];
-            const SweepRes rr = a.res[2 * bi];
-            qs = rr.end_tag;
-            const Acc* out = static_cast<const Acc*>(a.outpool) + sw.out_off;
-            if (qs < 0 || qs >= g.Q) {
-                set_error(a.ctl, ERR_CONSIST, 10);
-                qs = 0;
-            }
-            int i, j;
-            frame_to_global(b, g.axis, g.r, qs, i, j);
-            const Acc c = cell_cost<KIND, DIM>(pd, i, j, a.d);
-            if constexpr (KIND == KIND_ABS) {
-                total_i = rr.end_i;
-                if (b.known_i >= 0 && b.known_i != total_i) set_error(a.ctl, ERR_CONSIST, 11);
-                known_l = out[qs];
-                known_r = total_i - known_l + c;
-            } else {
-                total_f = rr.end_f;
-                kl_f = out[qs];
-                kr_f = total_f - kl_f + c;
-            }
+        const SweepRes rr = a.res[2 * bi];
+        qs = rr.end_tag;
+        const Acc* out = static_cast<const Acc*>(a.outpool) + fw.out_off;
+        if (qs < 0 || qs >= g.Q) {
+            set_error(a.ctl, ERR_CONSIST, 10);
+            qs = 0;
+        }
+        int i, j;
+        frame_to_global(b, g.axis, g.r, qs, i, j);
+        const Acc c = cell_cost<KIND, DIM>(pd, i, j, a.d);
+        if constexpr (KIND == KIND_ABS) {
+            total_i = rr.end_i;
+            if (b.known_i >= 0 && b.known_i != total_i) set_error(a.ctl, ERR_CONSIST, 11);
+            known_l = out[qs];
+            known_r = total_i - known_l + c;
+        } else {
+            total_f = rr.end_f;
+            kl_f = out[qs];
+            kr_f = total_f - kl_f + c;
         }
     } else {
-        // S = F + B - C on the window of split rows (Lemma 2): per row, its
-        // minimum, how many columns attain it and the lowest of them
-        const Sweep& fw = a.sweeps[2 * bi];
-        const Sweep& bw = a.sweeps[2 * bi + 1];
-        // out rows are stored in each sweep's frame order: the backward sweep's
-        // rows and columns run the other way
         const int nr = fw.nout, h = nr / 2;
         const int fs = fw.ostride, bs = bw.ostride;
         const Acc* F = static_cast<const Acc*>(a.outpool) + fw.out_off;
         const Acc* B = static_cast<const Acc*>(a.outpool) + bw.out_off + (size_t)(nr - 1) * bs + (g.Q - 1);
-        RowMin<V> part[kSplitRowsMax];
-        for (int m = 0; m < kSplitRowsMax; ++m) part[m] = RowMin<V>{(V)0, 0, INT_MAX};
-        bool first = true;
-        for (int q = threadIdx.x; q < g.Q; q += blockDim.x) {
-#pragma unroll
-            for (int m = 0; m < kSplitRowsMax; ++m) {
-                if (m < nr) {
-                    int i, j;
-                    frame_to_global(b, g.axis, g.r - h + m, q, i, j);
-                    const V c = (V)cell_cost<KIND, DIM>(pd, i, j, a.d);
-                    const V S = (V)F[(size_t)m * fs + q] + (V)B[-(long long)m * bs - q] - c;
-                    const RowMin<V> x{S, 1, q};
-                    part[m] = first ? x : merge(part[m], x);
-                }
-            }
-            first = false;
-        }
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int m = 0; m < nr; ++m) {
-            RowMin<V> x = part[m];
-            for (int o = 16; o; o >>= 1) {
-                RowMin<V> y;
-                y.v = __shfl_down_sync(kFull, x.v, o);
-                y.n = __shfl_down_sync(kFull, x.n, o);
-                y.q = __shfl_down_sync(kFull, x.q, o);
-                if (lane + o < 32) x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
-            }
-            if (lane == 0) s_part[m][wid] = x;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            RowMin<V> rm[kSplitRowsMax];
+        // every split row's minimum is the box's optimal cost (Lemma 2)
+        int pick = -1;
+        if constexpr (KIND == KIND_ABS) {
             for (int m = 0; m < nr; ++m) {
-                RowMin<V> x = s_part[m][0];
-                for (int w = 1; w < nw; ++w) {
-                    const RowMin<V> y = s_part[m][w];
-                    x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
-                }
-                rm[m] = x;
+                if (rm[m].v != rm[h].v) set_error(a.ctl, ERR_CONSIST, 12);
+                if (b.known_i >= 0 && rm[m].v != b.known_i) set_error(a.ctl, ERR_CONSIST, 13);
             }
-            // every split row's minimum is the box's optimal cost (Lemma 2)
-            int pick = -1;
+            // a row whose minimum is attained once: that cell is on every
+            // optimal path, hence on the canonical one; nearest the middle first
+            for (int k = 0; k <= h && pick < 0; ++k) {
+                if (rm[h - k].n == 1) pick = h - k;
+                else if (rm[h + k].n == 1) pick = h + k;
+            }
+            total_i = rm[h].v;
+        } else {
+            pick = h;  // any minimiser gives an optimal path (float kind)
+            total_f = rm[h].v;
+        }
+        if (pick < 0) {
+            retag = true;
+        } else {
+            row = g.r - h + pick;
+            qs = rm[pick].q;
             if constexpr (KIND == KIND_ABS) {
-                for (int m = 0; m < nr; ++m) {
-                    if (rm[m].v != rm[h].v) set_error(a.ctl, ERR_CONSIST, 12);
-                    if (b.known_i >= 0 && rm[m].v != b.known_i) set_error(a.ctl, ERR_CONSIST, 13);
-                }
-                // a row whose minimum is attained once: that cell is on every
-                // optimal path, hence on the canonical one; nearest the middle first
-                for (int k = 0; k <= h && pick < 0; ++k) {
-                    if (rm[h - k].n == 1) pick = h - k;
-                    else if (rm[h + k].n == 1) pick = h + k;
-                }
-                total_i = rm[h].v;
+                known_l = F[(size_t)pick * fs + qs];
+                known_r = B[-(long long)pick * bs - qs];
             } else {
-                pick = h;  // any minimiser gives an optimal path (float kind)
-                total_f = rm[h].v;
-            }
-            if (pick < 0) {
-                retag = true;
-            } else {
-                row = g.r - h + pick;
-                qs = rm[pick].q;
-                if constexpr (KIND == KIND_ABS) {
-                    known_l = F[(size_t)pick * fs + qs];
-                    known_r = B[-(long long)pick * bs - qs];
-                } else {
-                    kl_f = F[(size_t)pick * fs + qs];
-                    kr_f = B[-(long long)pick * bs - qs];
-                }
+                kl_f = F[(size_t)pick * fs + qs];
+                kr_f = B[-(long long)pick * bs - qs];
             }
         }
     }
-    if (threadIdx.x == 0) {
-        if (b.flags & BOX_ROOT) {
-            a.pres[b.pair].cost_i = total_i;
-            a.pres[b.pair].cost_f = total_f;
-        }
-        if (retag) {  // every split row tied: sweep this box again with split tags
-            Box t = b;
-            t.flags = BOX_TAG;
-            t.known_i = total_i;
-            atomicAdd((unsigned long long*)&a.ctl->retag, 1ULL);
-            emit_child(a, t);
+    if (b.flags & BOX_ROOT) {
+        a.pres[b.pair].cost_i = total_i;
+        a.pres[b.pair].cost_f = total_f;
+    }
+    if (retag) {  // every split row tied: sweep this box again with split tags
+        Box t = b;
+        t.flags = BOX_TAG;
+        t.known_i = total_i;
+        atomicAdd((unsigned long long*)&a.ctl->retag, 1ULL);
+        emit_child(a, t);
+    } else {
+        Box L = b, Rb = b;
+        L.flags = 0;
+        Rb.flags = 0;
+        if (g.axis == 0) {
+            L.H = row + 1;
+            L.W = qs + 1;
+            Rb.i0 = b.i0 + row;
+            Rb.j0 = b.j0 + qs;
+            Rb.H = b.H - row;
+            Rb.W = b.W - qs;
         } else {
-            Box L = b, Rb = b;
-            L.flags = 0;
-            Rb.flags = 0;
-            if (g.axis == 0) {
-                L.H = row + 1;
-                L.W = qs + 1;
-                Rb.i0 = b.i0 + row;
-                Rb.j0 = b.j0 + qs;
-                Rb.H = b.H - row;
-                Rb.W = b.W - qs;
-            } else {
-                L.H = qs + 1;
-                L.W = row + 1;
-                Rb.i0 = b.i0 + qs;
-                Rb.j0 = b.j0 + row;
-                Rb.H = b.H - qs;
-                Rb.W = b.W - row;
-            }
-            L.known_i = known_l;
-            Rb.known_i = known_r;
-            L.known_f = kl_f;
-            Rb.known_f = kr_f;
-            emit_child(a, L);
-            emit_child(a, Rb);
+            L.H = qs + 1;
+            L.W = row + 1;
+            Rb.i0 = b.i0 + qs;
+            Rb.j0 = b.j0 + row;
+            Rb.H = b.H - qs;
+            Rb.W = b.W - row;
         }
+        L.known_i = known_l;
+        Rb.known_i = known_r;
+        L.known_f = kl_f;
+        Rb.known_f = kr_f;
+        emit_child(a, L);
+        emit_child(a, Rb);
     }
 }
 
+// Work items of a level: every column chunk of every box's split rows (one
+// item for a tagged box).  Each item writes its partial minima; the item that
+// finishes a box last (per-box counter) merges them and emits the children.
 template <int KIND, int DIM>
 __global__ void __launch_bounds__(256) split_kernel(SplitArgs a) {
+    using V = typename std::conditional<KIND == KIND_ABS, long long, double>::type;
+    __shared__ RowMin<V> rm[kSplitRowsMax];
+    __shared__ int s_last;
     // after a planning or sweep error the sweep outputs are not valid
     if (ld_relaxed(&a.ctl->err) != ERR_NONE) return;
-    for (int bi = blockIdx.x; bi < a.n_boxes; bi += gridDim.x) {
-        split_box<KIND, DIM>(a, bi);
+    RowMin<V>* partials = static_cast<RowMin<V>*>(a.partials);
+    for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+        // the box of item it: the last box whose first item is <= it
+        int lo = 0, hi = a.n_boxes - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.sweeps[2 * mid].item0 <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const int bi = lo;
+        const Box b = a.boxes[bi];
+        const PairDesc pd = a.pairs[b.pair];
+        const Geom g = geom_of(b);
+        const Sweep& fw = a.sweeps[2 * bi];
+        const Sweep& bw = a.sweeps[2 * bi + 1];
+        if (b.flags & BOX_TAG) {
+            if (threadIdx.x == 0) finish_box<KIND, DIM, V>(a, b, pd, g, fw, bw, bi, rm);
+            __syncthreads();
+            continue;
+        }
+        const int chunk = it - fw.item0, nitems = fw.nitems;
+        const int q0 = chunk * kSplitChunk, q1 = min(q0 + kSplitChunk, g.Q);
+        chunk_minima<KIND, DIM, V>(a, b, pd, g, fw, bw, q0, q1, rm);
+        const int nr = fw.nout;
+        if (threadIdx.x == 0) {
+            if (nitems == 1) {
+                s_last = 1;
+            } else {
+                for (int m = 0; m < nr; ++m) partials[(size_t)it * kSplitRowsMax + m] = rm[m];
+                __threadfence();
+                s_last = atomicAdd(&a.box_done[bi], 1) == nitems - 1;
+            }
+        }
+        __syncthreads();
+        if (s_last && threadIdx.x == 0) {
+            if (nitems > 1) {
+                __threadfence();
+                for (int m = 0; m < nr; ++m) {
+                    RowMin<V> x = partials[(size_t)fw.item0 * kSplitRowsMax + m];
+                    for (int k = 1; k < nitems; ++k) {
+                        const RowMin<V> y = partials[(size_t)(fw.item0 + k) * kSplitRowsMax + m];
+                        x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
+                    }
+                    rm[m] = x;
+                }
+            }
+            finish_box<KIND, DIM, V>(a, b, pd, g, fw, bw, bi, rm);
+        }
         __syncthreads();
     }
 }
 
 cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
-    if (a.n_boxes <= 0) return cudaSuccess;
-    const int grid = a.n_boxes < 65535 ? a.n_boxes : 65535;
+    if (a.n_boxes <= 0 || a.n_items <= 0) return cudaSuccess;
+    int grid = a.n_items;
+    const int cap = 8 * (a.num_sms > 0 ? a.num_sms : 148);
+    if (grid > cap) grid = cap;
     if (a.kind == KIND_ABS) split_kernel<KIND_ABS, 1><<<grid, 256, 0, st>>>(a);
     else if (a.d == 12) split_kernel<KIND_EUC, 12><<<grid, 256, 0, st>>>(a);
     else split_kernel<KIND_EUC, 0><<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
+
 
 // ---------------------------------------------------------------- base case
 
