@@ -63,7 +63,7 @@ constexpr int URS = 64;                  // slots (column blocks) of a row ring
 #define DTW_SWEEP_KC 8
 #endif
 #ifndef DTW_SWEEP_UNROLL
-#define DTW_SWEEP_UNROLL 2
+#define DTW_SWEEP_UNROLL 4
 #endif
 constexpr int KC = DTW_SWEEP_KC;         // steps per group: rings are synchronised once per group
 constexpr int kGroupUnroll = DTW_SWEEP_UNROLL;
@@ -80,6 +80,21 @@ __device__ __forceinline__ void st_release_cta(int* p, int v) {
 }
 __device__ __forceinline__ void st_words2(unsigned long long* p, unsigned long long a, unsigned long long b) {
     asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+// The same store, executed only where pred holds (a predicated instruction, so
+// that the hot loop carries no divergent branch around it).
+__device__ __forceinline__ void st_words2_if(bool pred, unsigned long long* p, unsigned long long a,
+                                             unsigned long long b) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};\n\t}" ::"l"(p),
+        "l"(a), "l"(b), "r"((int)pred)
+        : "memory");
+}
+__device__ __forceinline__ void st_release_cta_if(bool pred, int* p, int v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.release.cta.shared.b32 [%0], %1;\n\t}" ::"r"(
+                     smem_addr(p)),
+                 "r"(v), "r"((int)pred)
+                 : "memory");
 }
 __device__ __forceinline__ unsigned long long mkword(uint32_t payload, uint32_t epoch) {
     return ((unsigned long long)epoch << 32) | payload;
@@ -355,16 +370,16 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     int uroom = URS;  // this warp may write blocks < uroom into rout
     const int nsteps = nblk + 31;
 
+    const bool w31_ring = to_ring && lane == 31, w31_global = to_global && lane == 31;
     // warp-uniform: release what the previous groups read and wrote, wait for
     // the blocks this group reads, and for room for the blocks it writes
     auto sync_group = [&](int s0) {
         if (s0 > 0) {
             __syncwarp();
-            if (lane == 0) {
-                if (has_above) st_release_cta(&sm.ucons[g], min(s0 + 1, nblk));
-                if (YW > 0 && s0 > 31) st_release_cta(&sm.ycons[g], min(s0 - 30, nblk));
-            }
-            if (to_ring && lane == 31 && s0 > 31) st_release_cta(&sm.uprog[g + 1], min(s0 - 31, nblk));
+            st_release_cta_if(lane == 0 && has_above, &sm.ucons[g], min(s0 + 1, nblk));
+            if constexpr (YW > 0) st_release_cta_if(lane == 0 && s0 > 31, &sm.ycons[g], min(s0 - 30, nblk));
+            st_release_cta_if(w31_ring && s0 > 31, &sm.uprog[g + 1 < kG ? g + 1 : g],
+                              min(s0 - 31, nblk));
         }
         if (s0 < nblk) {  // lane 0 reads blocks up to s0 + KC (the last one ahead of time)
             const int need = min(s0 + KC + 1, nblk);
@@ -378,7 +393,6 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         }
     };
 
-    const bool w31_ring = to_ring && lane == 31, w31_global = to_global && lane == 31;
     auto step = [&](int s, auto checked) {
         constexpr bool CHECK = decltype(checked)::value;
         uint32_t cw[BW];
@@ -462,12 +476,10 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
 #pragma unroll
             for (int u = 0; u < U; ++u) pack<KIND, NW>(bot[u], bott[u], w + u * NW);
             if (w31_ring) st_shared_words<BW>(rout + (ob & (URS - 1)) * SLOT, w);
-            if (w31_global) {
-                unsigned long long* dst = buf + (size_t)ob * BW;
+            unsigned long long* dst = buf + (size_t)ob * BW;
 #pragma unroll
-                for (int i = 0; i < BW / 2; ++i)
-                    st_words2(dst + 2 * i, mkword(w[2 * i], ep_out), mkword(w[2 * i + 1], ep_out));
-            }
+            for (int i = 0; i < BW / 2; ++i)
+                st_words2_if(w31_global, dst + 2 * i, mkword(w[2 * i], ep_out), mkword(w[2 * i + 1], ep_out));
         }
     };
 
