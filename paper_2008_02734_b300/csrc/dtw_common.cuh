@@ -164,7 +164,16 @@ template <> struct AccOf<KIND_EUC> {
 };
 
 __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return __vimin3_s32(a, b, c); }
-__device__ __forceinline__ double min3(double a, double b, double c) { return fmin(fmin(a, b), c); }
+// Accumulated costs are sums of nonnegative frame costs (or +infinity), and for
+// nonnegative doubles the IEEE-754 bit pattern, read as a signed 64-bit integer,
+// orders exactly like the value.  The minimum is therefore taken with integer
+// compares and selects, which run on the full-rate integer pipe, instead of
+// FP64 minimum instructions, which share the narrow FP64 pipe with the additions.
+__device__ __forceinline__ double min3(double a, double b, double c) {
+    const long long x = __double_as_longlong(a), y = __double_as_longlong(b), z = __double_as_longlong(c);
+    const long long m = x < y ? x : y;
+    return __longlong_as_double(m < z ? m : z);
+}
 
 // ---------------------------------------------------------------- frame features
 
@@ -233,15 +242,41 @@ __device__ __forceinline__ int32_t frame_cost(const Frame<KIND_ABS, 1>& a, const
     return abs(a.v - b.v);
 }
 
+// Exact FP32 -> FP64 widening of a frame cost with integer operations (the
+// conversion instruction would occupy the narrow FP64 pipe).  A Euclidean frame
+// cost is +0, a positive normal FP32 value (the square root of even the smallest
+// subnormal sum is normal) or +infinity: shifting the bit pattern into the
+// double's fields and rebasing the exponent (bias 127 -> 1023) is exact.
+__device__ __forceinline__ double widen_cost(float c) {
+    const unsigned u = __float_as_uint(c);
+    const unsigned long long b = ((unsigned long long)u << 29) + (896ULL << 52);
+    const long long r = u == 0u ? 0LL : (u >= 0x7f800000u ? 0x7ff0000000000000LL : (long long)b);
+    return __longlong_as_double(r);
+}
+
+// Fixed even dimension: packed FP32x2 arithmetic (one instruction per two
+// dimensions for the difference and one for the square-accumulate), two partial
+// sums over the even and the odd coordinates, added at the end.
 template <int DIM>
 __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, DIM>& a, const Frame<KIND_EUC, DIM>& b) {
-    float s = 0.f;
+    if constexpr (DIM % 2 == 0) {
+        float2 s = make_float2(0.f, 0.f);
+        const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-    for (int e = 0; e < DIM; ++e) {
-        float t = a.v[e] - b.v[e];
-        s = fmaf(t, t, s);
+        for (int e = 0; e < DIM; e += 2) {
+            const float2 t = __ffma2_rn(make_float2(b.v[e], b.v[e + 1]), m1, make_float2(a.v[e], a.v[e + 1]));
+            s = __ffma2_rn(t, t, s);
+        }
+        return widen_cost(__fsqrt_rn(s.x + s.y));
+    } else {
+        float s = 0.f;
+#pragma unroll
+        for (int e = 0; e < DIM; ++e) {
+            float t = a.v[e] - b.v[e];
+            s = fmaf(t, t, s);
+        }
+        return widen_cost(__fsqrt_rn(s));
     }
-    return (double)__fsqrt_rn(s);
 }
 
 __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, 0>& a, const Frame<KIND_EUC, 0>& b) {
@@ -250,7 +285,7 @@ __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, 0>& a, const 
         float t = __ldg(a.p + e) - __ldg(b.p + e);
         s = fmaf(t, t, s);
     }
-    return (double)__fsqrt_rn(s);
+    return widen_cost(__fsqrt_rn(s));
 }
 
 // Cost of global cell (i, j) of a pair, for the split and checks.

@@ -51,6 +51,13 @@
 #ifndef DTW_INT_U
 #define DTW_INT_U 4
 #endif
+// Lane block of the Euclidean d=12 sweep.
+#ifndef DTW_EUC_R
+#define DTW_EUC_R 2
+#endif
+#ifndef DTW_EUC_U
+#define DTW_EUC_U 2
+#endif
 
 namespace dtwb {
 
@@ -65,8 +72,15 @@ constexpr int URS = 64;                  // slots (column blocks) of a row ring
 #ifndef DTW_SWEEP_UNROLL
 #define DTW_SWEEP_UNROLL 4
 #endif
+#ifndef DTW_SWEEP_UNROLL_EUC
+#define DTW_SWEEP_UNROLL_EUC 1
+#endif
+#ifndef DTW_EUC_YPREFETCH
+#define DTW_EUC_YPREFETCH 0
+#endif
 constexpr int KC = DTW_SWEEP_KC;         // steps per group: rings are synchronised once per group
-constexpr int kGroupUnroll = DTW_SWEEP_UNROLL;
+constexpr int kGroupUnroll = DTW_SWEEP_UNROLL;        // integer kind
+constexpr int kGroupUnrollEuc = DTW_SWEEP_UNROLL_EUC;  // Euclidean kind (longer steps, larger code)
 constexpr int CHB = 32;                  // column blocks per loader round of a frame stream
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -342,10 +356,22 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     // above; every lane reads the same slot) and the frames of block s - lane
     uint32_t nwd[BW];
     Frame<KIND, DIM> ny[U];
+    // frames of the lane's block: loaded one step ahead (YPF), or at the step
+    // itself for large frames (fewer registers, more resident warps)
+    constexpr bool YPF = KIND == KIND_ABS || DTW_EUC_YPREFETCH != 0 || YW == 0;
+    auto load_frames = [&](int cb, Frame<KIND, DIM>* dst) {
+        if constexpr (YW > 0) {
+            const uint32_t* ys = yr + (cb & (YRS - 1)) * (U * YW);
+#pragma unroll
+            for (int u = 0; u < U; ++u) dst[u].load_shared(ys + u * YW);
+        }
+    };
     auto fetch = [&](int s) {
         ld_shared_words<BW>(rin + (s & (URS - 1)) * SLOT, nwd);
         const int cb = s - lane;
-        if constexpr (KIND == KIND_ABS && U % 4 == 0) {
+        if constexpr (!YPF) {
+            // frames are loaded by the step itself
+        } else if constexpr (KIND == KIND_ABS && U % 4 == 0) {
             uint32_t w[U];
             ld_shared_words<U>(yr + (cb & (YRS - 1)) * U, w);
 #pragma unroll
@@ -399,10 +425,14 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
 #pragma unroll
         for (int i = 0; i < BW; ++i) cw[i] = nwd[i];
         Frame<KIND, DIM> yc[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) yc[u] = ny[u];
-        fetch(s + 1);
         const int cb = s - lane;
+        if constexpr (YPF) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) yc[u] = ny[u];
+        } else {
+            load_frames(cb, yc);
+        }
+        fetch(s + 1);
         // the row above: lane 0 from the ring, the other lanes by shuffle
         Acc upv[U];
         int upt[U];
@@ -488,8 +518,13 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     for (int s0 = 0; s0 < nsteps; s0 += KC) {
         if (s0 > 0) sync_group(s0);
         if (s0 >= 31 && s0 + KC < nblk) {
+            if constexpr (KIND == KIND_ABS) {
 #pragma unroll kGroupUnroll
-            for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{});
+                for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{});
+            } else {
+#pragma unroll kGroupUnrollEuc
+                for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{});
+            }
         } else {
 #pragma unroll
             for (int i = 0; i < KC; ++i)
@@ -807,8 +842,9 @@ static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blo
 // anti-diagonals give the scheduler independent cells, and the per-step
 // hand-off work (shuffles, ring, boundary stores) is paid once per block.
 constexpr int kIntR = DTW_INT_R, kIntU = DTW_INT_U;
-int sweep_block_cols(int kind, int d) { return kind == KIND_ABS ? kIntU : 2; }
-int sweep_band_rows(int kind, int d) { return kind == KIND_ABS ? 32 * kIntR : 64; }
+constexpr int kEucR = DTW_EUC_R, kEucU = DTW_EUC_U;
+int sweep_block_cols(int kind, int d) { return kind == KIND_ABS ? kIntU : (d == 12 ? kEucU : 2); }
+int sweep_band_rows(int kind, int d) { return kind == KIND_ABS ? 32 * kIntR : (d == 12 ? 32 * kEucR : 64); }
 int sweep_group_bands() { return kG; }
 
 cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, long long max_blocks,
@@ -817,7 +853,7 @@ cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num
         if (tags) return launch_one<KIND_ABS, kIntR, kIntU, 1, true>(A, num_sms, max_blocks, st);
         return launch_one<KIND_ABS, kIntR, kIntU, 1, false>(A, num_sms, max_blocks, st);
     }
-    if (d == 12) return launch_one<KIND_EUC, 2, 2, 12, false>(A, num_sms, max_blocks, st);
+    if (d == 12) return launch_one<KIND_EUC, kEucR, kEucU, 12, false>(A, num_sms, max_blocks, st);
     return launch_one<KIND_EUC, 2, 2, 0, false>(A, num_sms, max_blocks, st);
 }
 
