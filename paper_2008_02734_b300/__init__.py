@@ -260,10 +260,23 @@ def submit(X, Y, path_out=None):
 
 
 def poll(ticket: int):
-    """(status, K, D*) of a submitted request."""
+    """(status, K, D*) of a submitted request; status PENDING while it runs."""
     K, c = ctypes.c_int64(), ctypes.c_double()
     rc = _get_lib().dtw_poll(int(ticket), ctypes.byref(K), ctypes.byref(c))
     return rc, K.value, c.value
+
+
+def wait(ticket: int, timeout_s: float = 120.0, interval_s: float = 2e-4):
+    """Polls until the request is no longer pending; returns (status, K, D*)."""
+    import time
+    t_end = time.monotonic() + timeout_s
+    while True:
+        rc, K, c = poll(ticket)
+        if rc != PENDING:
+            return rc, K, c
+        if time.monotonic() > t_end:
+            raise TimeoutError(f"request {ticket} still pending after {timeout_s} s")
+        time.sleep(interval_s)
 
 
 def footprint(M: int, N: int, d: int = 1, kind: int = ABS_I32) -> int:

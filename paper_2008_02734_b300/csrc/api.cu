@@ -12,6 +12,7 @@
 #include "dtw_b300.h"
 #include "dtw_common.cuh"
 #include "dtw_kernels.h"
+#include "workspace.h"
 
 using namespace dtwb;
 
@@ -33,14 +34,6 @@ struct Ctx {
     int num_sms = 0;
     int device = -1;
     dtw_stats stats = {};
-    // asynchronous interface
-    long long next_ticket = 0;
-    struct Done {
-        int status;
-        int64_t K;
-        double cost;
-    };
-    std::unordered_map<long long, Done> done;
 };
 
 Ctx& ctx() {
@@ -99,55 +92,6 @@ int workspace(Ctx& c, size_t bytes, void** out) {
     }
     *out = c.ws;
     return DTW_OK;
-}
-
-size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// Byte layout of the workspace for a batch (every size linear in sum(M+N)).
-struct Layout {
-    size_t feat, pairs, pres, boxA, boxB, base, sweeps, sres, bufpool, outpool, boxdone, partials, minmax, jlo, jhi,
-        off, path, ctl, total;
-    long long cap_box, cap_base, cap_sweeps, cap_buf, cap_out, cap_items;
-};
-
-Layout make_layout(int B, long long sumM, long long sumN, long long feat_bytes, long long path_pairs) {
-    Layout L{};
-    const long long S = sumM + sumN;
-    L.cap_box = S / 2 + B + 16;
-    L.cap_base = S + B + 16;
-    L.cap_sweeps = 2 * L.cap_box;
-    // two 64-bit words per column per sweep (columns padded to 8)
-    L.cap_buf = 4 * (S + 2 * L.cap_box) + 2 * L.cap_box * 16;
-    // out rows: per sweep nout <= kSplitRowsMax rows of its columns padded to whole blocks (<= 8 columns)
-    L.cap_out = kSplitRowsMax * (S + 2 * L.cap_box * 8);
-    // split work items: column chunks of every box's split rows
-    L.cap_items = S / kSplitChunk + L.cap_box + 16;
-    size_t o = 0;
-    auto take = [&](size_t bytes) {
-        size_t r = o;
-        o = align_up(o + bytes);
-        return r;
-    };
-    L.feat = take((size_t)feat_bytes);
-    L.pairs = take(sizeof(PairDesc) * B);
-    L.pres = take(sizeof(PairRes) * B);
-    L.boxA = take(sizeof(Box) * L.cap_box);
-    L.boxB = take(sizeof(Box) * L.cap_box);
-    L.base = take(sizeof(Box) * L.cap_base);
-    L.sweeps = take(sizeof(Sweep) * L.cap_sweeps);
-    L.sres = take(sizeof(SweepRes) * L.cap_sweeps);
-    L.bufpool = take(8 * (size_t)L.cap_buf);
-    L.outpool = take(8 * (size_t)L.cap_out);
-    L.boxdone = take(4 * (size_t)L.cap_box);
-    L.partials = take(16 * (size_t)kSplitRowsMax * (size_t)L.cap_items);
-    L.minmax = take(16 * (size_t)B);
-    L.jlo = take(4 * (size_t)sumM);
-    L.jhi = take(4 * (size_t)sumM);
-    L.off = take(4 * (size_t)sumM);
-    L.path = take(8 * (size_t)path_pairs);
-    L.ctl = take(sizeof(LevelCtl));
-    L.total = o;
-    return L;
 }
 
 int map_device_error(int err) {
@@ -339,7 +283,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     int* d_boxdone = reinterpret_cast<int*>(ws + L.boxdone);
     if (!roots.empty()) {
         PlanArgs pa{cur, (int)roots.size(), d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
-                    L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items};
+                    L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false};
         e = launch_plan(pa, st);
         ++launches;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
@@ -370,7 +314,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
             ++launches;
             // plan the next level from the boxes the split appended (count read on the device)
             PlanArgs pa{nxt, -1, d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
-                        L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items};
+                        L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false};
             if (e == cudaSuccess) e = launch_plan(pa, st);
             ++launches;
         }
@@ -393,7 +337,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     if (hc.err == ERR_NONE && want_path) {
         BaseArgs ba{d_base, hc.n_base, d_pairs, d_pres, d_jlo, d_jhi, d_ctl, kind, d};
         e = launch_base(ba, st);
-        AssembleArgs aa{d_pairs, B, (int)maxM, d_pres, d_jlo, d_jhi, d_off, d_ctl};
+        AssembleArgs aa{d_pairs, B, (int)maxM, d_pres, d_jlo, d_jhi, d_off, d_ctl, nullptr};
         if (e == cudaSuccess) e = launch_assemble(aa, st);
         launches += (hc.n_base > 0 ? 1 : 0) + 2;
         std::vector<PairRes> pr(B);
@@ -541,29 +485,6 @@ int dtw_align_batch(int32_t B, const void* const* X, const int64_t* M, const voi
     return run_batch(c, B, X, M, Y, N, d, kind, true, path_out, K_out, cost_out);
 }
 
-int64_t dtw_submit(const dtw_request* r) {
-    if (!r) return DTW_EINVAL;
-    double cost = 0;
-    const int64_t K = dtw_align(r->X, r->M, r->Y, r->N, r->d, r->cost_kind, r->path_out, &cost);
-    Ctx& c = ctx();
-    std::lock_guard<std::mutex> g(c.mu);
-    const long long t = c.next_ticket++;
-    c.done[t] = Ctx::Done{K < 0 ? (int)K : DTW_OK, K < 0 ? 0 : K, cost};
-    return t;
-}
-
-int dtw_poll(int64_t ticket, int64_t* K_out, double* cost_out) {
-    Ctx& c = ctx();
-    std::lock_guard<std::mutex> g(c.mu);
-    auto it = c.done.find(ticket);
-    if (it == c.done.end()) return DTW_EINVAL;
-    const Ctx::Done dn = it->second;
-    c.done.erase(it);
-    if (K_out) *K_out = dn.K;
-    if (cost_out) *cost_out = dn.cost;
-    return dn.status;
-}
-
 int dtw_set_stream(void* cuda_stream) {
     Ctx& c = ctx();
     std::lock_guard<std::mutex> g(c.mu);
@@ -575,6 +496,7 @@ int dtw_set_budget(uint64_t bytes) {
     Ctx& c = ctx();
     std::lock_guard<std::mutex> g(c.mu);
     c.budget = bytes;
+    serve_set_budget(bytes);
     return DTW_OK;
 }
 

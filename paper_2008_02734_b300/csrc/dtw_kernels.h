@@ -45,6 +45,7 @@ struct PlanArgs {
     long long cap_sweeps, cap_buf, cap_out;
     int* box_done;  // per-box split completion counters (reset here; MODE_ALIGN)
     long long cap_items;
+    bool reset_base;  // also empty the base list (its boxes have been finished)
 };
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st);
 
@@ -65,14 +66,14 @@ struct SplitArgs {
     int cap_next, cap_base;
     int* box_done;    // per-box count of finished work items
     void* partials;   // per work item: kSplitRowsMax partial row minima (16 B each)
-    int n_items;      // work items of the level (as planned)
+    int n_items;      // work items of the level (as planned); < 0: read ctl->n_items on the device
     int num_sms;
 };
 cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
 
 struct BaseArgs {
     const Box* base;
-    int n_base;
+    int n_base;  // < 0: read ctl->n_base on the device
     const PairDesc* pairs;
     PairRes* pres;
     int32_t* jlo;
@@ -93,12 +94,23 @@ struct AssembleArgs {
     int32_t* jhi;
     int32_t* off;
     LevelCtl* ctl;
+    const int* idx;  // pairs to assemble: idx[0..n_pairs) (null: pairs 0..n_pairs-1)
 };
 cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st);
 cudaError_t launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st);
-// minmax: 4 int32 per pair of scratch (min X, max X, min Y, max Y)
+// minmax: 4 int32 per pair of scratch (min X, max X, min Y, max Y).  pair_err
+// (optional): per-pair flags set to 1 instead of failing the whole call.
 cudaError_t launch_int_range_check(const PairDesc* pairs, int n_pairs, int max_len, int32_t* minmax, LevelCtl* ctl,
-                                   cudaStream_t st);
+                                   cudaStream_t st, int32_t* pair_err = nullptr);
+// Serving support: appends root boxes staged in `roots` (n of them) to the box
+// list `cur` from index cur0 on, or to the base list when their area is at most
+// base_area; and marks flags[pair] = 1 for every box of the current level.
+cudaError_t launch_append_roots(const Box* roots, int n, Box* cur, int cur0, Box* base, int cap_base,
+                                long long base_area, LevelCtl* ctl, cudaStream_t st);
+cudaError_t launch_mark_pairs(const Box* boxes, const LevelCtl* ctl, int32_t* flags, cudaStream_t st);
+
+// Serving engine (serve.cu): device memory its groups may take from now on.
+void serve_set_budget(uint64_t bytes);
 
 // The paper's plain form (plain.cu)
 struct PlainProblem {

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         c->ticket = 0;
         c->n_next = 0;
         c->n_cur = n_boxes;
+        if (a.reset_base) c->n_base = 0;
         c->need_buf = carry[1];
         c->epoch_base = ep_base + (uint32_t)total_bands + 1u;
         if (fits) {
@@ -419,9 +420,11 @@ __global__ void __launch_bounds__(256) split_kernel(SplitArgs a) {
     // after a planning or sweep error the sweep outputs are not valid
     if (ld_relaxed(&a.ctl->err) != ERR_NONE) return;
     RowMin<V>* partials = static_cast<RowMin<V>*>(a.partials);
-    for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    const int n_items = a.n_items >= 0 ? a.n_items : a.ctl->n_items;
+    const int n_boxes = a.n_boxes >= 0 ? a.n_boxes : a.ctl->n_cur;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         // the box of item it: the last box whose first item is <= it
-        int lo = 0, hi = a.n_boxes - 1;
+        int lo = 0, hi = n_boxes - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (a.sweeps[2 * mid].item0 <= it) lo = mid;
@@ -471,10 +474,12 @@ __global__ void __launch_bounds__(256) split_kernel(SplitArgs a) {
 }
 
 cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
-    if (a.n_boxes <= 0 || a.n_items <= 0) return cudaSuccess;
-    int grid = a.n_items;
     const int cap = 8 * (a.num_sms > 0 ? a.num_sms : 148);
-    if (grid > cap) grid = cap;
+    int grid = cap;  // counts read on the device: a full grid
+    if (a.n_items >= 0 && a.n_boxes >= 0) {
+        if (a.n_boxes == 0 || a.n_items == 0) return cudaSuccess;
+        if (a.n_items < grid) grid = a.n_items;
+    }
     if (a.kind == KIND_ABS) split_kernel<KIND_ABS, 1><<<grid, 256, 0, st>>>(a);
     else if (a.d == 12) split_kernel<KIND_EUC, 12><<<grid, 256, 0, st>>>(a);
     else split_kernel<KIND_EUC, 0><<<grid, 256, 0, st>>>(a);
@@ -507,7 +512,8 @@ __global__ void __launch_bounds__(32 * kBaseWarps) base_kernel(BaseArgs a) {
     BaseSmem<KIND>& sm = *reinterpret_cast<BaseSmem<KIND>*>(smem_raw);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const Acc INF = AccOf<KIND>::inf();
-    for (int bi = blockIdx.x * kBaseWarps + w; bi < a.n_base; bi += gridDim.x * kBaseWarps) {
+    const int n_base = a.n_base >= 0 ? a.n_base : a.ctl->n_base;
+    for (int bi = blockIdx.x * kBaseWarps + w; bi < n_base; bi += gridDim.x * kBaseWarps) {
         const Box b = a.base[bi];
         const PairDesc pd = a.pairs[b.pair];
         // frame: rows along the shorter side
@@ -606,14 +612,14 @@ static cudaError_t launch_base_t(const BaseArgs& a, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(base_kernel<KIND, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    int grid = (a.n_base + kBaseWarps - 1) / kBaseWarps;
+    int grid = a.n_base >= 0 ? (a.n_base + kBaseWarps - 1) / kBaseWarps : 1184;
     if (grid > 65535) grid = 65535;
     base_kernel<KIND, DIM><<<grid, 32 * kBaseWarps, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_base(const BaseArgs& a, cudaStream_t st) {
-    if (a.n_base <= 0) return cudaSuccess;
+    if (a.n_base == 0) return cudaSuccess;
     if (a.kind == KIND_ABS) return launch_base_t<KIND_ABS, 1>(a, st);
     if (a.d == 12) return launch_base_t<KIND_EUC, 12>(a, st);
     return launch_base_t<KIND_EUC, 0>(a, st);
@@ -625,7 +631,7 @@ cudaError_t launch_base(const BaseArgs& a, cudaStream_t st) {
 // (the row offsets in the path) and the structural checks of a warping path.
 __global__ void __launch_bounds__(1024) assemble_scan_kernel(AssembleArgs a) {
     __shared__ long long carry;
-    const int pb = blockIdx.x;
+    const int pb = a.idx ? a.idx[blockIdx.x] : blockIdx.x;
     const PairDesc pd = a.pairs[pb];
     const int32_t* jlo = a.jlo + pd.row_off;
     const int32_t* jhi = a.jhi + pd.row_off;
@@ -655,7 +661,7 @@ __global__ void __launch_bounds__(1024) assemble_scan_kernel(AssembleArgs a) {
 }
 
 __global__ void assemble_scatter_kernel(AssembleArgs a) {
-    const int pb = blockIdx.y;
+    const int pb = a.idx ? a.idx[blockIdx.y] : blockIdx.y;
     const PairDesc pd = a.pairs[pb];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= pd.M) return;
@@ -723,12 +729,15 @@ __global__ void int_range_kernel(const PairDesc* pairs, int32_t* minmax) {
     }
 }
 
-__global__ void int_range_finish_kernel(const PairDesc* pairs, int n_pairs, const int32_t* minmax, LevelCtl* ctl) {
+__global__ void int_range_finish_kernel(const PairDesc* pairs, int n_pairs, const int32_t* minmax, LevelCtl* ctl,
+                                        int32_t* pair_err) {
     for (int pb = blockIdx.x * blockDim.x + threadIdx.x; pb < n_pairs; pb += gridDim.x * blockDim.x) {
         const int32_t* r = minmax + 4 * pb;
         const long long c1 = (long long)r[1] - r[2], c2 = (long long)r[3] - r[0];
         const long long cmax = c1 > c2 ? c1 : c2;
-        if (cmax * ((long long)pairs[pb].M + pairs[pb].N - 1) >= (1LL << 29)) set_error(ctl, ERR_OVERFLOW, pb);
+        const bool bad = cmax * ((long long)pairs[pb].M + pairs[pb].N - 1) >= (1LL << 29);
+        if (pair_err) pair_err[pb] = bad ? 1 : 0;
+        else if (bad) set_error(ctl, ERR_OVERFLOW, pb);
     }
 }
 
@@ -738,7 +747,7 @@ __global__ void minmax_init_kernel(int32_t* minmax, int n_pairs) {
 }
 
 cudaError_t launch_int_range_check(const PairDesc* pairs, int n_pairs, int max_len, int32_t* minmax, LevelCtl* ctl,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, int32_t* pair_err) {
     const int g0 = (4 * n_pairs + 255) / 256;
     minmax_init_kernel<<<g0 < 1024 ? g0 : 1024, 256, 0, st>>>(minmax, n_pairs);
     int gx = (max_len + 1023) / 1024;
@@ -746,7 +755,42 @@ cudaError_t launch_int_range_check(const PairDesc* pairs, int n_pairs, int max_l
     dim3 grid(gx < 1 ? 1 : gx, n_pairs);
     int_range_kernel<<<grid, 256, 0, st>>>(pairs, minmax);
     const int g1 = (n_pairs + 255) / 256;
-    int_range_finish_kernel<<<g1 < 1024 ? g1 : 1024, 256, 0, st>>>(pairs, n_pairs, minmax, ctl);
+    int_range_finish_kernel<<<g1 < 1024 ? g1 : 1024, 256, 0, st>>>(pairs, n_pairs, minmax, ctl, pair_err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- serving support
+
+__global__ void append_roots_kernel(const Box* roots, int n, Box* cur, int cur0, Box* base, int cap_base,
+                                    long long base_area, LevelCtl* ctl) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int k = cur0;
+    for (int r = 0; r < n; ++r) {
+        const Box b = roots[r];
+        if ((long long)b.H * b.W <= base_area) {
+            const int j = ctl->n_base++;
+            if (j < cap_base) base[j] = b;
+            else set_error(ctl, ERR_CAPACITY, 3);
+        } else {
+            cur[k++] = b;
+        }
+    }
+}
+
+cudaError_t launch_append_roots(const Box* roots, int n, Box* cur, int cur0, Box* base, int cap_base,
+                                long long base_area, LevelCtl* ctl, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    append_roots_kernel<<<1, 32, 0, st>>>(roots, n, cur, cur0, base, cap_base, base_area, ctl);
+    return cudaGetLastError();
+}
+
+__global__ void mark_pairs_kernel(const Box* boxes, const LevelCtl* ctl, int32_t* flags) {
+    const int n = ctl->n_cur;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) flags[boxes[i].pair] = 1;
+}
+
+cudaError_t launch_mark_pairs(const Box* boxes, const LevelCtl* ctl, int32_t* flags, cudaStream_t st) {
+    mark_pairs_kernel<<<64, 256, 0, st>>>(boxes, ctl, flags);
     return cudaGetLastError();
 }
 

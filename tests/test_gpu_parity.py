@@ -164,7 +164,7 @@ def test_batch_float():
 def test_submit_poll():
     X, Y = synth.int_pair(9, 800, 900)
     t, path, keep = dtw.submit(_cuda(X), _cuda(Y))
-    rc, K, c = dtw.poll(t)
+    rc, K, c = dtw.wait(t)
     assert rc == dtw.OK
     p_ref, c_ref = oracle.dtw(X, Y)
     assert c == c_ref and np.array_equal(path[:K].cpu().numpy(), p_ref)
