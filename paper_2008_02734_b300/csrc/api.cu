@@ -208,9 +208,9 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     }
     if (e != cudaSuccess) return DTW_ECUDA;
     for (int b = 0; b < B; ++b) {
-        if (kind == KIND_EUC && d % 4 == 0 && d == 12 &&
+        if (kind == KIND_EUC && (d == 12 || d == 64) &&
             ((reinterpret_cast<uintptr_t>(pd[b].X) | reinterpret_cast<uintptr_t>(pd[b].Y)) & 15))
-            return DTW_EINVAL;  // the d=12 kernels load frames as float4
+            return DTW_EINVAL;  // the d=12 and d=64 kernels load frames in 16-byte pieces
     }
 
     PairDesc* d_pairs = reinterpret_cast<PairDesc*>(ws + L.pairs);

@@ -257,9 +257,30 @@ __device__ __forceinline__ double widen_cost(float c) {
 // Fixed even dimension: packed FP32x2 arithmetic (one instruction per two
 // dimensions for the difference and one for the square-accumulate), two partial
 // sums over the even and the odd coordinates, added at the end.
+// Dimensions that are multiples of 8: four packed partial sums (coordinates
+// e, e+1 go to sum (e/2) mod 4), so the accumulation chain is a quarter as long;
+// the sums are combined as ((s0 + s1) + (s2 + s3)) and then x + y.  Every kernel
+// evaluates a cost in exactly this order.
+template <int DIM>
+__device__ __forceinline__ float sumsq8(const float* a, const float* b) {
+    float2 s[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s[i] = make_float2(0.f, 0.f);
+    const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int e = 0; e < DIM; e += 2) {
+        const float2 t = __ffma2_rn(make_float2(b[e], b[e + 1]), m1, make_float2(a[e], a[e + 1]));
+        s[(e / 2) & 3] = __ffma2_rn(t, t, s[(e / 2) & 3]);
+    }
+    const float2 r = __fadd2_rn(__fadd2_rn(s[0], s[1]), __fadd2_rn(s[2], s[3]));
+    return r.x + r.y;
+}
+
 template <int DIM>
 __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, DIM>& a, const Frame<KIND_EUC, DIM>& b) {
-    if constexpr (DIM % 2 == 0) {
+    if constexpr (DIM % 8 == 0) {
+        return widen_cost(__fsqrt_rn(sumsq8<DIM>(a.v, b.v)));
+    } else if constexpr (DIM % 2 == 0) {
         float2 s = make_float2(0.f, 0.f);
         const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
@@ -286,6 +307,28 @@ __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, 0>& a, const 
         s = fmaf(t, t, s);
     }
     return widen_cost(__fsqrt_rn(s));
+}
+
+// A column frame read in place (shared memory), for large fixed dimensions whose
+// frames do not fit in registers next to the row frames.
+template <int DIM>
+struct FrameRef {
+    const float* p;
+};
+
+template <int DIM>
+__device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, DIM>& a, const FrameRef<DIM>& b) {
+    static_assert(DIM % 8 == 0, "in-place frames use the eight-coordinate order");
+    float y[DIM];
+#pragma unroll
+    for (int e = 0; e < DIM; e += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(b.p + e);
+        y[e] = t.x;
+        y[e + 1] = t.y;
+        y[e + 2] = t.z;
+        y[e + 3] = t.w;
+    }
+    return widen_cost(__fsqrt_rn(sumsq8<DIM>(a.v, y)));
 }
 
 // Cost of global cell (i, j) of a pair, for the split and checks.

@@ -482,6 +482,7 @@ cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
     }
     if (a.kind == KIND_ABS) split_kernel<KIND_ABS, 1><<<grid, 256, 0, st>>>(a);
     else if (a.d == 12) split_kernel<KIND_EUC, 12><<<grid, 256, 0, st>>>(a);
+    else if (a.d == 64) split_kernel<KIND_EUC, 64><<<grid, 256, 0, st>>>(a);
     else split_kernel<KIND_EUC, 0><<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -622,6 +623,7 @@ cudaError_t launch_base(const BaseArgs& a, cudaStream_t st) {
     if (a.n_base == 0) return cudaSuccess;
     if (a.kind == KIND_ABS) return launch_base_t<KIND_ABS, 1>(a, st);
     if (a.d == 12) return launch_base_t<KIND_EUC, 12>(a, st);
+    if (a.d == 64) return launch_base_t<KIND_EUC, 64>(a, st);
     return launch_base_t<KIND_EUC, 0>(a, st);
 }
 

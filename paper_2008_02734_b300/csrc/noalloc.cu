@@ -113,7 +113,7 @@ extern "C" int dtw_cost_noalloc(const void* X, int64_t M, const void* Y, int64_t
     if (lo > kShortMax || hi > kLongMax) return DTW_ENOMEM;  // larger than the fixed scratch
     if (!on_device(X) || !on_device(Y)) return DTW_EINVAL;   // no staging: inputs must be on the device
     const int kind = cost_kind == DTW_ABS_I32 ? KIND_ABS : KIND_EUC;
-    if (kind == KIND_EUC && d == 12 && ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15))
+    if (kind == KIND_EUC && (d == 12 || d == 64) && ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15))
         return DTW_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return DTW_ECUDA;

@@ -491,7 +491,7 @@ int64_t dtw_submit(const dtw_request* r) {
     if (k == DTW_ABS_I32 && r->d != 1) return DTW_EINVAL;
     if (r->M > (1LL << 30) || r->N > (1LL << 30)) return DTW_EINVAL;
     const int kind = k == DTW_ABS_I32 ? KIND_ABS : KIND_EUC;
-    if (kind == KIND_EUC && r->d == 12 &&
+    if (kind == KIND_EUC && (r->d == 12 || r->d == 64) &&
         ((reinterpret_cast<uintptr_t>(r->X) | reinterpret_cast<uintptr_t>(r->Y)) & 15))
         return DTW_EINVAL;  // the d=12 kernels load frames in 16-byte pieces
     Server& s = server();

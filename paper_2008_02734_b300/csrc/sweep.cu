@@ -81,7 +81,6 @@ constexpr int URS = 64;                  // slots (column blocks) of a row ring
 constexpr int KC = DTW_SWEEP_KC;         // steps per group: rings are synchronised once per group
 constexpr int kGroupUnroll = DTW_SWEEP_UNROLL;        // integer kind
 constexpr int kGroupUnrollEuc = DTW_SWEEP_UNROLL_EUC;  // Euclidean kind (longer steps, larger code)
-constexpr int CHB = 32;                  // column blocks per loader round of a frame stream
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ int ld_acquire_cta(const int* p) {
@@ -248,18 +247,50 @@ struct FrameWords {
 // reader (cons).
 //
 // Warps of a block that belong to the same sweep read one frame stream: the
-// ring of the first of them (ystream[g]).  The ring must span the lag between
-// the stream's first and last reader (a few dozen steps per warp) plus the
-// loader's lead, hence YRS slots.
+// ring of the first of them (ystream[g]).  The frame region of kYSlots column
+// blocks is split among the block's streams when the block takes a ticket.  A
+// stream read by w warps gets yslots(w) slots: a reader lags the warp above it
+// by at most 40 steps when it waits on it, so the stream's first reader is at
+// most 40(w-1) blocks ahead of its last one, which keeps 31 blocks (its lanes)
+// plus a group in use; the loader's next round (chunk(w) blocks) must fit
+// beside all that, otherwise the first reader could wait on the loader, the
+// loader on the last reader and the last reader, through the chain of row
+// rings, on the first one.  w = 4 or 3: 256 slots, rounds of 32; w = 2: 128, 32;
+// w = 1: 64, 16.  Every partition of four warps fits in 320 slots.
+constexpr int kYSlots = 320;
+__host__ __device__ constexpr int yslots(int w) { return w >= 3 ? 256 : (w == 2 ? 128 : 64); }
+__host__ __device__ constexpr int ychunk(int w) { return w >= 2 ? 32 : 16; }
+
+// A frame ring slot holds the U column frames of one block; lanes read the
+// slots of consecutive blocks, so the slot stride is padded to an odd number of
+// 16-byte units: the eight lanes of a 16-byte shared load then fall in eight
+// different bank groups.
+template <int U, int YW>
+struct FrameSlot {
+    static constexpr int W = (U * YW) % 4 != 0 || ((U * YW) / 4) % 2 == 1 ? U * YW : U * YW + 4;
+};
+
 template <int U, int NWMAX, int YW>
 struct StripSmem {
-    static constexpr int YRS = 256;  // frame ring slots (column blocks)
+    static constexpr int YSW = FrameSlot<U, YW>::W;  // words per frame ring slot
     __align__(16) uint32_t uring[kG][URS * U * NWMAX];
-    __align__(16) uint32_t yring[kG][YW > 0 ? YRS * U * YW : 4];
+    __align__(16) uint32_t yring[YW > 0 ? kYSlots * YSW : 4];
     int uprog[kG], ucons[kG], yprog[kG], ycons[kG];
+    int ybase[kG], yrs[kG], ychb[kG];  // per stream: first slot, slots, blocks per loader round
     int sweep_of[kG], band_of[kG], ystream[kG];
     long long ticket;
     int stop;
+};
+
+// Column frame held by a lane: in registers, or (large fixed dimensions) a
+// pointer into the frame ring.
+template <int KIND, int DIM>
+struct ColFrame {
+    using T = Frame<KIND, DIM>;
+};
+template <>
+struct ColFrame<KIND_EUC, 64> {
+    using T = FrameRef<64>;
 };
 
 // One band.  TAGM: 0 untagged rows, 1 every row of the band tagged, 2 the band
@@ -283,7 +314,6 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     using Acc = typename AccOf<KIND>::T;
     using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>;
     constexpr int YW = FrameWords<KIND, DIM>::v;
-    constexpr int YRS = SM::YRS;
     constexpr bool TAG = TAGM != 0;
     constexpr int SLOT = U * NWMAX;  // row ring slot stride (words)
     constexpr int BW = U * NW;       // payload words per block
@@ -314,7 +344,9 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     uint32_t* rin = sm.uring[g];
     uint32_t* rout = sm.uring[g + 1 < kG ? g + 1 : g];
     const int ys = sm.ystream[g];
-    const uint32_t* yr = sm.yring[ys];
+    constexpr int YSW = SM::YSW;
+    const uint32_t* yr = sm.yring + (size_t)sm.ybase[ys] * YSW;
+    const int ymask = sm.yrs[ys] - 1;
     if (!has_above) {
         // the row above the sweep: D(-1, q) = infinity (Eq. "dtwboundary")
         uint32_t w[NW];
@@ -354,16 +386,20 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
 
     // inputs of the next step: the row ring slot of block s (lane 0's row
     // above; every lane reads the same slot) and the frames of block s - lane
+    using YF = typename ColFrame<KIND, DIM>::T;
     uint32_t nwd[BW];
-    Frame<KIND, DIM> ny[U];
+    YF ny[U];
     // frames of the lane's block: loaded one step ahead (YPF), or at the step
     // itself for large frames (fewer registers, more resident warps)
     constexpr bool YPF = KIND == KIND_ABS || DTW_EUC_YPREFETCH != 0 || YW == 0;
-    auto load_frames = [&](int cb, Frame<KIND, DIM>* dst) {
+    auto load_frames = [&](int cb, YF* dst) {
         if constexpr (YW > 0) {
-            const uint32_t* ys = yr + (cb & (YRS - 1)) * (U * YW);
+            const uint32_t* ys = yr + (cb & ymask) * YSW;
 #pragma unroll
-            for (int u = 0; u < U; ++u) dst[u].load_shared(ys + u * YW);
+            for (int u = 0; u < U; ++u) {
+                if constexpr (std::is_same<YF, Frame<KIND, DIM>>::value) dst[u].load_shared(ys + u * YW);
+                else dst[u].p = reinterpret_cast<const float*>(ys + u * YW);
+            }
         }
     };
     auto fetch = [&](int s) {
@@ -373,13 +409,11 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
             // frames are loaded by the step itself
         } else if constexpr (KIND == KIND_ABS && U % 4 == 0) {
             uint32_t w[U];
-            ld_shared_words<U>(yr + (cb & (YRS - 1)) * U, w);
+            ld_shared_words<U>(yr + (cb & ymask) * YSW, w);
 #pragma unroll
             for (int u = 0; u < U; ++u) ny[u].v = (int32_t)w[u];
         } else if constexpr (YW > 0) {
-            const uint32_t* ys = yr + (cb & (YRS - 1)) * (U * YW);
-#pragma unroll
-            for (int u = 0; u < U; ++u) ny[u].load_shared(ys + u * YW);
+            load_frames(cb, ny);
         } else {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -424,7 +458,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         uint32_t cw[BW];
 #pragma unroll
         for (int i = 0; i < BW; ++i) cw[i] = nwd[i];
-        Frame<KIND, DIM> yc[U];
+        YF yc[U];
         const int cb = s - lane;
         if constexpr (YPF) {
 #pragma unroll
@@ -559,7 +593,6 @@ template <int KIND, int U, int DIM, int NWMAX, int NW>
 __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>& sm) {
     using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>;
     constexpr int YW = FrameWords<KIND, DIM>::v;
-    constexpr int YRS = SM::YRS;
     constexpr int SLOT = U * NWMAX;
     constexpr int FB = 4 * YW;  // bytes per frame
     static_assert(32 % U == 0, "a round of 32 boundary columns covers whole blocks");
@@ -591,7 +624,8 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
                 issued[j] = 0;
                 if (ynext[j] < yend[j]) {
                     work_left = true;
-                    const int b1 = min(ynext[j] + CHB, yend[j]);
+                    const int b1 = min(ynext[j] + sm.ychb[j], yend[j]);
+                    const int YRS = sm.yrs[j];
                     // room: the slowest reader of the stream
                     int rc = 1 << 30;
 #pragma unroll
@@ -602,10 +636,10 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
                         const int Q = sp->Q, cstep = sp->cstep;
                         const long long cbase = sp->cbase;
                         const char* cols = static_cast<const char*>(sp->colseq);
-                        uint32_t* yr = sm.yring[j];
+                        uint32_t* yr = sm.yring + (size_t)sm.ybase[j] * SM::YSW;
                         for (int c = ynext[j] * U + lane; c < b1 * U; c += 32) {
                             const char* src = cols + (cbase + (long long)cstep * min(c, Q - 1)) * FB;
-                            uint32_t* dst = yr + (c % (YRS * U)) * YW;
+                            uint32_t* dst = yr + ((c / U) % YRS) * SM::YSW + (c % U) * YW;
                             if constexpr (FB == 4) {
                                 cp_async4(dst, src);
                             } else {
@@ -755,8 +789,19 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
         __syncthreads();
         if (threadIdx.x == 0) {
             // frame streams: warps of one sweep share the first one's ring
-            for (int g = 0; g < kG; ++g)
+            int readers[kG] = {};
+            for (int g = 0; g < kG; ++g) {
                 sm.ystream[g] = (g > 0 && sweep_of[g] >= 0 && sweep_of[g] == sweep_of[g - 1]) ? sm.ystream[g - 1] : g;
+                if (sweep_of[g] >= 0) ++readers[sm.ystream[g]];
+            }
+            int base = 0;
+            for (int j = 0; j < kG; ++j) {
+                const int w = readers[j] > 0 ? readers[j] : 1;
+                sm.ybase[j] = base;
+                sm.yrs[j] = yslots(w);
+                sm.ychb[j] = ychunk(w);
+                if (readers[j] > 0) base += yslots(w);
+            }
         }
         __syncthreads();
         if (warp < kG) {
@@ -844,7 +889,9 @@ static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blo
 constexpr int kIntR = DTW_INT_R, kIntU = DTW_INT_U;
 constexpr int kEucR = DTW_EUC_R, kEucU = DTW_EUC_U;
 int sweep_block_cols(int kind, int d) { return kind == KIND_ABS ? kIntU : (d == 12 ? kEucU : 2); }
-int sweep_band_rows(int kind, int d) { return kind == KIND_ABS ? 32 * kIntR : (d == 12 ? 32 * kEucR : 64); }
+int sweep_band_rows(int kind, int d) {
+    return kind == KIND_ABS ? 32 * kIntR : (d == 12 ? 32 * kEucR : (d == 64 ? 32 : 64));
+}
 int sweep_group_bands() { return kG; }
 
 cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, long long max_blocks,
@@ -854,6 +901,8 @@ cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num
         return launch_one<KIND_ABS, kIntR, kIntU, 1, false>(A, num_sms, max_blocks, st);
     }
     if (d == 12) return launch_one<KIND_EUC, kEucR, kEucU, 12, false>(A, num_sms, max_blocks, st);
+    // d = 64: one row per lane (its frame in registers), column frames read in place
+    if (d == 64) return launch_one<KIND_EUC, 1, 2, 64, false>(A, num_sms, max_blocks, st);
     return launch_one<KIND_EUC, 2, 2, 0, false>(A, num_sms, max_blocks, st);
 }
 

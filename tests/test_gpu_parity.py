@@ -97,12 +97,15 @@ def test_int_degenerate_thin(M, N):
 
 
 @pytest.mark.parametrize("M,N,d", [(1, 1, 12), (5, 3, 12), (64, 80, 12), (300, 257, 12), (1000, 1300, 12),
-                                   (70, 90, 3), (257, 129, 5), (33, 2000, 12)])
+                                   (70, 90, 3), (257, 129, 5), (33, 2000, 12), (1, 5, 64), (200, 300, 64),
+                                   (700, 650, 64), (33, 2000, 64)])
 @pytest.mark.parametrize("base_area", [4, 16384])
 def test_float_small(M, N, d, base_area):
     dtw.set_option(dtw.OPT_BASE_AREA, base_area)
     if d == 12:
         X, Y = synth.chroma_pair(M + N, M, N)
+    elif d == 64:
+        X, Y = synth.mfcc_pair(M + N, M, N)
     else:
         rng = np.random.default_rng(M * N)
         X = rng.standard_normal((M, d)).astype(np.float32)
