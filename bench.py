@@ -323,19 +323,178 @@ def run_ours(args):
     return 0
 
 
+def _percentiles(ms):
+    return {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))}
+
+
+def run_batch_workload(args):
+    """The uneven batch: 256 chroma-like d=12 pairs, M log-uniform in [1000, 20000],
+    N = clip(r M), r log-uniform in [0.8, 1.25]; all pairs through dtw_align_batch
+    (every pair's boxes of a level share the launches).  value = sum(M N) / time."""
+    import torch
+
+    import paper_2008_02734_b300 as dtw
+
+    pairs = synth.workload_batch(B=args.batch)
+    cells = float(sum(len(x) * len(y) for x, y in pairs))
+    Xs = [torch.from_numpy(x).cuda() for x, _ in pairs]
+    Ys = [torch.from_numpy(y).cuda() for _, y in pairs]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        dtw.align_batch(Xs, Ys)
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dtw.align_batch(Xs, Ys)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    st = dtw.get_stats()
+    # end to end from host arrays
+    Xh = [x for x, _ in pairs]
+    Yh = [y for _, y in pairs]
+    e2e = []
+    for _ in range(max(1, args.steps // 2)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        dtw.align_batch(Xh, Yh)
+        e2e.append(1e3 * (time.perf_counter() - t))
+    h2d = int(sum(x.nbytes + y.nbytes for x, y in pairs))
+    d2h = int(sum(8 * (len(x) + len(y) - 1) for x, y in pairs))
+    line = {"metric": METRIC, "value": cells / (np.mean(ms) / 1e3) / 1e9, "unit": "GCUPS", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": float(np.mean(ms)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-cost/f64-dp",
+            "data": "synthetic",
+            "config": {"workload": f"uneven batch: {args.batch} chroma-like d=12 FP32 pairs, M log-uniform "
+                                   "[1000,20000], N = clip(r M), r log-uniform [0.8,1.25]",
+                       "pairs": args.batch, "problem_cells": cells, "l2": "flushed between steps"},
+            "latency_ms": _percentiles(ms),
+            "e2e": {"value": cells / (np.mean(e2e) / 1e3) / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": st["kernel_launches"], "levels": st["levels"],
+            "processed_cells_per_step": st["sweep_cells"] + st["base_cells"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_precision_workload(args):
+    """The orchestral-length pair: 60000 x 64-d MFCC-like frames vs a 75000-frame
+    warp plus noise, exact form (FP32 frame cost, FP64 accumulation)."""
+    import torch
+
+    import paper_2008_02734_b300 as dtw
+
+    X, Y = synth.workload_precision()
+    M, N = len(X), len(Y)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        dtw.align(Xd, Yd)
+    ms = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, cost = dtw.align(Xd, Yd)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    line = {"metric": METRIC, "value": M * N / (np.mean(ms) / 1e3) / 1e9, "unit": "GCUPS", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": float(np.mean(ms)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-cost/f64-dp",
+            "data": "synthetic",
+            "config": {"workload": "orchestral-length pair: 60000 x 64-d MFCC-like vs 75000-frame warp + "
+                                   "N(0,0.1^2), exact form", "M": M, "N": N, "cost": cost},
+            "latency_ms": _percentiles(ms)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving_workload(args):
+    """The serving stream: Poisson arrivals, lengths log-uniform in [500, max_len],
+    d = 12 (FP32 frames) or 64 with equal probability, submitted at their arrival
+    times through dtw_submit and collected with dtw_poll.  Reports throughput over
+    the makespan and per-request latency (submit to result), beside the serial
+    plain FP64 GPU form's throughput measured on one pair of the stream."""
+    import torch
+
+    import paper_2008_02734_b300 as dtw
+
+    dtw.set_budget(int(args.budget_gb * (1 << 30)))
+    reqs = synth.workload_serving(R=args.requests, rate_hz=args.rate, hi=args.max_len)
+    feats = [r.features() for r in reqs]
+    cells = float(sum(r.M * r.N for r in reqs))
+    bufs = [(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()) for x, y in feats]
+    torch.cuda.synchronize()
+    # warm the engines of both groups
+    for k in range(min(4, len(reqs))):
+        t, _, keep = dtw.submit(*bufs[k])
+        dtw.wait(t)
+    pend = {}
+    lat = []
+    t0 = time.perf_counter()
+    nxt = 0
+    while nxt < len(reqs) or pend:
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt].arrival_s <= now:
+            t, path, keep = dtw.submit(*bufs[nxt])
+            pend[t] = (time.perf_counter(), path, keep, nxt)
+            nxt += 1
+        for t in list(pend):
+            rc, K, c = dtw.poll(t)
+            if rc != dtw.PENDING:
+                if rc != dtw.OK:
+                    raise RuntimeError(f"request {pend[t][3]} failed: {rc}")
+                lat.append(1e3 * (time.perf_counter() - pend[t][0]))
+                del pend[t]
+        time.sleep(1e-4)
+    makespan = time.perf_counter() - t0
+    # the serial plain form on a mid-size request of the stream
+    k = int(np.argsort([r.M * r.N for r in reqs])[len(reqs) // 2])
+    torch.cuda.synchronize()
+    tp = time.perf_counter()
+    dtw.align(*bufs[k], plain=True)
+    torch.cuda.synchronize()
+    plain_gcups = reqs[k].M * reqs[k].N / (time.perf_counter() - tp) / 1e9
+    line = {"metric": METRIC, "value": cells / makespan / 1e9, "unit": "GCUPS", "n_gpus": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
+            "config": {"workload": f"serving stream: {args.requests} Poisson arrivals at {args.rate} Hz, lengths "
+                                   f"log-uniform [500,{args.max_len}], d 12 or 64, exact form, admission budget "
+                                   f"{args.budget_gb} GB", "problem_cells": cells},
+            "latency_ms": _percentiles(lat), "makespan_s": makespan,
+            "vs_plain_gpu": {"plain_gcups_one_request": plain_gcups,
+                             "serial_plain_makespan_s_est": cells / plain_gcups / 1e9,
+                             "speedup_est": (cells / makespan) / (plain_gcups * 1e9)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="int_pair")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "precision", "serving"], default="int_pair")
+    ap.add_argument("--batch", type=int, default=256, help="pairs of the batch workload")
+    ap.add_argument("--requests", type=int, default=200, help="requests of the serving workload")
+    ap.add_argument("--rate", type=float, default=100.0, help="arrival rate of the serving workload (Hz)")
+    ap.add_argument("--max-len", type=int, default=20000, help="longest request of the serving workload")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="admission budget of the serving workload")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 GPU comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch_workload(args)
+    if args.workload == "precision":
+        return run_precision_workload(args)
+    if args.workload == "serving":
+        return run_serving_workload(args)
     return run_ours(args)
 
 
