@@ -209,7 +209,11 @@ enum dtw_option {
     DTW_OPT_TIMING = 1,      /* 1: record CUDA events around each launch (default 0) */
     DTW_OPT_BASE_AREA = 2,   /* boxes of at most this many cells finish in the base case */
     DTW_OPT_SPIN_LIMIT = 3,  /* polls before a device-side wait gives up (DTW_ETIMEOUT) */
-    DTW_OPT_SKIP_PUBLISH = 4 /* test hook: one band never publishes (exercises DTW_ETIMEOUT) */
+    DTW_OPT_SKIP_PUBLISH = 4, /* test hook: one band never publishes (exercises DTW_ETIMEOUT) */
+    DTW_OPT_GRAPH = 5         /* 1 (default): the level loop of dtw_align / dtw_align_batch runs as one CUDA
+                                 graph with a device-side loop condition (no host round trip per level);
+                                 0: a host loop that reads the control block back after every level.
+                                 DTW_OPT_TIMING on forces the host loop (it times every level). */
 };
 DTW_API int dtw_set_option(int32_t key, int64_t value);
 

@@ -26,7 +26,7 @@ ABS_I32 = 1
 PLAIN_F64 = 1 << 8
 
 OK, PENDING, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBUSY, EINTERNAL = 0, 1, -1, -2, -3, -4, -5, -6, -7
-OPT_TIMING, OPT_BASE_AREA, OPT_SPIN_LIMIT, OPT_SKIP_PUBLISH = 1, 2, 3, 4
+OPT_TIMING, OPT_BASE_AREA, OPT_SPIN_LIMIT, OPT_SKIP_PUBLISH, OPT_GRAPH = 1, 2, 3, 4, 5
 
 
 class DTWError(RuntimeError):

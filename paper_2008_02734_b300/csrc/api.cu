@@ -34,6 +34,13 @@ struct Ctx {
     int num_sms = 0;
     int device = -1;
     dtw_stats stats = {};
+    int use_graph = 1;
+    // cached executable graph of the level loop and the parameters it was built for
+    struct LevelGraph {
+        cudaGraphExec_t exec = nullptr;
+        cudaStream_t cap = nullptr;  // capture stream (the library stream may be the legacy one)
+        std::vector<long long> key;
+    } lg;
 };
 
 Ctx& ctx() {
@@ -92,6 +99,62 @@ int workspace(Ctx& c, size_t bytes, void** out) {
     }
     *out = c.ws;
     return DTW_OK;
+}
+
+// The level loop of Algorithm 2 as one CUDA graph: a WHILE node whose body is
+// sweep -> split -> plan of the next level (which copies the next boxes into the
+// current list) -> condition kernel.  No host round trip per level.
+int level_graph(Ctx& c, const std::vector<long long>& key, const SweepArgs& sa, const SplitArgs& sp,
+                const PlanArgs& pn, LevelCtl* ctl, int kind, int d, int max_levels, cudaGraphExec_t* out) {
+    auto& lg = c.lg;
+    if (lg.exec && lg.key == key) {
+        *out = lg.exec;
+        return DTW_OK;
+    }
+    if (lg.exec) {
+        cudaGraphExecDestroy(lg.exec);
+        lg.exec = nullptr;
+    }
+    if (!lg.cap && cudaStreamCreateWithFlags(&lg.cap, cudaStreamNonBlocking) != cudaSuccess) return DTW_ECUDA;
+    if (sweep_prepare(kind, d, kind == KIND_ABS) != cudaSuccess) return DTW_ECUDA;
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return DTW_ECUDA;
+    int rc = DTW_OK;
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams np{};
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(lg.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = launch_sweep(kind, d, kind == KIND_ABS, sa, c.num_sms, 0, lg.cap);
+            if (e1 == cudaSuccess) e1 = launch_split(sp, lg.cap);
+            if (e1 == cudaSuccess) e1 = launch_plan(pn, lg.cap);
+            if (e1 == cudaSuccess) e1 = launch_level_cond(ctl, h, max_levels, lg.cap);
+            cudaGraph_t got = nullptr;
+            e = cudaStreamEndCapture(lg.cap, &got);
+            if (e == cudaSuccess) e = e1;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&lg.exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lg.exec = nullptr;
+        rc = DTW_ECUDA;
+    } else {
+        lg.key = key;
+        *out = lg.exec;
+    }
+    cudaGraphDestroy(g);
+    return rc;
 }
 
 int map_device_error(int err) {
@@ -283,7 +346,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     int* d_boxdone = reinterpret_cast<int*>(ws + L.boxdone);
     if (!roots.empty()) {
         PlanArgs pa{cur, (int)roots.size(), d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
-                    L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false};
+                    L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
         e = launch_plan(pa, st);
         ++launches;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
@@ -293,7 +356,26 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     } else {
         hc.n_cur = 0;
     }
-    while (hc.err == ERR_NONE && hc.n_cur > 0) {
+    const bool graph = c.use_graph && !c.timing && mode == MODE_ALIGN && !roots.empty() && hc.err == ERR_NONE;
+    if (graph) {
+        SweepArgs sa{d_sweeps, d_ctl, reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres, d,
+                     c.spin_limit, c.skip_publish};
+        SplitArgs sp{cur,       -1,   d_pairs, d_pres, kind,     d,          halo,    d_sweeps,
+                     d_sres,    ws + L.outpool, nxt, d_base,  d_ctl,      base_area, (int)L.cap_box,
+                     (int)L.cap_base, d_boxdone, ws + L.partials, -1, c.num_sms};
+        PlanArgs pn{nxt, -1, d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
+                    L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, cur};
+        const std::vector<long long> key{(long long)(uintptr_t)ws, (long long)L.total, L.cap_box, L.cap_base,
+                                         L.cap_sweeps, L.cap_buf, L.cap_out, L.cap_items, kind, d, base_area,
+                                         c.spin_limit, c.skip_publish, c.num_sms, max_levels, (long long)L.ctl};
+        cudaGraphExec_t ex = nullptr;
+        int grc = level_graph(c, key, sa, sp, pn, d_ctl, kind, d, max_levels, &ex);
+        if (grc != DTW_OK) return grc;
+        if (cudaGraphLaunch(ex, st) != cudaSuccess) return DTW_ECUDA;
+        hc.n_cur = 0;  // the loop ran on the device; its counters are read after the base case
+        hc.n_base = -1;
+    }
+    while (!graph && hc.err == ERR_NONE && hc.n_cur > 0) {
         if (levels >= max_levels) return DTW_EINTERNAL;
         const int n_cur = hc.n_cur;
         SweepArgs sa{d_sweeps, d_ctl,        reinterpret_cast<unsigned long long*>(ws + L.bufpool),
@@ -314,7 +396,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
             ++launches;
             // plan the next level from the boxes the split appended (count read on the device)
             PlanArgs pa{nxt, -1, d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
-                        L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false};
+                        L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
             if (e == cudaSuccess) e = launch_plan(pa, st);
             ++launches;
         }
@@ -339,7 +421,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         e = launch_base(ba, st);
         AssembleArgs aa{d_pairs, B, (int)maxM, d_pres, d_jlo, d_jhi, d_off, d_ctl, nullptr};
         if (e == cudaSuccess) e = launch_assemble(aa, st);
-        launches += (hc.n_base > 0 ? 1 : 0) + 2;
+        launches += (hc.n_base != 0 ? 1 : 0) + 2;
         std::vector<PairRes> pr(B);
         if (e == cudaSuccess) e = cudaMemcpyAsync(pr.data(), d_pres, sizeof(PairRes) * B, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
@@ -356,6 +438,12 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return DTW_ECUDA;
         }
+    }
+    if (graph) {
+        c.epoch = hc.epoch_base;
+        levels = sweeps = hc.levels;
+        launches += 4 * hc.levels;
+        if (hc.err == ERR_NONE && hc.n_cur > 0) return DTW_EINTERNAL;  // the level bound was reached
     }
     double total_ms = 0;
     if (c.timing) {
@@ -559,6 +647,7 @@ int dtw_set_option(int32_t key, int64_t value) {
             c.spin_limit = (int)value;
             return DTW_OK;
         case DTW_OPT_SKIP_PUBLISH: c.skip_publish = value; return DTW_OK;
+        case DTW_OPT_GRAPH: c.use_graph = value != 0; return DTW_OK;
         default: return DTW_EINVAL;
     }
 }

@@ -116,6 +116,8 @@ struct LevelCtl {
     long long retag;             // boxes sent back for a tagged sweep
     unsigned long long resyncs;  // prefetch-ring refills in the sweeps
     unsigned long long polls;    // failed polls of boundary words
+    int32_t levels;              // levels planned on the device (graph-driven level loop)
+    int32_t pad1;
 };
 
 // ---------------------------------------------------------------- memory order

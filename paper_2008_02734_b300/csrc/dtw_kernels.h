@@ -27,6 +27,8 @@ int sweep_group_bands();                // bands per ticket (compute warps per b
 // max_blocks > 0 caps the grid (one block per ticket suffices); 0: a full persistent grid.
 cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, long long max_blocks,
                          cudaStream_t st);
+// One-time launch setup of the variant (attributes, occupancy); must precede a stream capture.
+cudaError_t sweep_prepare(int kind, int d, bool tags);
 
 // Level planning modes
 constexpr int MODE_ALIGN = 0;  // per box: two half sweeps, or one tagged sweep (BOX_TAG)
@@ -46,6 +48,7 @@ struct PlanArgs {
     int* box_done;  // per-box split completion counters (reset here; MODE_ALIGN)
     long long cap_items;
     bool reset_base;  // also empty the base list (its boxes have been finished)
+    Box* copy_to;     // non-null: the planned boxes are also copied here (same index)
 };
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st);
 
@@ -108,6 +111,9 @@ cudaError_t launch_int_range_check(const PairDesc* pairs, int n_pairs, int max_l
 cudaError_t launch_append_roots(const Box* roots, int n, Box* cur, int cur0, Box* base, int cap_base,
                                 long long base_area, LevelCtl* ctl, cudaStream_t st);
 cudaError_t launch_mark_pairs(const Box* boxes, const LevelCtl* ctl, int32_t* flags, cudaStream_t st);
+// Graph-driven level loop: sets the loop's condition to "another level": boxes
+// planned, no device error and fewer than max_levels levels so far.
+cudaError_t launch_level_cond(LevelCtl* ctl, cudaGraphConditionalHandle h, int max_levels, cudaStream_t st);
 
 // Serving engine (serve.cu): device memory its groups may take from now on.
 void serve_set_budget(uint64_t bytes);

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         if (valid) {
             const int bi = s / nslot, dir = s % nslot;
             const Box b = a.boxes[bi];
+            if (a.copy_to && dir == 0) a.copy_to[bi] = b;
             const PairDesc pd = a.pairs[b.pair];
             const Geom g = geom_of(b);
             sw.box = bi;
@@ -758,6 +759,20 @@ cudaError_t launch_int_range_check(const PairDesc* pairs, int n_pairs, int max_l
     int_range_kernel<<<grid, 256, 0, st>>>(pairs, minmax);
     const int g1 = (n_pairs + 255) / 256;
     int_range_finish_kernel<<<g1 < 1024 ? g1 : 1024, 256, 0, st>>>(pairs, n_pairs, minmax, ctl, pair_err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- graph-driven level loop
+
+__global__ void level_cond_kernel(LevelCtl* ctl, cudaGraphConditionalHandle h, int max_levels) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int lv = ++ctl->levels;
+    const bool more = ctl->n_cur > 0 && ctl->err == ERR_NONE && lv < max_levels;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+cudaError_t launch_level_cond(LevelCtl* ctl, cudaGraphConditionalHandle h, int max_levels, cudaStream_t st) {
+    level_cond_kernel<<<1, 32, 0, st>>>(ctl, h, max_levels);
     return cudaGetLastError();
 }
 

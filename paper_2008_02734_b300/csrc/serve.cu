@@ -357,7 +357,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
     cudaError_t e = cudaSuccess;
     if (n_cur > 0) {
         PlanArgs pa{cur, n_cur, pairs(), MODE_ALIGN, kind, halo, U, BR, G, d_sweeps, ctl(),
-                    L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false};
+                    L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
         e = launch_plan(pa, st);
         SweepArgs sa{d_sweeps, ctl(), reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres,
                      d, spin_limit, -1};
@@ -369,7 +369,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
     BaseArgs ba{d_base, -1, pairs(), pres(), jlo(), jhi(), ctl(), kind, d};
     if (e == cudaSuccess) e = launch_base(ba, st);
     PlanArgs pn{nxt, -1, pairs(), MODE_ALIGN, kind, halo, U, BR, G, d_sweeps, ctl(),
-                L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, true};
+                L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, true, nullptr};
     if (e == cudaSuccess) e = launch_plan(pn, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_flags, 0, 4 * kSlots, st);
     if (e == cudaSuccess) e = launch_mark_pairs(nxt, ctl(), d_flags, st);

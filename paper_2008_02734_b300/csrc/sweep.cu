@@ -759,6 +759,9 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
     const int n_sweeps = A.ctl->n_sweeps;
     const long long n_tickets = A.ctl->n_tickets;
     const long long n_bands = A.ctl->n_bands;
+    // with fewer tickets than blocks only the first n_tickets blocks work: a grid
+    // fixed in advance then still puts a level's few strips on separate SMs
+    if ((long long)blockIdx.x >= n_tickets) return;
     for (;;) {
         if (threadIdx.x == 0) {
             sm.ticket = (long long)atomicAdd(&A.ctl->ticket, 1ULL);
@@ -863,7 +866,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
 // than SMs every block gets an SM of its own, so a level with few bands spreads
 // its warps over the schedulers of the whole GPU.
 template <int KIND, int R, int U, int DIM, bool TAGS>
-static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blocks, cudaStream_t st) {
+static cudaError_t setup_one(int* nb_out) {
     constexpr int NWMAX = (KIND == KIND_EUC || TAGS) ? 2 : 1;
     constexpr size_t smem = sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>);
     static int nb = 0;
@@ -871,9 +874,21 @@ static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blo
         cudaError_t e = cudaFuncSetAttribute(sweep_kernel<KIND, R, U, DIM, TAGS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<KIND, R, U, DIM, TAGS>, kThreads, smem);
-        if (nb < 1) nb = 1;
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<KIND, R, U, DIM, TAGS>, kThreads, smem);
+        nb = n < 1 ? 1 : n;
     }
+    *nb_out = nb;
+    return cudaSuccess;
+}
+
+template <int KIND, int R, int U, int DIM, bool TAGS>
+static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blocks, cudaStream_t st) {
+    constexpr int NWMAX = (KIND == KIND_EUC || TAGS) ? 2 : 1;
+    constexpr size_t smem = sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>);
+    int nb = 0;
+    cudaError_t e = setup_one<KIND, R, U, DIM, TAGS>(&nb);
+    if (e != cudaSuccess) return e;
     long long grid = (long long)num_sms * nb;
     if (max_blocks > 0 && max_blocks < grid) grid = max_blocks;
     if (max_blocks < 0 || grid < 1) grid = 1;
@@ -893,6 +908,17 @@ int sweep_band_rows(int kind, int d) {
     return kind == KIND_ABS ? 32 * kIntR : (d == 12 ? 32 * kEucR : (d == 64 ? 32 : 64));
 }
 int sweep_group_bands() { return kG; }
+
+cudaError_t sweep_prepare(int kind, int d, bool tags) {
+    int nb = 0;
+    if (kind == KIND_ABS) {
+        if (tags) return setup_one<KIND_ABS, kIntR, kIntU, 1, true>(&nb);
+        return setup_one<KIND_ABS, kIntR, kIntU, 1, false>(&nb);
+    }
+    if (d == 12) return setup_one<KIND_EUC, kEucR, kEucU, 12, false>(&nb);
+    if (d == 64) return setup_one<KIND_EUC, 1, 2, 64, false>(&nb);
+    return setup_one<KIND_EUC, 2, 2, 0, false>(&nb);
+}
 
 cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, long long max_blocks,
                          cudaStream_t st) {
