@@ -198,6 +198,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
+    if args.no_graph:
+        dtw.set_option(dtw.OPT_GRAPH, 0)
     X, Y = make_inputs(args.workload, seed_offset=rank)
     M, N = len(X), len(Y)
     Xd = torch.from_numpy(X).to(dev)
@@ -493,6 +495,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 GPU comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="run the level loop from the host (the same kernels; profilers list every launch)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

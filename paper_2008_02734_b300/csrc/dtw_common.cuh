@@ -58,7 +58,10 @@ struct Box {
 };
 
 // Columns of a split row handled by one split work item (one 256-thread block).
-constexpr int kSplitChunk = 1024;
+#ifndef DTW_SPLIT_CHUNK
+#define DTW_SPLIT_CHUNK 256
+#endif
+constexpr int kSplitChunk = DTW_SPLIT_CHUNK;
 
 // Half-width of the window of split rows written by forward/backward sweeps of
 // integer boxes: rows r-kSplitHalo .. r+kSplitHalo around the middle row r.

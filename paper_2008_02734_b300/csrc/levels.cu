@@ -456,20 +456,28 @@ __global__ void __launch_bounds__(256) split_kernel(SplitArgs a) {
             }
         }
         __syncthreads();
-        if (s_last && threadIdx.x == 0) {
-            if (nitems > 1) {
-                __threadfence();
-                for (int m = 0; m < nr; ++m) {
-                    RowMin<V> x = partials[(size_t)fw.item0 * kSplitRowsMax + m];
-                    for (int k = 1; k < nitems; ++k) {
-                        const RowMin<V> y = partials[(size_t)(fw.item0 + k) * kSplitRowsMax + m];
-                        x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
-                    }
-                    rm[m] = x;
+        if (s_last && nitems > 1) {
+            // merge the box's partial minima: one warp per split row, lanes over items
+            __threadfence();
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            for (int m = wid; m < nr; m += nw) {
+                RowMin<V> x{(V)0, 0, INT_MAX};
+                for (int k = lane; k < nitems; k += 32) {
+                    const RowMin<V> y = partials[(size_t)(fw.item0 + k) * kSplitRowsMax + m];
+                    x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
                 }
+                for (int o = 16; o; o >>= 1) {
+                    RowMin<V> y;
+                    y.v = __shfl_down_sync(kFull, x.v, o);
+                    y.n = __shfl_down_sync(kFull, x.n, o);
+                    y.q = __shfl_down_sync(kFull, x.q, o);
+                    if (lane + o < 32) x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
+                }
+                if (lane == 0) rm[m] = x;
             }
-            finish_box<KIND, DIM, V>(a, b, pd, g, fw, bw, bi, rm);
+            __syncthreads();
         }
+        if (s_last && threadIdx.x == 0) finish_box<KIND, DIM, V>(a, b, pd, g, fw, bw, bi, rm);
         __syncthreads();
     }
 }
