@@ -68,7 +68,14 @@ enum dtw_form {
      * when a box side drops below 500 (Section 3.2).  It is the comparator the
      * tiled path is measured against; its path is optimal but, under ties, not
      * necessarily the canonical one. */
-    DTW_PLAIN_F64 = 1 << 8
+    DTW_PLAIN_F64 = 1 << 8,
+    /* With DTW_EUCLID_F32: the accumulated costs are compensated FP32 pairs
+     * (hi + lo, about 48 significant bits; each FP32 frame cost added with
+     * TwoSum) instead of FP64 values, which keeps the DP off the narrow FP64
+     * pipe.  The split comparison still runs in FP64.  The cost matches the FP64
+     * form to about 1e-9 relative on the bundled workloads (the FP32 frame
+     * costs, shared by both forms, carry the 1e-7 error). */
+    DTW_DP_F32_KAHAN = 1 << 10
 };
 
 enum dtw_status {

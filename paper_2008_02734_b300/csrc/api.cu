@@ -171,9 +171,10 @@ int check_kind(int32_t cost_kind, int32_t d, int* kind, bool* plain) {
     const int k = cost_kind & 0xff;
     const int flags = cost_kind & ~0xff;
     if (k != DTW_EUCLID_F32 && k != DTW_ABS_I32) return DTW_EINVAL;
-    if (flags & ~(int)DTW_PLAIN_F64) return DTW_EINVAL;
+    if (flags & ~(int)(DTW_PLAIN_F64 | DTW_DP_F32_KAHAN)) return DTW_EINVAL;
+    if ((flags & DTW_DP_F32_KAHAN) && (k != DTW_EUCLID_F32 || (flags & DTW_PLAIN_F64))) return DTW_EINVAL;
     if (d < 1 || (k == DTW_ABS_I32 && d != 1)) return DTW_EINVAL;
-    *kind = k == DTW_ABS_I32 ? KIND_ABS : KIND_EUC;
+    *kind = k == DTW_ABS_I32 ? KIND_ABS : ((flags & DTW_DP_F32_KAHAN) ? KIND_EUCF : KIND_EUC);
     *plain = (flags & DTW_PLAIN_F64) != 0;
     return DTW_OK;
 }
@@ -271,7 +272,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     }
     if (e != cudaSuccess) return DTW_ECUDA;
     for (int b = 0; b < B; ++b) {
-        if (kind == KIND_EUC && (d == 12 || d == 64) &&
+        if (kind != KIND_ABS && (d == 12 || d == 64) &&
             ((reinterpret_cast<uintptr_t>(pd[b].X) | reinterpret_cast<uintptr_t>(pd[b].Y)) & 15))
             return DTW_EINVAL;  // the d=12 and d=64 kernels load frames in 16-byte pieces
     }

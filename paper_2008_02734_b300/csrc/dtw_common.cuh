@@ -19,6 +19,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // Cost kinds (low byte of the ABI's cost_kind).
 constexpr int KIND_EUC = 0;  // Euclidean distance of FP32 frames, FP64 accumulation
 constexpr int KIND_ABS = 1;  // |x - y| of int32 samples, exact int32 accumulation
+constexpr int KIND_EUCF = 2; // Euclidean distance of FP32 frames, compensated FP32-pair accumulation
 
 // "Infinity" of the int32 accumulator: above any reachable cost (the host
 // guarantees max C * (M+N-1) < 2^29) and far from overflow when C is added.
@@ -156,6 +157,47 @@ __device__ __forceinline__ void set_error(LevelCtl* ctl, int code, int info) {
 
 // ---------------------------------------------------------------- accumulators
 
+// Compensated FP32 accumulator (the DTW_DP_F32_KAHAN form): an unevaluated sum
+// hi + lo of two FP32 values with |lo| <= ulp(hi)/2, so about 48 significant
+// bits.  A frame cost c (an FP32 value) is added with TwoSum (the exact rounding
+// error of hi + c) followed by a renormalisation; the minimum compares (hi, lo)
+// lexicographically, which orders normalised pairs exactly.  "Infinity" is a
+// large finite hi, so that no operation ever meets inf - inf.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, float c) {
+    const float s = __fadd_rn(a.hi, c);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(c, bb));
+    const float t = __fadd_rn(e, a.lo);
+    const float hi = __fadd_rn(s, t);
+    return DF{hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ DF operator+(DF a, double c) { return df_add(a, (float)c); }  // c: a widened FP32 cost
+__device__ __forceinline__ bool operator==(DF a, DF b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ bool operator<(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ DF df_min(DF a, DF b) { return b < a ? b : a; }
+__device__ __forceinline__ DF min3(DF a, DF b, DF c) { return df_min(df_min(a, b), c); }
+__device__ __forceinline__ DF acc_min(DF a, DF b) { return df_min(a, b); }
+__device__ __forceinline__ double acc_min(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ int32_t acc_min(int32_t a, int32_t b) { return a < b ? a : b; }
+__device__ __forceinline__ double to_double(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double to_double(double a) { return a; }
+__device__ __forceinline__ double to_double(int32_t a) { return (double)a; }
+
+// Warp shuffle of an accumulator from the lane below (lane - 1).
+__device__ __forceinline__ int32_t shfl_up1(int32_t v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ DF shfl_up1(DF v) {
+    return DF{__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1)};
+}
+__device__ __forceinline__ int32_t shfl_down(int32_t v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ DF shfl_down(DF v, int o) {
+    return DF{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+
 template <int KIND> struct AccOf;
 template <> struct AccOf<KIND_ABS> {
     using T = int32_t;
@@ -166,6 +208,11 @@ template <> struct AccOf<KIND_EUC> {
     using T = double;
     static __device__ __forceinline__ T inf() { return __longlong_as_double(0x7ff0000000000000LL); }
     static __device__ __forceinline__ T zero() { return 0.0; }
+};
+template <> struct AccOf<KIND_EUCF> {
+    using T = DF;
+    static __device__ __forceinline__ T inf() { return DF{1e30f, 0.f}; }
+    static __device__ __forceinline__ T zero() { return DF{0.f, 0.f}; }
 };
 
 __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return __vimin3_s32(a, b, c); }
@@ -240,6 +287,9 @@ template <> struct Frame<KIND_EUC, 0> {
     }
     __device__ __forceinline__ void load_shared(const void*) {}
 };
+
+// The compensated kind reads the same frames (its costs are the same FP32 values).
+template <int DIM> struct Frame<KIND_EUCF, DIM> : Frame<KIND_EUC, DIM> {};
 
 // Frame cost C (Section 2.1): |x-y|, or the Euclidean distance (Section 4.1)
 // evaluated in FP32 (sum of squares with FMA, correctly rounded sqrt) and widened.
@@ -338,7 +388,7 @@ __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, DIM>& a, cons
 
 // Cost of global cell (i, j) of a pair, for the split and checks.
 template <int KIND, int DIM>
-__device__ __forceinline__ typename AccOf<KIND>::T cell_cost(const PairDesc& pd, int i, int j, int d) {
+__device__ __forceinline__ auto cell_cost(const PairDesc& pd, int i, int j, int d) {
     Frame<KIND, DIM> a, b;
     a.load(pd.X, i, d);
     b.load(pd.Y, j, d);

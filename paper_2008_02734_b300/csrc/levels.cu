@@ -245,6 +245,13 @@ __device__ __forceinline__ RowMin<V> merge(RowMin<V> x, RowMin<V> y) {
     return RowMin<V>{x.v, x.n + y.n, min(x.q, y.q)};
 }
 
+// An accumulator as the split's comparison type (exact for every kind).
+template <typename V, typename A>
+__device__ __forceinline__ V as_v(A x) {
+    if constexpr (std::is_same<A, DF>::value) return (V)to_double(x);
+    else return (V)x;
+}
+
 // Partial minima of the window of split rows over one chunk of columns: for
 // every row m, S = F + B - C (Lemma 2) minimised over the chunk, with the number
 // of columns attaining the minimum and the lowest of them.  Block of 256 threads;
@@ -270,7 +277,7 @@ __device__ void chunk_minima(const SplitArgs& a, const Box& b, const PairDesc& p
                 int i, j;
                 frame_to_global(b, g.axis, g.r - h + m, q, i, j);
                 const V c = (V)cell_cost<KIND, DIM>(pd, i, j, a.d);
-                const V S = (V)F[(size_t)m * fs + q] + (V)B[-(long long)m * bs - q] - c;
+                const V S = as_v<V>(F[(size_t)m * fs + q]) + as_v<V>(B[-(long long)m * bs - q]) - c;
                 const RowMin<V> x{S, 1, q};
                 part[m] = part[m].n == 0 ? x : merge(part[m], x);
             }
@@ -324,7 +331,7 @@ __device__ void finish_box(const SplitArgs& a, const Box& b, const PairDesc& pd,
         }
         int i, j;
         frame_to_global(b, g.axis, g.r, qs, i, j);
-        const Acc c = cell_cost<KIND, DIM>(pd, i, j, a.d);
+        const auto c = cell_cost<KIND, DIM>(pd, i, j, a.d);
         if constexpr (KIND == KIND_ABS) {
             total_i = rr.end_i;
             if (b.known_i >= 0 && b.known_i != total_i) set_error(a.ctl, ERR_CONSIST, 11);
@@ -332,8 +339,8 @@ __device__ void finish_box(const SplitArgs& a, const Box& b, const PairDesc& pd,
             known_r = total_i - known_l + c;
         } else {
             total_f = rr.end_f;
-            kl_f = out[qs];
-            kr_f = total_f - kl_f + c;
+            kl_f = as_v<double>(out[qs]);
+            kr_f = total_f - kl_f + (double)c;
         }
     } else {
         const int nr = fw.nout, h = nr / 2;
@@ -367,8 +374,8 @@ __device__ void finish_box(const SplitArgs& a, const Box& b, const PairDesc& pd,
                 known_l = F[(size_t)pick * fs + qs];
                 known_r = B[-(long long)pick * bs - qs];
             } else {
-                kl_f = F[(size_t)pick * fs + qs];
-                kr_f = B[-(long long)pick * bs - qs];
+                kl_f = as_v<double>(F[(size_t)pick * fs + qs]);
+                kr_f = as_v<double>(B[-(long long)pick * bs - qs]);
             }
         }
     }
@@ -490,6 +497,9 @@ cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
         if (a.n_items < grid) grid = a.n_items;
     }
     if (a.kind == KIND_ABS) split_kernel<KIND_ABS, 1><<<grid, 256, 0, st>>>(a);
+    else if (a.kind == KIND_EUCF && a.d == 12) split_kernel<KIND_EUCF, 12><<<grid, 256, 0, st>>>(a);
+    else if (a.kind == KIND_EUCF && a.d == 64) split_kernel<KIND_EUCF, 64><<<grid, 256, 0, st>>>(a);
+    else if (a.kind == KIND_EUCF) split_kernel<KIND_EUCF, 0><<<grid, 256, 0, st>>>(a);
     else if (a.d == 12) split_kernel<KIND_EUC, 12><<<grid, 256, 0, st>>>(a);
     else if (a.d == 64) split_kernel<KIND_EUC, 64><<<grid, 256, 0, st>>>(a);
     else split_kernel<KIND_EUC, 0><<<grid, 256, 0, st>>>(a);
@@ -547,13 +557,13 @@ __global__ void __launch_bounds__(32 * kBaseWarps) base_kernel(BaseArgs a) {
             uint32_t word = 0;
             for (int s = 0; s < Q + 31; ++s) {
                 const int q = s - lane;
-                Acc up = __shfl_up_sync(kFull, cur, 1);
+                Acc up = shfl_up1(cur);
                 const bool act = rowok && q >= 0 && q < Q;
                 if (lane == 0) up = (band == 0 || !act) ? INF : row[q];
                 if (act) {
                     Frame<KIND, DIM> yc;
                     yc.load(cs, cbase + q, a.d);
-                    const Acc c = frame_cost(xr, yc);
+                    const auto c = frame_cost(xr, yc);
                     const Acc m = min3(dprev, up, left);
                     uint32_t pt;
                     if (p == 0 && q == 0) pt = 3;
@@ -576,15 +586,15 @@ __global__ void __launch_bounds__(32 * kBaseWarps) base_kernel(BaseArgs a) {
         }
         // the box cost and its consistency with the parent's split
         for (int o = 16; o; o >>= 1) {
-            const Acc t = __shfl_down_sync(kFull, end_v, o);
-            end_v = min(end_v, t);
+            const Acc t = shfl_down(end_v, o);
+            end_v = acc_min(end_v, t);
         }
         if (lane == 0) {
             if constexpr (KIND == KIND_ABS) {
                 if (b.known_i >= 0 && b.known_i != (long long)end_v) set_error(a.ctl, ERR_CONSIST, 20);
                 if (b.flags & BOX_ROOT) a.pres[b.pair].cost_i = end_v;
             } else {
-                if (b.flags & BOX_ROOT) a.pres[b.pair].cost_f = end_v;
+                if (b.flags & BOX_ROOT) a.pres[b.pair].cost_f = to_double(end_v);
             }
             atomicAdd(&a.ctl->base_cells, (unsigned long long)P * (unsigned long long)Q);
             // backtrace: per global row, the range of path columns
@@ -631,6 +641,11 @@ static cudaError_t launch_base_t(const BaseArgs& a, cudaStream_t st) {
 cudaError_t launch_base(const BaseArgs& a, cudaStream_t st) {
     if (a.n_base == 0) return cudaSuccess;
     if (a.kind == KIND_ABS) return launch_base_t<KIND_ABS, 1>(a, st);
+    if (a.kind == KIND_EUCF) {
+        if (a.d == 12) return launch_base_t<KIND_EUCF, 12>(a, st);
+        if (a.d == 64) return launch_base_t<KIND_EUCF, 64>(a, st);
+        return launch_base_t<KIND_EUCF, 0>(a, st);
+    }
     if (a.d == 12) return launch_base_t<KIND_EUC, 12>(a, st);
     if (a.d == 64) return launch_base_t<KIND_EUC, 64>(a, st);
     return launch_base_t<KIND_EUC, 0>(a, st);

@@ -169,7 +169,7 @@ __device__ __forceinline__ void store_row(T* p, const T* v) {
 #pragma unroll
         for (int i = 0; i < U; i += 4)
             *reinterpret_cast<int4*>(p + i) = make_int4((int)v[i], (int)v[i + 1], (int)v[i + 2], (int)v[i + 3]);
-    } else if constexpr (sizeof(T) == 8 && U % 2 == 0) {
+    } else if constexpr (std::is_same<T, double>::value && U % 2 == 0) {
 #pragma unroll
         for (int i = 0; i < U; i += 2) {
             double2 t;
@@ -215,6 +215,9 @@ __device__ __forceinline__ void pack(typename AccOf<KIND>::T v, int t, uint32_t*
     if constexpr (KIND == KIND_ABS) {
         w[0] = (uint32_t)v;
         if constexpr (NW == 2) w[1] = (uint32_t)t;
+    } else if constexpr (KIND == KIND_EUCF) {
+        w[0] = __float_as_uint(v.hi);
+        w[1] = __float_as_uint(v.lo);
     } else {
         w[0] = (uint32_t)__double2loint((double)v);
         w[1] = (uint32_t)__double2hiint((double)v);
@@ -225,6 +228,9 @@ __device__ __forceinline__ void unpack(const uint32_t* w, typename AccOf<KIND>::
     if constexpr (KIND == KIND_ABS) {
         v = (int32_t)w[0];
         t = NW == 2 ? (int)w[1] : 0;
+    } else if constexpr (KIND == KIND_EUCF) {
+        v = DF{__uint_as_float(w[0]), __uint_as_float(w[1])};
+        t = 0;
     } else {
         v = __hiloint2double((int)w[1], (int)w[0]);
         t = 0;
@@ -290,6 +296,10 @@ struct ColFrame {
 };
 template <>
 struct ColFrame<KIND_EUC, 64> {
+    using T = FrameRef<64>;
+};
+template <>
+struct ColFrame<KIND_EUCF, 64> {
     using T = FrameRef<64>;
 };
 
@@ -475,7 +485,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
             Acc rv;
             int rt;
             unpack<KIND, NW>(cw + u * NW, rv, rt);
-            const Acc sv = __shfl_up_sync(kFull, bot[u], 1);
+            const Acc sv = shfl_up1(bot[u]);
             upv[u] = lane == 0 ? rv : sv;
             if constexpr (TAG) {
                 const int st = __shfl_up_sync(kFull, bott[u], 1);
@@ -495,7 +505,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                 int t_dg = (u == 0) ? dprevt : upt[u - 1];
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
-                    const Acc c = frame_cost(xr[k], yc[u]);
+                    const auto c = frame_cost(xr[k], yc[u]);
                     const Acc lf = L[k];
                     const Acc m = min3(a_dg, a_up, lf);
                     const Acc nv = m + c;
@@ -570,7 +580,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         if (end_k >= 0 && end_k < R) {
             SweepRes* r = A.res + sweep_idx;
             if constexpr (KIND == KIND_ABS) r->end_i = end_v;
-            else r->end_f = end_v;
+            else r->end_f = to_double(end_v);
             r->end_tag = end_t;
         }
     }
@@ -749,7 +759,7 @@ __device__ __forceinline__ int find_sweep(const Sweep* sweeps, int n_sweeps, lon
 // two payload words per column; untagged integer sweeps use one.
 template <int KIND, int R, int U, int DIM, bool TAGS>
 __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__ SweepArgs A) {
-    constexpr int NWMAX = (KIND == KIND_EUC || TAGS) ? 2 : 1;
+    constexpr int NWMAX = (KIND != KIND_ABS || TAGS) ? 2 : 1;
     using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM& sm = *reinterpret_cast<SM*>(smem_raw);
@@ -821,7 +831,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
                 const int b_lo = band * BR, b_hi = b_lo + BR;  // band rows [b_lo, b_hi)
                 const bool special =
                     (sp->nout > 0 && sp->out_row0 < b_hi && sp->out_row0 + sp->nout > b_lo) || (rows - 1 < b_hi);
-                if constexpr (KIND == KIND_EUC) {
+                if constexpr (KIND != KIND_ABS) {
                     run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true>(special, sp, si, band, to_ring, to_global, A, sm,
                                                                    warp);
                 } else if (!TAGS || tag_row < 0) {
@@ -851,7 +861,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
             }
         } else {
             const int si0 = sweep_of[0];
-            if (KIND == KIND_EUC || (TAGS && si0 >= 0 && A.sweeps[si0].tag_row >= 0))
+            if (KIND != KIND_ABS || (TAGS && si0 >= 0 && A.sweeps[si0].tag_row >= 0))
                 run_loader<KIND, U, DIM, NWMAX, 2>(A, sm);
             else
                 run_loader<KIND, U, DIM, NWMAX, 1>(A, sm);
@@ -867,7 +877,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
 // its warps over the schedulers of the whole GPU.
 template <int KIND, int R, int U, int DIM, bool TAGS>
 static cudaError_t setup_one(int* nb_out) {
-    constexpr int NWMAX = (KIND == KIND_EUC || TAGS) ? 2 : 1;
+    constexpr int NWMAX = (KIND != KIND_ABS || TAGS) ? 2 : 1;
     constexpr size_t smem = sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>);
     static int nb = 0;
     if (nb == 0) {
@@ -884,7 +894,7 @@ static cudaError_t setup_one(int* nb_out) {
 
 template <int KIND, int R, int U, int DIM, bool TAGS>
 static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blocks, cudaStream_t st) {
-    constexpr int NWMAX = (KIND == KIND_EUC || TAGS) ? 2 : 1;
+    constexpr int NWMAX = (KIND != KIND_ABS || TAGS) ? 2 : 1;
     constexpr size_t smem = sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>);
     int nb = 0;
     cudaError_t e = setup_one<KIND, R, U, DIM, TAGS>(&nb);
@@ -915,6 +925,11 @@ cudaError_t sweep_prepare(int kind, int d, bool tags) {
         if (tags) return setup_one<KIND_ABS, kIntR, kIntU, 1, true>(&nb);
         return setup_one<KIND_ABS, kIntR, kIntU, 1, false>(&nb);
     }
+    if (kind == KIND_EUCF) {
+        if (d == 12) return setup_one<KIND_EUCF, kEucR, kEucU, 12, false>(&nb);
+        if (d == 64) return setup_one<KIND_EUCF, 1, 2, 64, false>(&nb);
+        return setup_one<KIND_EUCF, 2, 2, 0, false>(&nb);
+    }
     if (d == 12) return setup_one<KIND_EUC, kEucR, kEucU, 12, false>(&nb);
     if (d == 64) return setup_one<KIND_EUC, 1, 2, 64, false>(&nb);
     return setup_one<KIND_EUC, 2, 2, 0, false>(&nb);
@@ -925,6 +940,11 @@ cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num
     if (kind == KIND_ABS) {
         if (tags) return launch_one<KIND_ABS, kIntR, kIntU, 1, true>(A, num_sms, max_blocks, st);
         return launch_one<KIND_ABS, kIntR, kIntU, 1, false>(A, num_sms, max_blocks, st);
+    }
+    if (kind == KIND_EUCF) {
+        if (d == 12) return launch_one<KIND_EUCF, kEucR, kEucU, 12, false>(A, num_sms, max_blocks, st);
+        if (d == 64) return launch_one<KIND_EUCF, 1, 2, 64, false>(A, num_sms, max_blocks, st);
+        return launch_one<KIND_EUCF, 2, 2, 0, false>(A, num_sms, max_blocks, st);
     }
     if (d == 12) return launch_one<KIND_EUC, kEucR, kEucU, 12, false>(A, num_sms, max_blocks, st);
     // d = 64: one row per lane (its frame in registers), column frames read in place

@@ -232,3 +232,39 @@ def test_arena():
         check_int(X, Y)
     finally:
         dtw.set_arena(None)
+
+
+@pytest.mark.parametrize("M,N,d", [(1, 7, 12), (300, 257, 12), (1000, 1300, 12), (200, 300, 64), (700, 650, 64),
+                                   (70, 90, 3)])
+def test_dp_f32_kahan_form(M, N, d):
+    """The compensated FP32 DP form: optimal within the float tolerance and within
+    1e-9 relative of the FP64 form (both use the same FP32 frame costs)."""
+    if d == 12:
+        X, Y = synth.chroma_pair(M + 5 * N, M, N)
+    elif d == 64:
+        X, Y = synth.mfcc_pair(M + 5 * N, M, N)
+    else:
+        rng = np.random.default_rng(M + N)
+        X = rng.standard_normal((M, d)).astype(np.float32)
+        Y = rng.standard_normal((N, d)).astype(np.float32)
+    path, cost = dtw.align(_cuda(X), _cuda(Y), dp_f32=True)
+    p = path.cpu().numpy()
+    check_path_struct(p, M, N)
+    c_ref = oracle.dtw(X, Y)[1]
+    assert cost == pytest.approx(c_ref, rel=REL_TOL, abs=1e-9)
+    assert oracle.path_cost(X, Y, p) == pytest.approx(c_ref, rel=REL_TOL, abs=1e-9)
+    c64 = dtw.align(_cuda(X), _cuda(Y))[1]
+    assert cost == pytest.approx(c64, rel=1e-9, abs=1e-12)
+    assert dtw.cost(_cuda(X), _cuda(Y), dp_f32=True) == pytest.approx(c64, rel=1e-9, abs=1e-12)
+
+
+def test_dp_f32_kahan_batch_and_serving():
+    pairs = [synth.chroma_pair(90 + k, m, n) for k, (m, n) in enumerate([(500, 600), (800, 700), (40, 30)])]
+    res = dtw.align_batch([_cuda(x) for x, _ in pairs], [_cuda(y) for _, y in pairs], dp_f32=True)
+    for (X, Y), (path, cost) in zip(pairs, res):
+        c_ref = oracle.dtw(X, Y)[1]
+        assert cost == pytest.approx(c_ref, rel=REL_TOL)
+    X, Y = pairs[1]
+    t, path, keep = dtw.submit(_cuda(X), _cuda(Y), dp_f32=True)
+    rc, K, c = dtw.wait(t)
+    assert rc == dtw.OK and c == pytest.approx(oracle.dtw(X, Y)[1], rel=REL_TOL)
