@@ -75,7 +75,18 @@ enum dtw_form {
      * pipe.  The split comparison still runs in FP64.  The cost matches the FP64
      * form to about 1e-9 relative on the bundled workloads (the FP32 frame
      * costs, shared by both forms, carry the 1e-7 error). */
-    DTW_DP_F32_KAHAN = 1 << 10
+    DTW_DP_F32_KAHAN = 1 << 10,
+    /* With DTW_EUCLID_F32 and d == 64: a reduced-precision form.  The frame cost
+     * is the expanded form sqrt(max(0, |x|^2 + |y|^2 - 2 x.y)) with the squared
+     * norms in FP32 and the dot product of the BF16-rounded frames on the tensor
+     * cores (FP32 accumulation) in 32 x 32 cost tiles; the DP is the
+     * compensated FP32 one (implies DTW_DP_F32_KAHAN).  Its error against the
+     * exact FP64 optimum is far above 1e-6: BF16 keeps 8 significant bits and the
+     * expanded form cancels where frames are close, i.e. along the optimal path
+     * (the measured error on the 60000 x 75000 MFCC-like pair is stated in the
+     * library's design notes).  The returned path is a warping path; its cost is
+     * the optimum of the form's own costs. */
+    DTW_COST_BF16 = 1 << 9
 };
 
 enum dtw_status {

@@ -24,7 +24,12 @@ _LIB_PATH = os.path.join(_PKG, "libdtw_b300.so")
 EUCLID_F32 = 0
 ABS_I32 = 1
 PLAIN_F64 = 1 << 8
+COST_BF16 = 1 << 9
 DP_F32_KAHAN = 1 << 10
+
+
+def _form(dp_f32: bool, cost_bf16: bool) -> int:
+    return (DP_F32_KAHAN if dp_f32 else 0) | (COST_BF16 if cost_bf16 else 0)
 
 OK, PENDING, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBUSY, EINTERNAL = 0, 1, -1, -2, -3, -4, -5, -6, -7
 OPT_TIMING, OPT_BASE_AREA, OPT_SPIN_LIMIT, OPT_SKIP_PUBLISH, OPT_GRAPH = 1, 2, 3, 4, 5
@@ -174,18 +179,19 @@ def _path_buffer(M, N, like_cuda):
     return torch.empty((M + N - 1, 2), dtype=torch.int32)
 
 
-def align(X, Y, *, plain: bool = False, dp_f32: bool = False, path_out=None):
+def align(X, Y, *, plain: bool = False, dp_f32: bool = False, cost_bf16: bool = False, path_out=None):
     """Exact DTW of one pair: returns (path as an int32 tensor of shape (K, 2), D*).
 
     ``plain=True`` runs the paper's plain FP64 form (one launch per anti-diagonal)
     instead of the tiled path; ``dp_f32=True`` (float frames) accumulates in
-    compensated FP32 pairs instead of FP64.  ``path_out`` may supply the
+    compensated FP32 pairs instead of FP64; ``cost_bf16=True`` (d = 64) uses the
+    reduced-precision tensor-core cost form.  ``path_out`` may supply the
     (M+N-1, 2) int32 output buffer (host or device)."""
     keep, xp, M, yp, N, d, kind, on_cuda, cu = _prep_pair(X, Y)
     if cu is not None:
         _sync_stream(cu)
     path = _path_buffer(M, N, cu) if path_out is None else path_out
-    ck = kind | (PLAIN_F64 if plain else 0) | (DP_F32_KAHAN if dp_f32 else 0)
+    ck = kind | (PLAIN_F64 if plain else 0) | _form(dp_f32, cost_bf16)
     cost = ctypes.c_double()
     K = _get_lib().dtw_align(xp, M, yp, N, d, ck, ctypes.c_void_p(path.data_ptr()), ctypes.byref(cost))
     _check(K, "dtw_align")
@@ -193,13 +199,13 @@ def align(X, Y, *, plain: bool = False, dp_f32: bool = False, path_out=None):
     return path[:K], (int(c) if kind == ABS_I32 else c)
 
 
-def cost(X, Y, *, dp_f32: bool = False):
+def cost(X, Y, *, dp_f32: bool = False, cost_bf16: bool = False):
     """D* only (one forward sweep, no path)."""
     keep, xp, M, yp, N, d, kind, on_cuda, cu = _prep_pair(X, Y)
     if cu is not None:
         _sync_stream(cu)
     c = ctypes.c_double()
-    ck = kind | (DP_F32_KAHAN if dp_f32 else 0)
+    ck = kind | _form(dp_f32, cost_bf16)
     _check(_get_lib().dtw_cost(xp, M, yp, N, d, ck, ctypes.byref(c)), "dtw_cost")
     return int(c.value) if kind == ABS_I32 else c.value
 
@@ -218,7 +224,7 @@ def cost_noalloc(X, Y):
     return int(c.value) if kind == ABS_I32 else c.value
 
 
-def align_batch(Xs, Ys, *, dp_f32: bool = False):
+def align_batch(Xs, Ys, *, dp_f32: bool = False, cost_bf16: bool = False):
     """Aligns B pairs together; returns a list of (path, D*)."""
     B = len(Xs)
     if B != len(Ys) or B == 0:
@@ -246,19 +252,19 @@ def align_batch(Xs, Ys, *, dp_f32: bool = False):
     K = I64()
     C = (ctypes.c_double * B)()
     rc = _get_lib().dtw_align_batch(B, VP(*xps), I64(*Ms), VP(*yps), I64(*Ns), d0,
-                                    kind0 | (DP_F32_KAHAN if dp_f32 else 0),
+                                    kind0 | _form(dp_f32, cost_bf16),
                              VP(*[p.data_ptr() for p in paths]), K, C)
     _check(rc, "dtw_align_batch")
     return [(paths[b][:K[b]], int(C[b]) if kind0 == ABS_I32 else C[b]) for b in range(B)]
 
 
-def submit(X, Y, path_out=None, *, dp_f32: bool = False):
+def submit(X, Y, path_out=None, *, dp_f32: bool = False, cost_bf16: bool = False):
     """Queues one alignment; returns (ticket, path buffer, keep-alive)."""
     keep, xp, M, yp, N, d, kind, on_cuda, cu = _prep_pair(X, Y)
     if cu is not None:
         _sync_stream(cu)
     path = _path_buffer(M, N, cu) if path_out is None else path_out
-    r = Request(xp, M, yp, N, d, kind | (DP_F32_KAHAN if dp_f32 else 0), path.data_ptr())
+    r = Request(xp, M, yp, N, d, kind | _form(dp_f32, cost_bf16), path.data_ptr())
     t = _check(_get_lib().dtw_submit(ctypes.byref(r)), "dtw_submit")
     return t, path, keep
 

@@ -171,10 +171,13 @@ int check_kind(int32_t cost_kind, int32_t d, int* kind, bool* plain) {
     const int k = cost_kind & 0xff;
     const int flags = cost_kind & ~0xff;
     if (k != DTW_EUCLID_F32 && k != DTW_ABS_I32) return DTW_EINVAL;
-    if (flags & ~(int)(DTW_PLAIN_F64 | DTW_DP_F32_KAHAN)) return DTW_EINVAL;
-    if ((flags & DTW_DP_F32_KAHAN) && (k != DTW_EUCLID_F32 || (flags & DTW_PLAIN_F64))) return DTW_EINVAL;
+    if (flags & ~(int)(DTW_PLAIN_F64 | DTW_DP_F32_KAHAN | DTW_COST_BF16)) return DTW_EINVAL;
+    if ((flags & (DTW_DP_F32_KAHAN | DTW_COST_BF16)) && (k != DTW_EUCLID_F32 || (flags & DTW_PLAIN_F64)))
+        return DTW_EINVAL;
+    if ((flags & DTW_COST_BF16) && d != 64) return DTW_EINVAL;  // the tensor-core tiles are built for d = 64
     if (d < 1 || (k == DTW_ABS_I32 && d != 1)) return DTW_EINVAL;
-    *kind = k == DTW_ABS_I32 ? KIND_ABS : ((flags & DTW_DP_F32_KAHAN) ? KIND_EUCF : KIND_EUC);
+    *kind = k == DTW_ABS_I32 ? KIND_ABS
+                             : ((flags & DTW_COST_BF16) ? KIND_EUCB : ((flags & DTW_DP_F32_KAHAN) ? KIND_EUCF : KIND_EUC));
     *plain = (flags & DTW_PLAIN_F64) != 0;
     return DTW_OK;
 }

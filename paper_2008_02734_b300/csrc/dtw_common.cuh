@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace dtwb {
@@ -20,6 +21,8 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int KIND_EUC = 0;  // Euclidean distance of FP32 frames, FP64 accumulation
 constexpr int KIND_ABS = 1;  // |x - y| of int32 samples, exact int32 accumulation
 constexpr int KIND_EUCF = 2; // Euclidean distance of FP32 frames, compensated FP32-pair accumulation
+constexpr int KIND_EUCB = 3; // Euclidean distance in the expanded form with BF16 products (tensor-core
+                             // cost tiles), compensated FP32-pair accumulation; d = 64
 
 // "Infinity" of the int32 accumulator: above any reachable cost (the host
 // guarantees max C * (M+N-1) < 2^29) and far from overflow when C is added.
@@ -214,6 +217,7 @@ template <> struct AccOf<KIND_EUCF> {
     static __device__ __forceinline__ T inf() { return DF{1e30f, 0.f}; }
     static __device__ __forceinline__ T zero() { return DF{0.f, 0.f}; }
 };
+template <> struct AccOf<KIND_EUCB> : AccOf<KIND_EUCF> {};
 
 __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return __vimin3_s32(a, b, c); }
 // Accumulated costs are sums of nonnegative frame costs (or +infinity), and for
@@ -290,6 +294,26 @@ template <> struct Frame<KIND_EUC, 0> {
 
 // The compensated kind reads the same frames (its costs are the same FP32 values).
 template <int DIM> struct Frame<KIND_EUCF, DIM> : Frame<KIND_EUC, DIM> {};
+// The BF16 form reads the same FP32 frames; its cost is the expanded form below.
+template <int DIM> struct Frame<KIND_EUCB, DIM> : Frame<KIND_EUC, DIM> {};
+
+// Expanded-form cost of the BF16 form: sqrt(max(0, |x|^2 + |y|^2 - 2 x.y)) with
+// the squared norms summed in FP32 from the FP32 coordinates (in coordinate
+// order) and the dot product of the BF16-rounded coordinates accumulated in FP32
+// -- the products of two BF16 values are exact in FP32, as in the tensor-core
+// tiles of the sweep, which accumulate the same products in their own order.
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float expanded_cost(float xx, float yy, float dot) {
+    const float t = __fmaf_rn(-2.f, dot, __fadd_rn(xx, yy));
+    return __fsqrt_rn(fmaxf(t, 0.f));
+}
+template <int DIM>
+__device__ __forceinline__ float sqnorm(const float* v) {
+    float s = 0.f;
+#pragma unroll
+    for (int e = 0; e < DIM; ++e) s = __fmaf_rn(v[e], v[e], s);
+    return s;
+}
 
 // Frame cost C (Section 2.1): |x-y|, or the Euclidean distance (Section 4.1)
 // evaluated in FP32 (sum of squares with FMA, correctly rounded sqrt) and widened.
@@ -362,6 +386,14 @@ __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, 0>& a, const 
         s = fmaf(t, t, s);
     }
     return widen_cost(__fsqrt_rn(s));
+}
+
+template <int DIM>
+__device__ __forceinline__ double frame_cost(const Frame<KIND_EUCB, DIM>& a, const Frame<KIND_EUCB, DIM>& b) {
+    float dot = 0.f;
+#pragma unroll
+    for (int e = 0; e < DIM; ++e) dot = __fmaf_rn(bf16_round(a.v[e]), bf16_round(b.v[e]), dot);
+    return widen_cost(expanded_cost(sqnorm<DIM>(a.v), sqnorm<DIM>(b.v), dot));
 }
 
 // A column frame read in place (shared memory), for large fixed dimensions whose

@@ -497,6 +497,7 @@ cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
         if (a.n_items < grid) grid = a.n_items;
     }
     if (a.kind == KIND_ABS) split_kernel<KIND_ABS, 1><<<grid, 256, 0, st>>>(a);
+    else if (a.kind == KIND_EUCB) split_kernel<KIND_EUCB, 64><<<grid, 256, 0, st>>>(a);
     else if (a.kind == KIND_EUCF && a.d == 12) split_kernel<KIND_EUCF, 12><<<grid, 256, 0, st>>>(a);
     else if (a.kind == KIND_EUCF && a.d == 64) split_kernel<KIND_EUCF, 64><<<grid, 256, 0, st>>>(a);
     else if (a.kind == KIND_EUCF) split_kernel<KIND_EUCF, 0><<<grid, 256, 0, st>>>(a);
@@ -641,6 +642,7 @@ static cudaError_t launch_base_t(const BaseArgs& a, cudaStream_t st) {
 cudaError_t launch_base(const BaseArgs& a, cudaStream_t st) {
     if (a.n_base == 0) return cudaSuccess;
     if (a.kind == KIND_ABS) return launch_base_t<KIND_ABS, 1>(a, st);
+    if (a.kind == KIND_EUCB) return launch_base_t<KIND_EUCB, 64>(a, st);
     if (a.kind == KIND_EUCF) {
         if (a.d == 12) return launch_base_t<KIND_EUCF, 12>(a, st);
         if (a.d == 64) return launch_base_t<KIND_EUCF, 64>(a, st);

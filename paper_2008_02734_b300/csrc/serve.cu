@@ -488,12 +488,15 @@ int64_t dtw_submit(const dtw_request* r) {
     if (!r || !r->X || !r->Y || !r->path_out || r->M < 1 || r->N < 1 || r->d < 1) return DTW_EINVAL;
     const int k = r->cost_kind & 0xff, flags = r->cost_kind & ~0xff;
     if (k != DTW_EUCLID_F32 && k != DTW_ABS_I32) return DTW_EINVAL;
-    // forms: the compensated FP32 DP only (the plain FP64 form is not served)
-    if (flags & ~(int)DTW_DP_F32_KAHAN) return DTW_EINVAL;
-    if ((flags & DTW_DP_F32_KAHAN) && k != DTW_EUCLID_F32) return DTW_EINVAL;
+    // forms: the compensated FP32 DP and the BF16 tensor-core cost (the plain FP64 form is not served)
+    if (flags & ~(int)(DTW_DP_F32_KAHAN | DTW_COST_BF16)) return DTW_EINVAL;
+    if (flags && k != DTW_EUCLID_F32) return DTW_EINVAL;
+    if ((flags & DTW_COST_BF16) && r->d != 64) return DTW_EINVAL;
     if (k == DTW_ABS_I32 && r->d != 1) return DTW_EINVAL;
     if (r->M > (1LL << 30) || r->N > (1LL << 30)) return DTW_EINVAL;
-    const int kind = k == DTW_ABS_I32 ? KIND_ABS : ((flags & DTW_DP_F32_KAHAN) ? KIND_EUCF : KIND_EUC);
+    const int kind = k == DTW_ABS_I32 ? KIND_ABS
+                                      : ((flags & DTW_COST_BF16) ? KIND_EUCB
+                                                                 : ((flags & DTW_DP_F32_KAHAN) ? KIND_EUCF : KIND_EUC));
     if (kind != KIND_ABS && (r->d == 12 || r->d == 64) &&
         ((reinterpret_cast<uintptr_t>(r->X) | reinterpret_cast<uintptr_t>(r->Y)) & 15))
         return DTW_EINVAL;  // the d=12 kernels load frames in 16-byte pieces

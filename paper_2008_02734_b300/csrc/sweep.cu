@@ -215,7 +215,7 @@ __device__ __forceinline__ void pack(typename AccOf<KIND>::T v, int t, uint32_t*
     if constexpr (KIND == KIND_ABS) {
         w[0] = (uint32_t)v;
         if constexpr (NW == 2) w[1] = (uint32_t)t;
-    } else if constexpr (KIND == KIND_EUCF) {
+    } else if constexpr (std::is_same<typename AccOf<KIND>::T, DF>::value) {
         w[0] = __float_as_uint(v.hi);
         w[1] = __float_as_uint(v.lo);
     } else {
@@ -228,7 +228,7 @@ __device__ __forceinline__ void unpack(const uint32_t* w, typename AccOf<KIND>::
     if constexpr (KIND == KIND_ABS) {
         v = (int32_t)w[0];
         t = NW == 2 ? (int)w[1] : 0;
-    } else if constexpr (KIND == KIND_EUCF) {
+    } else if constexpr (std::is_same<typename AccOf<KIND>::T, DF>::value) {
         v = DF{__uint_as_float(w[0]), __uint_as_float(w[1])};
         t = 0;
     } else {
@@ -243,8 +243,33 @@ __device__ __forceinline__ void unpack(const uint32_t* w, typename AccOf<KIND>::
 // global memory by every lane, the runtime-dimension variant).
 template <int KIND, int DIM>
 struct FrameWords {
-    static constexpr int v = KIND == KIND_ABS ? 1 : DIM;
+    static constexpr int v = KIND == KIND_ABS ? 1 : (KIND == KIND_EUCB ? 0 : DIM);
 };
+
+// Per-warp shared memory of the BF16 tensor-core form: the band's 32 row frames
+// and a tile's 32 column frames as BF16 (rows padded to 36 words: conflict-free
+// fragment loads), their FP32 squared norms, and a ring of three 32 x 32 cost
+// tiles (rows padded to 33 floats: conflict-free reads along the skewed lanes).
+struct TcWarp {
+    uint32_t xb[32][36];
+    uint32_t yb[32][36];
+    float xx[32], yy[32];
+    float tile[3][32][33];
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 t = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&t);
+}
+
+// D += A(16x16, row) B(16x8, col), BF16 inputs, FP32 accumulators.
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
 
 // Shared memory of a block.  Row ring g carries the last row of the band above
 // warp g's band (written by warp g-1, or by the loader from global memory for
@@ -320,10 +345,13 @@ struct ColFrame<KIND_EUCF, 64> {
 template <int KIND, int R, int U, int DIM, int NWMAX, int NW, int TAGM, bool VF, bool SPECIAL>
 __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_idx, int band, bool to_ring,
                                       bool to_global, const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>& sm,
-                                      int g) {
+                                      int g, TcWarp* tc) {
     using Acc = typename AccOf<KIND>::T;
     using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>;
     constexpr int YW = FrameWords<KIND, DIM>::v;
+    // BF16 tensor-core form: one row per lane, 16 column blocks of 2 per tile
+    constexpr bool TC = KIND == KIND_EUCB;
+    static_assert(!TC || (DIM == 64 && R == 1 && U == 2), "the tensor-core form is built for d = 64, R = 1, U = 2");
     constexpr bool TAG = TAGM != 0;
     constexpr int SLOT = U * NWMAX;  // row ring slot stride (words)
     constexpr int BW = U * NW;       // payload words per block
@@ -369,11 +397,92 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     }
 
     Frame<KIND, DIM> xr[R];
+    if constexpr (!TC) {
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const int p = min(p0 + k, rows - 1);
-        xr[k].load(rowseq, (long long)rbase + (long long)rstep * p, A.d);
+        for (int k = 0; k < R; ++k) {
+            const int p = min(p0 + k, rows - 1);
+            xr[k].load(rowseq, (long long)rbase + (long long)rstep * p, A.d);
+        }
     }
+
+    // ---- tensor-core cost tiles (BF16 form)
+    // A fragments of the band's rows (m16 x k16 tiles, 2 x 4 of them) stay in
+    // registers for the whole band; each tile of 16 column blocks (32 columns)
+    // is built by the whole warp when lane 0 reaches it: the column frames,
+    // loaded one tile ahead from global memory, become BF16 B fragments, 32
+    // MMAs give the dot products and the expanded form gives the costs.
+    uint32_t afr[TC ? 2 : 1][TC ? 4 : 1][4];
+    float yv[TC ? 64 : 1];
+    const float* colf = static_cast<const float*>(sp->colseq);
+    const long long cbase0 = sp->cbase;
+    const int cstep0 = sp->cstep;
+    auto load_ycol = [&](int t) {  // lane c: column frame 32t + c (clamped)
+        if constexpr (TC) {
+            const int q = min(32 * t + lane, Q - 1);
+            const float4* src = reinterpret_cast<const float4*>(colf + (cbase0 + (long long)cstep0 * q) * 64);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const float4 v = __ldg(src + e);
+                yv[4 * e] = v.x;
+                yv[4 * e + 1] = v.y;
+                yv[4 * e + 2] = v.z;
+                yv[4 * e + 3] = v.w;
+            }
+        }
+    };
+    if constexpr (TC) {
+        Frame<KIND_EUC, 64> xf;
+        xf.load(rowseq, (long long)rbase + (long long)rstep * min(p0, rows - 1), 64);
+        tc->xx[lane] = sqnorm<64>(xf.v);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) tc->xb[lane][e] = pack_bf16x2(xf.v[2 * e], xf.v[2 * e + 1]);
+        __syncwarp();
+        const int gr = lane >> 2, qd = lane & 3;
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                afr[m][k][0] = tc->xb[m * 16 + gr][k * 8 + qd];
+                afr[m][k][1] = tc->xb[m * 16 + gr + 8][k * 8 + qd];
+                afr[m][k][2] = tc->xb[m * 16 + gr][k * 8 + 4 + qd];
+                afr[m][k][3] = tc->xb[m * 16 + gr + 8][k * 8 + 4 + qd];
+            }
+        load_ycol(0);
+    }
+    auto build_tile = [&](int t) {
+        if constexpr (TC) {
+            tc->yy[lane] = sqnorm<64>(yv);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) tc->yb[lane][e] = pack_bf16x2(yv[2 * e], yv[2 * e + 1]);
+            load_ycol(t + 1);  // the next tile's frames, consumed at its build
+            __syncwarp();
+            const int gr = lane >> 2, qd = lane & 3;
+            float (*tile)[33] = tc->tile[t % 3];
+#pragma unroll
+            for (int n = 0; n < 4; ++n) {
+                float acc[2][4] = {};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t b0 = tc->yb[n * 8 + gr][k * 8 + qd];
+                    const uint32_t b1 = tc->yb[n * 8 + gr][k * 8 + 4 + qd];
+                    mma_bf16(acc[0], afr[0][k], b0, b1);
+                    mma_bf16(acc[1], afr[1][k], b0, b1);
+                }
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int r = m * 16 + gr + 8 * h;
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const int c = n * 8 + 2 * qd + j;
+                            tile[r][c] = expanded_cost(tc->xx[r], tc->yy[c], acc[m][2 * h + j]);
+                        }
+                    }
+            }
+            __syncwarp();
+        }
+    };
 
     Acc L[R];  // D(p0+k, q-1): the column left of the current one
     int LT[R];
@@ -415,8 +524,8 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     auto fetch = [&](int s) {
         ld_shared_words<BW>(rin + (s & (URS - 1)) * SLOT, nwd);
         const int cb = s - lane;
-        if constexpr (!YPF) {
-            // frames are loaded by the step itself
+        if constexpr (TC || !YPF) {
+            // tensor-core form: costs come from the tiles; otherwise frames are loaded by the step itself
         } else if constexpr (KIND == KIND_ABS && U % 4 == 0) {
             uint32_t w[U];
             ld_shared_words<U>(yr + (cb & ymask) * YSW, w);
@@ -470,7 +579,8 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         for (int i = 0; i < BW; ++i) cw[i] = nwd[i];
         YF yc[U];
         const int cb = s - lane;
-        if constexpr (YPF) {
+        if constexpr (TC) {
+        } else if constexpr (YPF) {
 #pragma unroll
             for (int u = 0; u < U; ++u) yc[u] = ny[u];
         } else {
@@ -505,10 +615,20 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                 int t_dg = (u == 0) ? dprevt : upt[u - 1];
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
-                    const auto c = frame_cost(xr[k], yc[u]);
+                    double c;
+                    if constexpr (TC) {
+                        const int t = cb >> 4;  // cb >= 0 here
+                        c = (double)tc->tile[t % 3][lane][(2 * cb + u) & 31];
+                    } else {
+                        c = 0.0;
+                    }
+                    const auto cc = [&]() {
+                        if constexpr (TC) return c;
+                        else return frame_cost(xr[k], yc[u]);
+                    }();
                     const Acc lf = L[k];
                     const Acc m = min3(a_dg, a_up, lf);
-                    const Acc nv = m + c;
+                    const Acc nv = m + cc;
                     int t = 0;
                     if constexpr (TAG) {
                         const int t_lf = LT[k];
@@ -561,6 +681,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     fetch(0);
     for (int s0 = 0; s0 < nsteps; s0 += KC) {
         if (s0 > 0) sync_group(s0);
+        if (TC && (s0 & 15) == 0 && s0 < nblk) build_tile(s0 >> 4);
         if (s0 >= 31 && s0 + KC < nblk) {
             if constexpr (KIND == KIND_ABS) {
 #pragma unroll kGroupUnroll
@@ -738,9 +859,17 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
 template <int KIND, int R, int U, int DIM, int NWMAX, int NW, int TAGM, bool VF>
 __device__ __forceinline__ void run_band_s(bool special, const Sweep* sp, int si, int band, bool to_ring,
                                            bool to_global, const SweepArgs& A,
-                                           StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>& sm, int g) {
-    if (special) run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, true>(sp, si, band, to_ring, to_global, A, sm, g);
-    else run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, false>(sp, si, band, to_ring, to_global, A, sm, g);
+                                           StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>& sm, int g, TcWarp* tc) {
+    if (special) run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, true>(sp, si, band, to_ring, to_global, A, sm, g, tc);
+    else run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, false>(sp, si, band, to_ring, to_global, A, sm, g, tc);
+}
+
+// Dynamic shared memory of a block: the strip state, then (tensor-core form)
+// one TcWarp per band warp.
+template <int KIND, int U, int NWMAX, int DIM>
+constexpr size_t strip_smem_bytes() {
+    constexpr size_t base = (sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>) + 127) & ~(size_t)127;
+    return base + (KIND == KIND_EUCB ? kG * sizeof(TcWarp) : 0);
 }
 
 // Index of the sweep holding level band gb: the last sweep whose band_begin is
@@ -763,6 +892,10 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
     using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM& sm = *reinterpret_cast<SM*>(smem_raw);
+    constexpr size_t tc_off = (sizeof(SM) + 127) & ~(size_t)127;
+    TcWarp* tcw = KIND == KIND_EUCB && (threadIdx.x >> 5) < kG
+                      ? reinterpret_cast<TcWarp*>(smem_raw + tc_off) + (threadIdx.x >> 5)
+                      : nullptr;
     int* sweep_of = sm.sweep_of;
     int* band_of = sm.band_of;
     const int warp = threadIdx.x >> 5;
@@ -833,29 +966,29 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
                     (sp->nout > 0 && sp->out_row0 < b_hi && sp->out_row0 + sp->nout > b_lo) || (rows - 1 < b_hi);
                 if constexpr (KIND != KIND_ABS) {
                     run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true>(special, sp, si, band, to_ring, to_global, A, sm,
-                                                                   warp);
+                                                                   warp, tcw);
                 } else if (!TAGS || tag_row < 0) {
                     run_band_s<KIND, R, U, DIM, NWMAX, 1, 0, true>(special, sp, si, band, to_ring, to_global, A, sm,
-                                                                   warp);
+                                                                   warp, tcw);
                 } else if constexpr (TAGS) {
                     const bool vf = sp->axis == 0;
                     if (b_hi <= tag_row) {
                         run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true>(special, sp, si, band, to_ring, to_global, A,
-                                                                       sm, warp);
+                                                                       sm, warp, tcw);
                     } else if (b_lo > tag_row) {
                         if (vf)
                             run_band_s<KIND, R, U, DIM, NWMAX, 2, 1, true>(special, sp, si, band, to_ring, to_global,
-                                                                           A, sm, warp);
+                                                                           A, sm, warp, tcw);
                         else
                             run_band_s<KIND, R, U, DIM, NWMAX, 2, 1, false>(special, sp, si, band, to_ring, to_global,
-                                                                            A, sm, warp);
+                                                                            A, sm, warp, tcw);
                     } else {
                         if (vf)
                             run_band_s<KIND, R, U, DIM, NWMAX, 2, 2, true>(special, sp, si, band, to_ring, to_global,
-                                                                           A, sm, warp);
+                                                                           A, sm, warp, tcw);
                         else
                             run_band_s<KIND, R, U, DIM, NWMAX, 2, 2, false>(special, sp, si, band, to_ring, to_global,
-                                                                            A, sm, warp);
+                                                                            A, sm, warp, tcw);
                     }
                 }
             }
@@ -878,7 +1011,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__
 template <int KIND, int R, int U, int DIM, bool TAGS>
 static cudaError_t setup_one(int* nb_out) {
     constexpr int NWMAX = (KIND != KIND_ABS || TAGS) ? 2 : 1;
-    constexpr size_t smem = sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>);
+    constexpr size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>();
     static int nb = 0;
     if (nb == 0) {
         cudaError_t e = cudaFuncSetAttribute(sweep_kernel<KIND, R, U, DIM, TAGS>,
@@ -895,7 +1028,7 @@ static cudaError_t setup_one(int* nb_out) {
 template <int KIND, int R, int U, int DIM, bool TAGS>
 static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blocks, cudaStream_t st) {
     constexpr int NWMAX = (KIND != KIND_ABS || TAGS) ? 2 : 1;
-    constexpr size_t smem = sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>);
+    constexpr size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>();
     int nb = 0;
     cudaError_t e = setup_one<KIND, R, U, DIM, TAGS>(&nb);
     if (e != cudaSuccess) return e;
@@ -925,6 +1058,7 @@ cudaError_t sweep_prepare(int kind, int d, bool tags) {
         if (tags) return setup_one<KIND_ABS, kIntR, kIntU, 1, true>(&nb);
         return setup_one<KIND_ABS, kIntR, kIntU, 1, false>(&nb);
     }
+    if (kind == KIND_EUCB) return setup_one<KIND_EUCB, 1, 2, 64, false>(&nb);
     if (kind == KIND_EUCF) {
         if (d == 12) return setup_one<KIND_EUCF, kEucR, kEucU, 12, false>(&nb);
         if (d == 64) return setup_one<KIND_EUCF, 1, 2, 64, false>(&nb);
@@ -941,6 +1075,7 @@ cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num
         if (tags) return launch_one<KIND_ABS, kIntR, kIntU, 1, true>(A, num_sms, max_blocks, st);
         return launch_one<KIND_ABS, kIntR, kIntU, 1, false>(A, num_sms, max_blocks, st);
     }
+    if (kind == KIND_EUCB) return launch_one<KIND_EUCB, 1, 2, 64, false>(A, num_sms, max_blocks, st);
     if (kind == KIND_EUCF) {
         if (d == 12) return launch_one<KIND_EUCF, kEucR, kEucU, 12, false>(A, num_sms, max_blocks, st);
         if (d == 64) return launch_one<KIND_EUCF, 1, 2, 64, false>(A, num_sms, max_blocks, st);
