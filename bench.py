@@ -200,6 +200,11 @@ def run_ours(args):
 
     if args.no_graph:
         dtw.set_option(dtw.OPT_GRAPH, 0)
+    tuned = None
+    if args.workload == "int_pair" and not args.no_tune:
+        # the library's autotuner picks the lane block and the base-case cutoff for this size
+        from paper_2008_02734_b300 import autotune
+        tuned = autotune.tune(WORKLOADS["int_pair"][1], WORKLOADS["int_pair"][2], reps=3)
     X, Y = make_inputs(args.workload, seed_offset=rank)
     M, N = len(X), len(Y)
     Xd = torch.from_numpy(X).to(dev)
@@ -315,7 +320,9 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "i32" if args.workload == "int_pair" else "f32-cost/f64-dp",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][0], "M": M, "N": N, "pairs_per_rank": 1,
-                   "parallelism": f"replicas{ws}", "l2": "flushed between steps (256 MiB write outside the events)"},
+                   "parallelism": f"replicas{ws}", "l2": "flushed between steps (256 MiB write outside the events)",
+                   "autotuned": None if tuned is None else {"sweep_variant": tuned["variant"],
+                                                           "base_area": tuned["base_area"]}},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "host_p50": float(np.percentile(host_ms, 50))},
         "e2e": {"value": e2e_value, "unit": "GCUPS", "h2d_bytes_per_step": (M + N) * 4,
@@ -437,9 +444,11 @@ def run_serving_workload(args):
     cells = float(sum(r.M * r.N for r in reqs))
     bufs = [(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()) for x, y in feats]
     torch.cuda.synchronize()
+    # d = 64 requests use the BF16 tensor-core cost tiles with the compensated FP32 DP
+    bf16 = [r.d == 64 and not args.exact for r in reqs]
     # warm the engines of both groups
     for k in range(min(4, len(reqs))):
-        t, _, keep = dtw.submit(*bufs[k])
+        t, _, keep = dtw.submit(*bufs[k], cost_bf16=bf16[k])
         dtw.wait(t)
     pend = {}
     lat = []
@@ -448,7 +457,7 @@ def run_serving_workload(args):
     while nxt < len(reqs) or pend:
         now = time.perf_counter() - t0
         while nxt < len(reqs) and reqs[nxt].arrival_s <= now:
-            t, path, keep = dtw.submit(*bufs[nxt])
+            t, path, keep = dtw.submit(*bufs[nxt], cost_bf16=bf16[nxt])
             pend[t] = (time.perf_counter(), path, keep, nxt)
             nxt += 1
         for t in list(pend):
@@ -470,8 +479,9 @@ def run_serving_workload(args):
     line = {"metric": METRIC, "value": cells / makespan / 1e9, "unit": "GCUPS", "n_gpus": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
             "config": {"workload": f"serving stream: {args.requests} Poisson arrivals at {args.rate} Hz, lengths "
-                                   f"log-uniform [500,{args.max_len}], d 12 or 64, exact form, admission budget "
-                                   f"{args.budget_gb} GB", "problem_cells": cells},
+                                   f"log-uniform [500,{args.max_len}], d 12 (FP32 cost, FP64 DP) or 64 ("
+                                   + ("exact form" if args.exact else "BF16 tensor-core cost, compensated FP32 DP")
+                                   + f"), admission budget {args.budget_gb} GB", "problem_cells": cells},
             "latency_ms": _percentiles(lat), "makespan_s": makespan,
             "vs_plain_gpu": {"plain_gcups_one_request": plain_gcups,
                              "serial_plain_makespan_s_est": cells / plain_gcups / 1e9,
@@ -492,9 +502,11 @@ def main():
     ap.add_argument("--rate", type=float, default=100.0, help="arrival rate of the serving workload (Hz)")
     ap.add_argument("--max-len", type=int, default=20000, help="longest request of the serving workload")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="admission budget of the serving workload")
+    ap.add_argument("--exact", action="store_true", help="serving workload: exact form for d = 64 too")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 GPU comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default lane block and cutoff)")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the level loop from the host (the same kernels; profilers list every launch)")
     args = ap.parse_args()

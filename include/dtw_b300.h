@@ -228,10 +228,12 @@ enum dtw_option {
     DTW_OPT_BASE_AREA = 2,   /* boxes of at most this many cells finish in the base case */
     DTW_OPT_SPIN_LIMIT = 3,  /* polls before a device-side wait gives up (DTW_ETIMEOUT) */
     DTW_OPT_SKIP_PUBLISH = 4, /* test hook: one band never publishes (exercises DTW_ETIMEOUT) */
-    DTW_OPT_GRAPH = 5         /* 1 (default): the level loop of dtw_align / dtw_align_batch runs as one CUDA
+    DTW_OPT_GRAPH = 5,        /* 1 (default): the level loop of dtw_align / dtw_align_batch runs as one CUDA
                                  graph with a device-side loop condition (no host round trip per level);
                                  0: a host loop that reads the control block back after every level.
                                  DTW_OPT_TIMING on forces the host loop (it times every level). */
+    DTW_OPT_SWEEP_VARIANT = 6 /* integer-kind sweep lane block: 0 (default) 4 rows x 4 columns per lane and
+                                 step, 1: 2 x 4, 2: 8 x 4 (chosen by the autotuner in the Python package) */
 };
 DTW_API int dtw_set_option(int32_t key, int64_t value);
 

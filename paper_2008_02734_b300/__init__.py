@@ -32,7 +32,7 @@ def _form(dp_f32: bool, cost_bf16: bool) -> int:
     return (DP_F32_KAHAN if dp_f32 else 0) | (COST_BF16 if cost_bf16 else 0)
 
 OK, PENDING, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBUSY, EINTERNAL = 0, 1, -1, -2, -3, -4, -5, -6, -7
-OPT_TIMING, OPT_BASE_AREA, OPT_SPIN_LIMIT, OPT_SKIP_PUBLISH, OPT_GRAPH = 1, 2, 3, 4, 5
+OPT_TIMING, OPT_BASE_AREA, OPT_SPIN_LIMIT, OPT_SKIP_PUBLISH, OPT_GRAPH, OPT_SWEEP_VARIANT = 1, 2, 3, 4, 5, 6
 
 
 class DTWError(RuntimeError):

@@ -35,6 +35,7 @@ struct Ctx {
     int device = -1;
     dtw_stats stats = {};
     int use_graph = 1;
+    int variant = 0;  // integer sweep variant (rows per lane), see sweep_band_rows
     // cached executable graph of the level loop and the parameters it was built for
     struct LevelGraph {
         cudaGraphExec_t exec = nullptr;
@@ -116,7 +117,7 @@ int level_graph(Ctx& c, const std::vector<long long>& key, const SweepArgs& sa, 
         lg.exec = nullptr;
     }
     if (!lg.cap && cudaStreamCreateWithFlags(&lg.cap, cudaStreamNonBlocking) != cudaSuccess) return DTW_ECUDA;
-    if (sweep_prepare(kind, d, kind == KIND_ABS) != cudaSuccess) return DTW_ECUDA;
+    if (sweep_prepare(kind, d, kind == KIND_ABS, c.variant) != cudaSuccess) return DTW_ECUDA;
     cudaGraph_t g = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return DTW_ECUDA;
     int rc = DTW_OK;
@@ -135,7 +136,7 @@ int level_graph(Ctx& c, const std::vector<long long>& key, const SweepArgs& sa, 
         cudaGraph_t body = np.conditional.phGraph_out[0];
         e = cudaStreamBeginCaptureToGraph(lg.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = launch_sweep(kind, d, kind == KIND_ABS, sa, c.num_sms, 0, lg.cap);
+            cudaError_t e1 = launch_sweep(kind, d, kind == KIND_ABS, sa, c.num_sms, 0, lg.cap, c.variant);
             if (e1 == cudaSuccess) e1 = launch_split(sp, lg.cap);
             if (e1 == cudaSuccess) e1 = launch_plan(pn, lg.cap);
             if (e1 == cudaSuccess) e1 = launch_level_cond(ctl, h, max_levels, lg.cap);
@@ -335,8 +336,8 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     // size the next sweep's grid).
     const int mode = want_path ? MODE_ALIGN : MODE_COST;
     const int halo = kind == KIND_ABS ? kSplitHalo : 0;
-    const int U = sweep_block_cols(kind, d);
-    const int BR = sweep_band_rows(kind, d);
+    const int U = sweep_block_cols(kind, d, c.variant);
+    const int BR = sweep_band_rows(kind, d, c.variant);
     const int G = sweep_group_bands();
     Box* cur = boxA;
     Box* nxt = boxB;
@@ -371,7 +372,8 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
                     L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, cur};
         const std::vector<long long> key{(long long)(uintptr_t)ws, (long long)L.total, L.cap_box, L.cap_base,
                                          L.cap_sweeps, L.cap_buf, L.cap_out, L.cap_items, kind, d, base_area,
-                                         c.spin_limit, c.skip_publish, c.num_sms, max_levels, (long long)L.ctl};
+                                         c.spin_limit, c.skip_publish, c.num_sms, max_levels, (long long)L.ctl,
+                                         c.variant};
         cudaGraphExec_t ex = nullptr;
         int grc = level_graph(c, key, sa, sp, pn, d_ctl, kind, d, max_levels, &ex);
         if (grc != DTW_OK) return grc;
@@ -387,7 +389,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         cudaEvent_t s0 = nullptr, s1 = nullptr;
         if (c.timing) s0 = T.mark();
         // integer levels may mix tagged and untagged boxes
-        e = launch_sweep(kind, d, mode == MODE_ALIGN && kind == KIND_ABS, sa, c.num_sms, hc.n_tickets, st);
+        e = launch_sweep(kind, d, mode == MODE_ALIGN && kind == KIND_ABS, sa, c.num_sms, hc.n_tickets, st, c.variant);
         ++launches;
         if (c.timing) s1 = T.mark();
         ++sweeps;
@@ -652,6 +654,10 @@ int dtw_set_option(int32_t key, int64_t value) {
             return DTW_OK;
         case DTW_OPT_SKIP_PUBLISH: c.skip_publish = value; return DTW_OK;
         case DTW_OPT_GRAPH: c.use_graph = value != 0; return DTW_OK;
+        case DTW_OPT_SWEEP_VARIANT:
+            if (value < 0 || value >= kSweepVariants) return DTW_EINVAL;
+            c.variant = (int)value;
+            return DTW_OK;
         default: return DTW_EINVAL;
     }
 }

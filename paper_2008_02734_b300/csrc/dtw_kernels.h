@@ -21,14 +21,16 @@ struct SweepArgs {
 };
 
 // Sweep variants
-int sweep_block_cols(int kind, int d);  // U
-int sweep_band_rows(int kind, int d);   // 32*R
+// variant (integer kind): 0 R=4 (default), 1 R=2, 2 R=8 rows per lane; U=4 columns.
+constexpr int kSweepVariants = 3;
+int sweep_block_cols(int kind, int d, int variant = 0);  // U
+int sweep_band_rows(int kind, int d, int variant = 0);   // 32*R
 int sweep_group_bands();                // bands per ticket (compute warps per block)
 // max_blocks > 0 caps the grid (one block per ticket suffices); 0: a full persistent grid.
 cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, long long max_blocks,
-                         cudaStream_t st);
+                         cudaStream_t st, int variant = 0);
 // One-time launch setup of the variant (attributes, occupancy); must precede a stream capture.
-cudaError_t sweep_prepare(int kind, int d, bool tags);
+cudaError_t sweep_prepare(int kind, int d, bool tags, int variant = 0);
 
 // Level planning modes
 constexpr int MODE_ALIGN = 0;  // per box: two half sweeps, or one tagged sweep (BOX_TAG)

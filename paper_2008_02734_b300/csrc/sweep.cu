@@ -1046,15 +1046,20 @@ static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blo
 // hand-off work (shuffles, ring, boundary stores) is paid once per block.
 constexpr int kIntR = DTW_INT_R, kIntU = DTW_INT_U;
 constexpr int kEucR = DTW_EUC_R, kEucU = DTW_EUC_U;
-int sweep_block_cols(int kind, int d) { return kind == KIND_ABS ? kIntU : (d == 12 ? kEucU : 2); }
-int sweep_band_rows(int kind, int d) {
-    return kind == KIND_ABS ? 32 * kIntR : (d == 12 ? 32 * kEucR : (d == 64 ? 32 : 64));
+// Integer variants (selected at run time, e.g. by the autotuner): rows per lane.
+constexpr int kIntRVar[kSweepVariants] = {kIntR, 2, 8};
+int sweep_block_cols(int kind, int d, int variant) { return kind == KIND_ABS ? kIntU : (d == 12 ? kEucU : 2); }
+int sweep_band_rows(int kind, int d, int variant) {
+    if (kind == KIND_ABS) return 32 * kIntRVar[(unsigned)variant < (unsigned)kSweepVariants ? variant : 0];
+    return d == 12 ? 32 * kEucR : (d == 64 ? 32 : 64);
 }
 int sweep_group_bands() { return kG; }
 
-cudaError_t sweep_prepare(int kind, int d, bool tags) {
+cudaError_t sweep_prepare(int kind, int d, bool tags, int variant) {
     int nb = 0;
     if (kind == KIND_ABS) {
+        if (variant == 1) return tags ? setup_one<KIND_ABS, 2, kIntU, 1, true>(&nb) : setup_one<KIND_ABS, 2, kIntU, 1, false>(&nb);
+        if (variant == 2) return tags ? setup_one<KIND_ABS, 8, kIntU, 1, true>(&nb) : setup_one<KIND_ABS, 8, kIntU, 1, false>(&nb);
         if (tags) return setup_one<KIND_ABS, kIntR, kIntU, 1, true>(&nb);
         return setup_one<KIND_ABS, kIntR, kIntU, 1, false>(&nb);
     }
@@ -1070,8 +1075,14 @@ cudaError_t sweep_prepare(int kind, int d, bool tags) {
 }
 
 cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, long long max_blocks,
-                         cudaStream_t st) {
+                         cudaStream_t st, int variant) {
     if (kind == KIND_ABS) {
+        if (variant == 1)
+            return tags ? launch_one<KIND_ABS, 2, kIntU, 1, true>(A, num_sms, max_blocks, st)
+                        : launch_one<KIND_ABS, 2, kIntU, 1, false>(A, num_sms, max_blocks, st);
+        if (variant == 2)
+            return tags ? launch_one<KIND_ABS, 8, kIntU, 1, true>(A, num_sms, max_blocks, st)
+                        : launch_one<KIND_ABS, 8, kIntU, 1, false>(A, num_sms, max_blocks, st);
         if (tags) return launch_one<KIND_ABS, kIntR, kIntU, 1, true>(A, num_sms, max_blocks, st);
         return launch_one<KIND_ABS, kIntR, kIntU, 1, false>(A, num_sms, max_blocks, st);
     }

@@ -51,6 +51,7 @@ def _defaults(cuda_device):
     dtw.set_option(dtw.OPT_BASE_AREA, 16384)
     dtw.set_option(dtw.OPT_SPIN_LIMIT, 1 << 22)
     dtw.set_option(dtw.OPT_SKIP_PUBLISH, -1)
+    dtw.set_option(dtw.OPT_SWEEP_VARIANT, 0)
 
 
 SHAPES = [(1, 1), (1, 9), (9, 1), (2, 2), (3, 7), (7, 13), (33, 65), (64, 64), (65, 63), (100, 37),
@@ -330,3 +331,25 @@ def test_cost_bf16_rejects_other_dims():
     with pytest.raises(dtw.DTWError) as ei:
         dtw.align(_cuda(X), _cuda(Y), cost_bf16=True)
     assert ei.value.status == dtw.EINVAL
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("M,N", [(3000, 3500), (257, 1300), (2000, 1800)])
+def test_int_sweep_variants_bit_exact(variant, M, N):
+    """Every lane block of the integer sweep gives the canonical path."""
+    dtw.set_option(dtw.OPT_SWEEP_VARIANT, variant)
+    X, Y = synth.int_pair(M + 11 * N, M, N)
+    check_int(X, Y)
+    rng = np.random.default_rng(M)
+    Xt = rng.integers(0, 3, M).astype(np.int32)
+    Yt = rng.integers(0, 3, N).astype(np.int32)
+    check_int(Xt, Yt)
+
+
+def test_autotuner_applies_a_candidate():
+    from paper_2008_02734_b300 import autotune
+    r = autotune.tune(1500, 1700, base_areas=(4096, 16384), reps=2)
+    assert r["variant"] in (0, 1, 2) and r["base_area"] in (4096, 16384)
+    assert len(r["table"]) == 6 and all(t["ms"] > 0 for t in r["table"])
+    X, Y = synth.int_pair(4, 2500, 2100)
+    check_int(X, Y)
