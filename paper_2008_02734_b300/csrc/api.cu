@@ -338,7 +338,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     const int halo = kind == KIND_ABS ? kSplitHalo : 0;
     const int U = sweep_block_cols(kind, d, c.variant);
     const int BR = sweep_band_rows(kind, d, c.variant);
-    const int G = sweep_group_bands();
+    const int G = sweep_group_bands(kind);
     Box* cur = boxA;
     Box* nxt = boxB;
     int levels = 0, sweeps = 0;

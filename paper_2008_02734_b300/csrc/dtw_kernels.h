@@ -25,7 +25,7 @@ struct SweepArgs {
 constexpr int kSweepVariants = 3;
 int sweep_block_cols(int kind, int d, int variant = 0);  // U
 int sweep_band_rows(int kind, int d, int variant = 0);   // 32*R
-int sweep_group_bands();                // bands per ticket (compute warps per block)
+int sweep_group_bands(int kind);  // bands per ticket (compute warps per block)
 // max_blocks > 0 caps the grid (one block per ticket suffices); 0: a full persistent grid.
 cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, long long max_blocks,
                          cudaStream_t st, int variant = 0);

@@ -136,7 +136,7 @@ extern "C" int dtw_cost_noalloc(const void* X, int64_t M, const void* Y, int64_t
     if (e == cudaSuccess && kind == KIND_ABS) e = launch_int_range_check(pairs, 1, (int)hi, minmax, ctl, st);
     // the plan resets the band ticket and assigns this call's epochs
     PlanArgs pa{box, 1, pairs, MODE_COST, kind, 0, sweep_block_cols(kind, d), sweep_band_rows(kind, d),
-                sweep_group_bands(), sweep, ctl,
+                sweep_group_bands(kind), sweep, ctl,
                 1, kBufWords, 0, nullptr, 0, false, nullptr};
     if (e == cudaSuccess) e = launch_plan(pa, st);
     SweepArgs sa{sweep, ctl, reinterpret_cast<unsigned long long*>(base + kOffBuf), nullptr, res, d, 1 << 22, -1};

@@ -349,7 +349,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
 
     // ---- 2. one level for every active pair
     const int halo = kind == KIND_ABS ? kSplitHalo : 0;
-    const int U = sweep_block_cols(kind, d), BR = sweep_band_rows(kind, d), G = sweep_group_bands();
+    const int U = sweep_block_cols(kind, d), BR = sweep_band_rows(kind, d), G = sweep_group_bands(kind);
     int* d_boxdone = reinterpret_cast<int*>(ws + L.boxdone);
     Sweep* d_sweeps = reinterpret_cast<Sweep*>(ws + L.sweeps);
     SweepRes* d_sres = reinterpret_cast<SweepRes*>(ws + L.sres);

@@ -12,9 +12,9 @@
 // last cell's value leaves the SM: the D matrix itself is never stored (linear
 // memory, Section 3.2).
 //
-// Strips.  A thread block has kG compute warps and one loader warp.  It takes
-// tickets of kG consecutive bands of the level (band numbering runs through
-// the level's sweeps in order, top band first), so a block usually holds kG
+// Strips.  A thread block has G compute warps and one loader warp.  It takes
+// tickets of G consecutive bands of the level (band numbering runs through
+// the level's sweeps in order, top band first), so a block usually holds G
 // adjacent bands of one sweep, or several short sweeps side by side.  Warp g
 // hands its band's last row to warp g+1 through a ring of column blocks in
 // shared memory, published with release/acquire progress counters: the
@@ -63,8 +63,20 @@ namespace dtwb {
 
 namespace {
 
-constexpr int kG = 4;                    // compute warps (bands) per block
-constexpr int kThreads = 32 * (kG + 1);  // + the loader warp
+// Compute warps (bands) per block, G: integer kind 2, Euclidean kinds 4.  An
+// integer step is short, so a level's few bands do better spread over more
+// SMs; the longer Euclidean steps gain from four warps sharing a frame stream.
+#ifndef DTW_SWEEP_G_INT
+#define DTW_SWEEP_G_INT 2
+#endif
+#ifndef DTW_SWEEP_G_EUC
+#define DTW_SWEEP_G_EUC 4
+#endif
+template <int KIND>
+__host__ __device__ constexpr int group_of() { return KIND == KIND_ABS ? DTW_SWEEP_G_INT : DTW_SWEEP_G_EUC; }
+template <int KIND>
+__host__ __device__ constexpr int threads_of() { return 32 * (group_of<KIND>() + 1); }  // + the loader warp
+constexpr int kGMax = 8;  // the frame ring partition covers up to 8 warps
 constexpr int URS = 64;                  // slots (column blocks) of a row ring
 #ifndef DTW_SWEEP_KC
 #define DTW_SWEEP_KC 8
@@ -278,7 +290,7 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
 // reader (cons).
 //
 // Warps of a block that belong to the same sweep read one frame stream: the
-// ring of the first of them (ystream[g]).  The frame region of kYSlots column
+// ring of the first of them (ystream[g]).  The frame region of kYSlotsOf(G) column
 // blocks is split among the block's streams when the block takes a ticket.  A
 // stream read by w warps gets yslots(w) slots: a reader lags the warp above it
 // by at most 40 steps when it waits on it, so the stream's first reader is at
@@ -286,10 +298,11 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
 // plus a group in use; the loader's next round (chunk(w) blocks) must fit
 // beside all that, otherwise the first reader could wait on the loader, the
 // loader on the last reader and the last reader, through the chain of row
-// rings, on the first one.  w = 4 or 3: 256 slots, rounds of 32; w = 2: 128, 32;
-// w = 1: 64, 16.  Every partition of four warps fits in 320 slots.
-constexpr int kYSlots = 320;
-__host__ __device__ constexpr int yslots(int w) { return w >= 3 ? 256 : (w == 2 ? 128 : 64); }
+// rings, on the first one.  w = 5..8: 512 slots, rounds of 32; w = 4 or 3:
+// 256, 32; w = 2: 128, 32; w = 1: 64, 16.  Every partition of four warps fits
+// in 320 slots, every partition of eight in 1024.
+__host__ __device__ constexpr int kYSlotsOf(int G) { return G > 4 ? 1024 : 320; }
+__host__ __device__ constexpr int yslots(int w) { return w >= 5 ? 512 : (w >= 3 ? 256 : (w == 2 ? 128 : 64)); }
 __host__ __device__ constexpr int ychunk(int w) { return w >= 2 ? 32 : 16; }
 
 // A frame ring slot holds the U column frames of one block; lanes read the
@@ -301,14 +314,15 @@ struct FrameSlot {
     static constexpr int W = (U * YW) % 4 != 0 || ((U * YW) / 4) % 2 == 1 ? U * YW : U * YW + 4;
 };
 
-template <int U, int NWMAX, int YW>
+template <int U, int NWMAX, int YW, int G>
 struct StripSmem {
+    static_assert(G >= 1 && G <= kGMax, "compute warps per block");
     static constexpr int YSW = FrameSlot<U, YW>::W;  // words per frame ring slot
-    __align__(16) uint32_t uring[kG][URS * U * NWMAX];
-    __align__(16) uint32_t yring[YW > 0 ? kYSlots * YSW : 4];
-    int uprog[kG], ucons[kG], yprog[kG], ycons[kG];
-    int ybase[kG], yrs[kG], ychb[kG];  // per stream: first slot, slots, blocks per loader round
-    int sweep_of[kG], band_of[kG], ystream[kG];
+    __align__(16) uint32_t uring[G][URS * U * NWMAX];
+    __align__(16) uint32_t yring[YW > 0 ? kYSlotsOf(G) * YSW : 4];
+    int uprog[G], ucons[G], yprog[G], ycons[G];
+    int ybase[G], yrs[G], ychb[G];  // per stream: first slot, slots, blocks per loader round
+    int sweep_of[G], band_of[G], ystream[G];
     long long ticket;
     int stop;
 };
@@ -344,10 +358,10 @@ struct ColFrame<KIND_EUCF, 64> {
 // per-lane activity tests.
 template <int KIND, int R, int U, int DIM, int NWMAX, int NW, int TAGM, bool VF, bool SPECIAL>
 __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_idx, int band, bool to_ring,
-                                      bool to_global, const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>& sm,
+                                      bool to_global, const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>& sm,
                                       int g, TcWarp* tc) {
     using Acc = typename AccOf<KIND>::T;
-    using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>;
+    using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>;
     constexpr int YW = FrameWords<KIND, DIM>::v;
     // BF16 tensor-core form: one row per lane, 16 column blocks of 2 per tile
     constexpr bool TC = KIND == KIND_EUCB;
@@ -380,6 +394,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     }
 
     uint32_t* rin = sm.uring[g];
+    constexpr int kG = group_of<KIND>();
     uint32_t* rout = sm.uring[g + 1 < kG ? g + 1 : g];
     const int ys = sm.ystream[g];
     constexpr int YSW = SM::YSW;
@@ -552,18 +567,30 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     const bool w31_ring = to_ring && lane == 31, w31_global = to_global && lane == 31;
     // warp-uniform: release what the previous groups read and wrote, wait for
     // the blocks this group reads, and for room for the blocks it writes
+    int uavail = 0, yavail = 0;  // blocks known to be in the row ring / the frame ring
     auto sync_group = [&](int s0) {
         if (s0 > 0) {
-            __syncwarp();
+            // row ring: only lane 0's part of each (warp-wide) slot load is used, and
+            // its own release orders it
             st_release_cta_if(lane == 0 && has_above, &sm.ucons[g], min(s0 + 1, nblk));
-            if constexpr (YW > 0) st_release_cta_if(lane == 0 && s0 > 31, &sm.ycons[g], min(s0 - 30, nblk));
+            // frame ring: every lane reads slots, so the warp synchronises first;
+            // every 16 steps (the rings leave room for that staleness)
+            if constexpr (YW > 0) {
+                if ((s0 & 15) == 0 && s0 > 31) {
+                    __syncwarp();
+                    st_release_cta_if(lane == 0, &sm.ycons[g], min(s0 - 30, nblk));
+                }
+            }
             st_release_cta_if(w31_ring && s0 > 31, &sm.uprog[g + 1 < kG ? g + 1 : g],
                               min(s0 - 31, nblk));
         }
         if (s0 < nblk) {  // lane 0 reads blocks up to s0 + KC (the last one ahead of time)
             const int need = min(s0 + KC + 1, nblk);
-            if (has_above) wait_counter(&sm.uprog[g], need, A.ctl, A.spin_limit, band, gave_up, ws);
-            if constexpr (YW > 0) wait_counter(&sm.yprog[ys], need, A.ctl, A.spin_limit, band, gave_up, ws);
+            if (has_above && need > uavail)
+                uavail = wait_counter(&sm.uprog[g], need, A.ctl, A.spin_limit, band, gave_up, ws);
+            if constexpr (YW > 0) {
+                if (need > yavail) yavail = wait_counter(&sm.yprog[ys], need, A.ctl, A.spin_limit, band, gave_up, ws);
+            }
         }
         if (to_ring) {  // this group writes blocks up to s0 + KC - 32
             const int last = s0 + KC - 32;
@@ -721,12 +748,13 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
 // warp: a round that can do nothing sleeps briefly, and a bounded number of
 // idle rounds ends in ERR_TIMEOUT.
 template <int KIND, int U, int DIM, int NWMAX, int NW>
-__device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>& sm) {
-    using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>;
+__device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>& sm) {
+    using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>;
     constexpr int YW = FrameWords<KIND, DIM>::v;
     constexpr int SLOT = U * NWMAX;
     constexpr int FB = 4 * YW;  // bytes per frame
     static_assert(32 % U == 0, "a round of 32 boundary columns covers whole blocks");
+    constexpr int kG = group_of<KIND>();
     const int lane = threadIdx.x & 31;
     int ynext[kG], yend[kG], ypend[kG];  // blocks issued, to issue, issued in the round in flight
 #pragma unroll
@@ -859,7 +887,7 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
 template <int KIND, int R, int U, int DIM, int NWMAX, int NW, int TAGM, bool VF>
 __device__ __forceinline__ void run_band_s(bool special, const Sweep* sp, int si, int band, bool to_ring,
                                            bool to_global, const SweepArgs& A,
-                                           StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>& sm, int g, TcWarp* tc) {
+                                           StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>& sm, int g, TcWarp* tc) {
     if (special) run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, true>(sp, si, band, to_ring, to_global, A, sm, g, tc);
     else run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, false>(sp, si, band, to_ring, to_global, A, sm, g, tc);
 }
@@ -868,8 +896,8 @@ __device__ __forceinline__ void run_band_s(bool special, const Sweep* sp, int si
 // one TcWarp per band warp.
 template <int KIND, int U, int NWMAX, int DIM>
 constexpr size_t strip_smem_bytes() {
-    constexpr size_t base = (sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>) + 127) & ~(size_t)127;
-    return base + (KIND == KIND_EUCB ? kG * sizeof(TcWarp) : 0);
+    constexpr size_t base = (sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>) + 127) & ~(size_t)127;
+    return base + (KIND == KIND_EUCB ? group_of<KIND>() * sizeof(TcWarp) : 0);
 }
 
 // Index of the sweep holding level band gb: the last sweep whose band_begin is
@@ -887,9 +915,10 @@ __device__ __forceinline__ int find_sweep(const Sweep* sweeps, int n_sweeps, lon
 // TAGS: the launch may contain tagged sweeps (integer kind), whose rows carry
 // two payload words per column; untagged integer sweeps use one.
 template <int KIND, int R, int U, int DIM, bool TAGS>
-__global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__ SweepArgs A) {
+__global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_constant__ SweepArgs A) {
     constexpr int NWMAX = (KIND != KIND_ABS || TAGS) ? 2 : 1;
-    using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v>;
+    constexpr int kG = group_of<KIND>();
+    using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM& sm = *reinterpret_cast<SM*>(smem_raw);
     constexpr size_t tc_off = (sizeof(SM) + 127) & ~(size_t)127;
@@ -1018,7 +1047,7 @@ static cudaError_t setup_one(int* nb_out) {
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<KIND, R, U, DIM, TAGS>, kThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<KIND, R, U, DIM, TAGS>, threads_of<KIND>(), smem);
         nb = n < 1 ? 1 : n;
     }
     *nb_out = nb;
@@ -1035,7 +1064,7 @@ static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blo
     long long grid = (long long)num_sms * nb;
     if (max_blocks > 0 && max_blocks < grid) grid = max_blocks;
     if (max_blocks < 0 || grid < 1) grid = 1;
-    sweep_kernel<KIND, R, U, DIM, TAGS><<<(unsigned)grid, kThreads, smem, st>>>(A);
+    sweep_kernel<KIND, R, U, DIM, TAGS><<<(unsigned)grid, threads_of<KIND>(), smem, st>>>(A);
     return cudaGetLastError();
 }
 
@@ -1053,7 +1082,7 @@ int sweep_band_rows(int kind, int d, int variant) {
     if (kind == KIND_ABS) return 32 * kIntRVar[(unsigned)variant < (unsigned)kSweepVariants ? variant : 0];
     return d == 12 ? 32 * kEucR : (d == 64 ? 32 : 64);
 }
-int sweep_group_bands() { return kG; }
+int sweep_group_bands(int kind) { return kind == KIND_ABS ? group_of<KIND_ABS>() : group_of<KIND_EUC>(); }
 
 cudaError_t sweep_prepare(int kind, int d, bool tags, int variant) {
     int nb = 0;
