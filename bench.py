@@ -63,7 +63,7 @@ def measured_peaks():
     return {"sm_max_mhz": 2032.0, "hbm_gbs": 6400.0}, "fallback"
 
 
-SWEEP_SRC = os.path.join(ROOT, "paper_2008_02734_b300", "csrc", "sweep.cu")
+SWEEP_SRC = [os.path.join(ROOT, "paper_2008_02734_b300", "csrc", f) for f in ("sweep.cu", "dtw_common.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_kernel_int_pair_traffic.json")
 
 
@@ -74,8 +74,11 @@ def sweep_traffic():
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f)
-        with open(SWEEP_SRC, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        h = hashlib.sha256()
+        for src in SWEEP_SRC:
+            with open(src, "rb") as f:
+                h.update(f.read())
+        sha = h.hexdigest()
     except (OSError, ValueError):
         return None, "no capture"
     if rec.get("source_sha256") != sha:
@@ -396,9 +399,26 @@ def run_batch_workload(args):
     return 0
 
 
+GOLDEN_MFCC = os.path.join(ROOT, "tests", "golden", "mfcc_pair_60000x75000.txt")
+
+
+def golden_mfcc_cost():
+    """The oracle's optimal cost of the precision workload, stored by
+    tests/golden/make_mfcc_pair_cost.py (oracle 2, FP64 throughout)."""
+    try:
+        with open(GOLDEN_MFCC) as f:
+            rows = [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")]
+        return float(rows[-1].split("|")[3])
+    except (OSError, IndexError, ValueError):
+        return None
+
+
 def run_precision_workload(args):
     """The orchestral-length pair: 60000 x 64-d MFCC-like frames vs a 75000-frame
-    warp plus noise, exact form (FP32 frame cost, FP64 accumulation)."""
+    warp plus noise, in each precision form: FP32 frame cost with FP64
+    accumulation (exact form), FP32 cost with compensated FP32 accumulation, and
+    BF16 tensor-core cost tiles (FP32 accumulation) with compensated FP32 DP.
+    Each form's optimal cost is set against the FP64 oracle's."""
     import torch
 
     import paper_2008_02734_b300 as dtw
@@ -407,23 +427,33 @@ def run_precision_workload(args):
     M, N = len(X), len(Y)
     Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
     stream = torch.cuda.current_stream()
-    for _ in range(max(args.warmup, 3)):
-        dtw.align(Xd, Yd)
-    ms = []
-    for _ in range(args.steps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        _, cost = dtw.align(Xd, Yd)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
-    line = {"metric": METRIC, "value": M * N / (np.mean(ms) / 1e3) / 1e9, "unit": "GCUPS", "n_gpus": 1,
-            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": float(np.mean(ms)),
+    c_ref = golden_mfcc_cost()
+    forms = {}
+    for name, kw, desc in (("f32cost_f64dp", {}, "FP32 frame cost, FP64 DP"),
+                           ("f32cost_f32kahan", {"dp_f32": True}, "FP32 frame cost, compensated FP32 DP"),
+                           ("bf16cost_f32kahan", {"cost_bf16": True},
+                            "BF16 tensor-core cost tiles (FP32 accumulation), compensated FP32 DP")):
+        for _ in range(max(args.warmup, 3)):
+            dtw.align(Xd, Yd, **kw)
+        ms = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, cost = dtw.align(Xd, Yd, **kw)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        forms[name] = {"form": desc, "ms": float(np.mean(ms)), "gcups": M * N / (np.mean(ms) / 1e3) / 1e9,
+                       "cost": cost, "rel_err_vs_oracle": None if c_ref is None else abs(cost - c_ref) / c_ref}
+    ex = forms["f32cost_f64dp"]
+    line = {"metric": METRIC, "value": ex["gcups"], "unit": "GCUPS", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ex["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-cost/f64-dp",
             "data": "synthetic",
             "config": {"workload": "orchestral-length pair: 60000 x 64-d MFCC-like vs 75000-frame warp + "
-                                   "N(0,0.1^2), exact form", "M": M, "N": N, "cost": cost},
-            "latency_ms": _percentiles(ms)}
+                                   "N(0,0.1^2); value is the FP32-cost/FP64-DP form", "M": M, "N": N,
+                       "oracle_cost": c_ref, "oracle_source": "tests/golden/mfcc_pair_60000x75000.txt"},
+            "forms": forms}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -292,7 +292,7 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
 // Warps of a block that belong to the same sweep read one frame stream: the
 // ring of the first of them (ystream[g]).  The frame region of kYSlotsOf(G) column
 // blocks is split among the block's streams when the block takes a ticket.  A
-// stream read by w warps gets yslots(w) slots: a reader lags the warp above it
+// stream read by w warps gets yslots(G, w) slots: a reader lags the warp above it
 // by at most 40 steps when it waits on it, so the stream's first reader is at
 // most 40(w-1) blocks ahead of its last one, which keeps 31 blocks (its lanes)
 // plus a group in use; the loader's next round (chunk(w) blocks) must fit
@@ -300,9 +300,15 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
 // loader on the last reader and the last reader, through the chain of row
 // rings, on the first one.  w = 5..8: 512 slots, rounds of 32; w = 4 or 3:
 // 256, 32; w = 2: 128, 32; w = 1: 64, 16.  Every partition of four warps fits
-// in 320 slots, every partition of eight in 1024.
-__host__ __device__ constexpr int kYSlotsOf(int G) { return G > 4 ? 1024 : 320; }
-__host__ __device__ constexpr int yslots(int w) { return w >= 5 ? 512 : (w >= 3 ? 256 : (w == 2 ? 128 : 64)); }
+// in 320 slots, every partition of eight in 1024.  That is the least room that
+// cannot deadlock; a lower band that runs late (its waits on the band above
+// make it lag by some 50 steps rather than 40) then holds back the first
+// reader.  With two warps per block (the integer kind, 16-byte slots) the
+// region is 512 slots and a stream gets 512 (two readers) or 256 (one).
+__host__ __device__ constexpr int kYSlotsOf(int G) { return G > 4 ? 1024 : (G > 2 ? 320 : 512); }
+__host__ __device__ constexpr int yslots(int G, int w) {
+    return G <= 2 ? (w >= 2 ? 512 : 256) : (w >= 5 ? 512 : (w >= 3 ? 256 : (w == 2 ? 128 : 64)));
+}
 __host__ __device__ constexpr int ychunk(int w) { return w >= 2 ? 32 : 16; }
 
 // A frame ring slot holds the U column frames of one block; lanes read the
@@ -973,9 +979,9 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
             for (int j = 0; j < kG; ++j) {
                 const int w = readers[j] > 0 ? readers[j] : 1;
                 sm.ybase[j] = base;
-                sm.yrs[j] = yslots(w);
+                sm.yrs[j] = yslots(kG, w);
                 sm.ychb[j] = ychunk(w);
-                if (readers[j] > 0) base += yslots(w);
+                if (readers[j] > 0) base += yslots(kG, w);
             }
         }
         __syncthreads();
