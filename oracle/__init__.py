@@ -15,6 +15,10 @@ Wraps ``dtw_oracle.c`` (plain C, FP64 / int64):
 * :func:`acc_matrix`-- whole forward D or backward B matrix (small cases), for
                        the split-cost identity of Lemma 2.
 * :func:`path_cost` -- sum of C along a path (re-scoring in FP64 / int64).
+* :func:`path_discrepancy` -- the alignment discrepancy of two warping paths
+                       (Section 4.3, Results): per cell of the first path, its
+                       distance along its row and along its column to the
+                       second path (plain Python over the cells; small paths).
 
 Parity status: every function here is pinned by ``tests/test_oracle.py``
 against brute-force enumeration, closed forms and invariants.
@@ -153,3 +157,25 @@ def path_cost(X, Y, path):
     if rc != 0:
         raise RuntimeError(f"oracle_path_cost failed: {rc}")
     return _cost(kind, c, ci)
+
+
+def path_discrepancy(P1, P2):
+    """Section 4.3 (Results): for every cell (i, j) of path P1, the row error is
+    min |j - k| over the cells (i, k) of path P2, and the column error is
+    min |i - k| over the cells (k, j) of P2.  Returns (row_errors, col_errors),
+    int64 arrays in P1's order.  Written from the definition: every P2 cell of
+    the row (column) is compared; a row or column P2 never visits gives -1."""
+    P1 = np.asarray(P1, dtype=np.int64).reshape(-1, 2)
+    P2 = np.asarray(P2, dtype=np.int64).reshape(-1, 2)
+    by_row, by_col = {}, {}
+    for i, k in P2:
+        by_row.setdefault(int(i), []).append(int(k))
+        by_col.setdefault(int(k), []).append(int(i))
+    row_err = np.empty(len(P1), dtype=np.int64)
+    col_err = np.empty(len(P1), dtype=np.int64)
+    for t, (i, j) in enumerate(P1):
+        ks = by_row.get(int(i))
+        row_err[t] = min(abs(int(j) - k) for k in ks) if ks else -1
+        ks = by_col.get(int(j))
+        col_err[t] = min(abs(int(i) - k) for k in ks) if ks else -1
+    return row_err, col_err

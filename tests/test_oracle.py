@@ -6,7 +6,10 @@
 * closed forms (identical series, constant series, a single row);
 * invariants: endpoints, step set, the path's cost equals D*, reversal and
   transposition invariance of D*, Lemma 2's split identity on every row, and the
-  work bound of Section 3.2 for oracle 2.
+  work bound of Section 3.2 for oracle 2;
+* the alignment discrepancy of Section 4.3 against hand-worked cases
+  (tests/golden/discrepancy.txt), against the run-extent closed form on random
+  monotone paths, and its zero and symmetry properties.
 """
 import math
 import os
@@ -248,3 +251,69 @@ def test_linmdtw_work_bound():
         assert cells <= 2 * M * N + (M + N) * math.log2(M + N)
         assert 1.6 < cells / (M * N) <= 2.1
         assert c == oracle.dtw(X, Y)[1]
+
+
+DISC_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "discrepancy.txt")
+
+
+def _pairs(s):
+    return np.array([[int(v) for v in c.split(",")] for c in s.split(";")], dtype=np.int64)
+
+
+def _disc_cases():
+    with open(DISC_GOLDEN) as f:
+        for ln in f:
+            ln = ln.strip()
+            if ln and not ln.startswith("#"):
+                name, M, N, p1, p2, re, ce = ln.split("|")
+                yield name, int(M), int(N), _pairs(p1), _pairs(p2), [int(v) for v in re.split(",")], \
+                    [int(v) for v in ce.split(",")]
+
+
+@pytest.mark.parametrize("case", list(_disc_cases()), ids=lambda c: c[0])
+def test_discrepancy_handworked(case):
+    name, M, N, P1, P2, re, ce = case
+    r, c = oracle.path_discrepancy(P1, P2)
+    assert r.tolist() == re and c.tolist() == ce
+
+
+def random_warping_path(rng, M, N):
+    """A seeded random warping path from (0,0) to (M-1,N-1) (test input)."""
+    i = j = 0
+    out = [(0, 0)]
+    while (i, j) != (M - 1, N - 1):
+        moves = [m for m in ((1, 1), (1, 0), (0, 1)) if i + m[0] < M and j + m[1] < N]
+        di, dj = moves[rng.integers(len(moves))]
+        i, j = i + di, j + dj
+        out.append((i, j))
+    return np.array(out, dtype=np.int64)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_discrepancy_closed_form_on_random_paths(seed):
+    """A warping path's cells in one row form one run [lo, hi] (steps never go
+    back), so the row error of (i, j) is max(0, lo_i - j, j - hi_i); likewise for
+    columns.  The oracle compares every cell and must agree."""
+    rng = np.random.default_rng(seed)
+    M, N = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+    P1, P2 = random_warping_path(rng, M, N), random_warping_path(rng, M, N)
+    lo = {int(i): int(P2[P2[:, 0] == i, 1].min()) for i in range(M)}
+    hi = {int(i): int(P2[P2[:, 0] == i, 1].max()) for i in range(M)}
+    clo = {int(j): int(P2[P2[:, 1] == j, 0].min()) for j in range(N)}
+    chi = {int(j): int(P2[P2[:, 1] == j, 0].max()) for j in range(N)}
+    r, c = oracle.path_discrepancy(P1, P2)
+    for t, (i, j) in enumerate(P1):
+        assert r[t] == max(0, lo[int(i)] - j, j - hi[int(i)])
+        assert c[t] == max(0, clo[int(j)] - i, i - chi[int(j)])
+
+
+def test_discrepancy_zero_and_symmetry():
+    """A path against itself has no error; swapping the roles of rows and
+    columns (transposing both paths) swaps row and column errors."""
+    rng = np.random.default_rng(7)
+    P1, P2 = random_warping_path(rng, 25, 31), random_warping_path(rng, 25, 31)
+    r, c = oracle.path_discrepancy(P1, P1)
+    assert not r.any() and not c.any()
+    r, c = oracle.path_discrepancy(P1, P2)
+    rt, ct = oracle.path_discrepancy(P1[:, ::-1], P2[:, ::-1])
+    assert (rt == c).all() and (ct == r).all()
