@@ -428,7 +428,7 @@ def run_precision_workload(args):
     Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
     stream = torch.cuda.current_stream()
     c_ref = golden_mfcc_cost()
-    forms = {}
+    forms, paths = {}, {}
     for name, kw, desc in (("f32cost_f64dp", {}, "FP32 frame cost, FP64 DP"),
                            ("f32cost_f32kahan", {"dp_f32": True}, "FP32 frame cost, compensated FP32 DP"),
                            ("bf16cost_f32kahan", {"cost_bf16": True},
@@ -439,12 +439,25 @@ def run_precision_workload(args):
         for _ in range(args.steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            _, cost = dtw.align(Xd, Yd, **kw)
+            path, cost = dtw.align(Xd, Yd, **kw)
             b.record(stream)
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
+        paths[name] = path
         forms[name] = {"form": desc, "ms": float(np.mean(ms)), "gcups": M * N / (np.mean(ms) / 1e3) / 1e9,
                        "cost": cost, "rel_err_vs_oracle": None if c_ref is None else abs(cost - c_ref) / c_ref}
+    # Section 4.3's alignment discrepancy of the BF16 form's path against the
+    # exact form's, as the share of errors within 1, 2, 22 and 43 frames (23 ms,
+    # 47 ms, 0.51 s and 1 s at the features' ~43 frames per second)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    err, emax = dtw.path_discrepancy(paths["bf16cost_f32kahan"], paths["f32cost_f64dp"], M, N)
+    b.record(stream)
+    torch.cuda.synchronize()
+    e = err.cpu().numpy().ravel()
+    disc = {"of": "bf16cost_f32kahan path vs f32cost_f64dp path", "cells": int(err.shape[1]), "max_frames": emax,
+            "within_frames": {str(f): float(np.mean(e <= f)) for f in (0, 1, 2, 22, 43)},
+            "call_ms": a.elapsed_time(b)}
     ex = forms["f32cost_f64dp"]
     line = {"metric": METRIC, "value": ex["gcups"], "unit": "GCUPS", "n_gpus": 1,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ex["ms"],
@@ -453,7 +466,7 @@ def run_precision_workload(args):
             "config": {"workload": "orchestral-length pair: 60000 x 64-d MFCC-like vs 75000-frame warp + "
                                    "N(0,0.1^2); value is the FP32-cost/FP64-DP form", "M": M, "N": N,
                        "oracle_cost": c_ref, "oracle_source": "tests/golden/mfcc_pair_60000x75000.txt"},
-            "forms": forms}
+            "forms": forms, "path_discrepancy": disc}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -175,6 +175,26 @@ DTW_API size_t dtw_footprint(int64_t M, int64_t N, int32_t d, int32_t cost_kind)
 DTW_API const char* dtw_strerror(int status);
 
 /*
+ * dtw_path_discrepancy -- the alignment discrepancy of two warping paths of the
+ * same M x N problem (Section 4.3, Results): for every cell (i, j) of path 1,
+ * its row error min |j - k| over the cells (i, k) of path 2 and its column error
+ * min |i - k| over the cells (k, j) of path 2.  Used to compare the paths of two
+ * precision forms, or a path that took another tie than the oracle's.
+ *   P1, P2     K1 x 2 / K2 x 2 int32 (i, j) pairs, row-major, each a warping path
+ *              from (0, 0) to (M-1, N-1) with steps (0,1), (1,0), (1,1); host or
+ *              device pointers; max(M, N) <= K <= M + N - 1
+ *   err_out    2*K1 int32, host or device: the row errors of P1's cells in path
+ *              order, then their column errors
+ *   max_out    host int32, the largest error (NULL: not wanted)
+ * The caller owns every buffer.  Returns DTW_OK; DTW_EINVAL for bad sizes or a
+ * path that is not a warping path of M x N (checked on the device; err_out is
+ * then unspecified); DTW_ENOMEM or DTW_ECUDA.  Blocks until the result is
+ * written.
+ */
+DTW_API int dtw_path_discrepancy(const int32_t* P1, int64_t K1, const int32_t* P2, int64_t K2, int64_t M, int64_t N,
+                                 int32_t* err_out, int32_t* max_out);
+
+/*
  * dtw_cost_noalloc -- D* of one pair, like dtw_cost, without allocating any
  * device memory.  The paper has no counterpart: this entry point exists for
  * callers that cannot call cudaMalloc -- a process whose device memory is fully

@@ -79,6 +79,7 @@ def _load():
         "dtw_get_stats": (ctypes.c_int, [vp]),
         "dtw_set_option": (ctypes.c_int, [i32, i64]),
         "dtw_cost_noalloc": (ctypes.c_int, [vp, i64, vp, i64, i32, i32, vp, vp]),
+        "dtw_path_discrepancy": (ctypes.c_int, [vp, i64, vp, i64, i64, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -107,7 +108,7 @@ def __getattr__(name):
 # exported names of the C ABI, for the symbol check
 ABI_FUNCTIONS = ("dtw_align", "dtw_cost", "dtw_align_batch", "dtw_submit", "dtw_poll", "dtw_set_stream",
                  "dtw_set_budget", "dtw_set_arena", "dtw_footprint", "dtw_strerror", "dtw_get_stats",
-                 "dtw_set_option", "dtw_cost_noalloc")
+                 "dtw_set_option", "dtw_cost_noalloc", "dtw_path_discrepancy")
 
 
 def _strerror(status: int) -> str:
@@ -222,6 +223,26 @@ def cost_noalloc(X, Y):
     st = ctypes.c_void_p(torch.cuda.current_stream(cu.device).cuda_stream)
     _check(_get_lib().dtw_cost_noalloc(xp, M, yp, N, d, kind, ctypes.byref(c), st), "dtw_cost_noalloc")
     return int(c.value) if kind == ABS_I32 else c.value
+
+
+def path_discrepancy(P1, P2, M: int, N: int):
+    """Alignment discrepancy of two warping paths of an M x N problem (Section
+    4.3): returns (errors, max) with errors an int32 (2, K1) tensor on P1's device
+    -- row 0 the row errors of P1's cells, row 1 their column errors."""
+    import torch
+    P1 = torch.as_tensor(P1, dtype=torch.int32).contiguous()
+    P2 = torch.as_tensor(P2, dtype=torch.int32).contiguous()
+    if P1.dim() != 2 or P1.shape[1] != 2 or P2.dim() != 2 or P2.shape[1] != 2:
+        raise ValueError("paths are (K, 2) arrays of (i, j)")
+    if P1.is_cuda:
+        _sync_stream(P1)
+    elif P2.is_cuda:
+        _sync_stream(P2)
+    err = torch.empty((2, P1.shape[0]), dtype=torch.int32, device=P1.device)
+    mx = ctypes.c_int32()
+    _check(_get_lib().dtw_path_discrepancy(P1.data_ptr(), P1.shape[0], P2.data_ptr(), P2.shape[0], int(M), int(N),
+                                           err.data_ptr(), ctypes.byref(mx)), "dtw_path_discrepancy")
+    return err, int(mx.value)
 
 
 def align_batch(Xs, Ys, *, dp_f32: bool = False, cost_bf16: bool = False):

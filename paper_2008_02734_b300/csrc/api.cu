@@ -616,6 +616,43 @@ size_t dtw_footprint(int64_t M, int64_t N, int32_t d, int32_t cost_kind) {
     return L.total;
 }
 
+int dtw_path_discrepancy(const int32_t* P1, int64_t K1, const int32_t* P2, int64_t K2, int64_t M, int64_t N,
+                         int32_t* err_out, int32_t* max_out) {
+    if (!P1 || !P2 || !err_out || M < 1 || N < 1) return DTW_EINVAL;
+    const int64_t kmin = M > N ? M : N, kmax = M + N - 1;
+    if (K1 < kmin || K1 > kmax || K2 < kmin || K2 > kmax) return DTW_EINVAL;
+    Ctx& c = ctx();
+    std::lock_guard<std::mutex> g(c.mu);
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    const bool d1 = is_device_ptr(P1), d2 = is_device_ptr(P2), de = is_device_ptr(err_out);
+    const size_t b1 = sizeof(int32_t) * 2 * (size_t)K1, b2 = sizeof(int32_t) * 2 * (size_t)K2;
+    const size_t s1 = d1 ? 0 : align_up(b1), s2 = d2 ? 0 : align_up(b2), se = de ? 0 : align_up(b1);
+    const size_t used = s1 + s2 + se + discrepancy_workspace_bytes(M, N);
+    void* wsv = nullptr;
+    rc = workspace(c, used, &wsv);
+    if (rc) return rc;
+    char* ws = static_cast<char*>(wsv);
+    cudaStream_t st = c.stream;
+    const int32_t* p1 = d1 ? P1 : reinterpret_cast<const int32_t*>(ws);
+    const int32_t* p2 = d2 ? P2 : reinterpret_cast<const int32_t*>(ws + s1);
+    int32_t* err = de ? err_out : reinterpret_cast<int32_t*>(ws + s1 + s2);
+    cudaError_t e = cudaSuccess;
+    if (!d1) e = cudaMemcpyAsync(ws, P1, b1, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !d2) e = cudaMemcpyAsync(ws + s1, P2, b2, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return DTW_ECUDA;
+    rc = path_discrepancy(p1, K1, p2, K2, M, N, err, max_out, ws + s1 + s2 + se, c.num_sms, st);
+    if (rc == DTW_OK && !de) {
+        e = cudaMemcpyAsync(err_out, err, b1, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = DTW_ECUDA;
+    }
+    // the workspace also holds epoch-stamped boundary words of later alignments:
+    // leave no stray value behind that could carry a future epoch
+    if (cudaMemsetAsync(ws, 0, used, st) != cudaSuccess && rc == DTW_OK) rc = DTW_ECUDA;
+    return rc;
+}
+
 const char* dtw_strerror(int status) {
     switch (status) {
         case DTW_OK: return "ok";

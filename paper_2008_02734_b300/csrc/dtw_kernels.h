@@ -133,4 +133,10 @@ int plain_align(const PlainProblem& pb, int32_t* d_path, double* cost, int64_t* 
                 size_t work_bytes, cudaStream_t st, long long* cells);
 size_t plain_workspace_bytes(int64_t M, int64_t N);
 
+// Alignment discrepancy of two warping paths (discrepancy.cu): P1, P2, err on
+// the device; err gets 2*K1 int32 (row errors, then column errors).
+size_t discrepancy_workspace_bytes(long long M, long long N);
+int path_discrepancy(const int32_t* P1, long long K1, const int32_t* P2, long long K2, long long M, long long N,
+                     int32_t* err, int32_t* max_out, void* ws, int num_sms, cudaStream_t st);
+
 }  // namespace dtwb
