@@ -15,6 +15,12 @@ Wraps ``dtw_oracle.c`` (plain C, FP64 / int64):
 * :func:`acc_matrix`-- whole forward D or backward B matrix (small cases), for
                        the split-cost identity of Lemma 2.
 * :func:`path_cost` -- sum of C along a path (re-scoring in FP64 / int64).
+* :func:`edit`      -- weighted edit distance (Section 5 names it as a problem of
+                       the same DP design): its plain definition over the node
+                       grid with a pointer per node (ties DIAG, UP, LEFT) and a
+                       backtrace (``edit_oracle.c``).
+* :func:`edit_table`-- the whole edit-distance table, forward or of the reversed
+                       sequences (the recursion's split identity).
 * :func:`path_discrepancy` -- the alignment discrepancy of two warping paths
                        (Section 4.3, Results): per cell of the first path, its
                        distance along its row and along its column to the
@@ -33,7 +39,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
-_SRC = [os.path.join(_HERE, "dtw_oracle.c"), os.path.join(_HERE, "oracle_impl.h")]
+_SRC = [os.path.join(_HERE, "dtw_oracle.c"), os.path.join(_HERE, "edit_oracle.c"), os.path.join(_HERE, "oracle_impl.h")]
 
 EUCLID_F32 = 0
 ABS_I32 = 1
@@ -47,7 +53,7 @@ def build(force: bool = False) -> str:
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(
             ["gcc", "-O2", "-std=c99", "-Wall", "-ffp-contract=off", "-shared", "-fPIC",
-             _SRC[0], "-o", tmp, "-lm"])
+             _SRC[0], _SRC[1], "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -65,7 +71,10 @@ def _L():
         lib.oracle_linmdtw.argtypes = [p, i64, p, i64, i32, i32, i64, p, p, p, p, p]
         lib.oracle_acc_matrix.argtypes = [p, i64, p, i64, i32, i32, i32, p, p]
         lib.oracle_path_cost.argtypes = [p, i64, p, i64, i32, i32, p, i64, p, p]
-        for f in (lib.oracle_dtw, lib.oracle_linmdtw, lib.oracle_acc_matrix, lib.oracle_path_cost):
+        lib.oracle_edit.argtypes = [p, i64, p, i64, i64, i64, p, p, p]
+        lib.oracle_edit_table.argtypes = [p, i64, p, i64, i64, i64, i32, p]
+        for f in (lib.oracle_dtw, lib.oracle_linmdtw, lib.oracle_acc_matrix, lib.oracle_path_cost, lib.oracle_edit,
+                  lib.oracle_edit_table):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -179,3 +188,47 @@ def path_discrepancy(P1, P2):
         ks = by_col.get(int(j))
         col_err[t] = min(abs(int(i) - k) for k in ks) if ks else -1
     return row_err, col_err
+
+
+def _int_seq(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(-1))
+    if a.size < 1:
+        raise ValueError("empty sequence")
+    return a
+
+
+def edit(X, Y, sub: int = 1, gap: int = 1):
+    """Weighted edit distance of int32 symbol sequences (Section 5): returns
+    (path of nodes (a, b) from (0, 0) to (M, N), int32 (K, 2); optimal cost)."""
+    X, Y = _int_seq(X), _int_seq(Y)
+    M, N = len(X), len(Y)
+    path = np.empty((M + N + 1, 2), dtype=np.int32)
+    K, c = ctypes.c_int64(), ctypes.c_int64()
+    rc = _L().oracle_edit(_ptr(X), M, _ptr(Y), N, int(sub), int(gap), _ptr(path), ctypes.byref(K), ctypes.byref(c))
+    if rc != 0:
+        raise RuntimeError(f"oracle_edit failed: {rc}")
+    return path[:K.value].copy(), int(c.value)
+
+
+def edit_table(X, Y, sub: int = 1, gap: int = 1, reverse: bool = False):
+    """The (M+1) x (N+1) edit-distance table E (reverse: of the reversed sequences)."""
+    X, Y = _int_seq(X), _int_seq(Y)
+    M, N = len(X), len(Y)
+    out = np.empty((M + 1, N + 1), dtype=np.int64)
+    rc = _L().oracle_edit_table(_ptr(X), M, _ptr(Y), N, int(sub), int(gap), int(reverse), _ptr(out))
+    if rc != 0:
+        raise RuntimeError(f"oracle_edit_table failed: {rc}")
+    return out
+
+
+def edit_path_cost(X, Y, path, sub: int = 1, gap: int = 1):
+    """Sum of the edge costs along a node path (DIAG: 0 or sub, UP/LEFT: gap)."""
+    X, Y = _int_seq(X), _int_seq(Y)
+    P = np.asarray(path, dtype=np.int64).reshape(-1, 2)
+    total = 0
+    for (a0, b0), (a1, b1) in zip(P[:-1], P[1:]):
+        if a1 == a0 + 1 and b1 == b0 + 1:
+            total += 0 if X[a1 - 1] == Y[b1 - 1] else sub
+        else:
+            total += gap
+    return int(total)

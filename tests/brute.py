@@ -100,3 +100,48 @@ def suffix_optimum(X, Y, i, j):
     summed from the last cell back to (i,j)."""
     Xr, Yr = X[i:][::-1], Y[j:][::-1]
     return solve(Xr, Yr)[0]
+
+
+# ---------------------------------------------------------------- edit distance
+
+def edit_all_paths(M, N):
+    """Every node path from (0, 0) to (M, N) with steps (1,1), (1,0), (0,1)."""
+    out = []
+
+    def rec(a, b, acc):
+        if (a, b) == (M, N):
+            out.append(list(acc))
+            return
+        for da, db in ((1, 1), (1, 0), (0, 1)):
+            if a + da <= M and b + db <= N:
+                acc.append((a + da, b + db))
+                rec(a + da, b + db, acc)
+                acc.pop()
+
+    rec(0, 0, [(0, 0)])
+    return out
+
+
+def edit_path_cost(X, Y, path, S, G):
+    total = 0
+    for (a0, b0), (a1, b1) in zip(path[:-1], path[1:]):
+        if a1 == a0 + 1 and b1 == b0 + 1:
+            total += 0 if X[a1 - 1] == Y[b1 - 1] else S
+        else:
+            total += G
+    return total
+
+
+def edit_solve(X, Y, S, G):
+    """(optimal cost, canonical path): the minimum over every node path, and among
+    the optimal ones the lexicographically smallest backward move sequence with
+    DIAG < UP < LEFT."""
+    M, N = len(X), len(Y)
+    best, cands = None, []
+    for p in edit_all_paths(M, N):
+        c = edit_path_cost(X, Y, p, S, G)
+        if best is None or c < best:
+            best, cands = c, [p]
+        elif c == best:
+            cands.append(p)
+    return best, min(cands, key=backward_moves)
