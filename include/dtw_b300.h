@@ -57,7 +57,20 @@ extern "C" {
 /* Frame cost kinds: the low byte of cost_kind. */
 enum dtw_kind {
     DTW_EUCLID_F32 = 0, /* sqrt(sum_k (x_k - y_k)^2) of FP32 frames; FP64 accumulation */
-    DTW_ABS_I32 = 1     /* |x - y| of int32 samples (d == 1); exact int accumulation */
+    DTW_ABS_I32 = 1,    /* |x - y| of int32 samples (d == 1); exact int accumulation */
+    /* Weighted edit distance of int32 symbol sequences (d == 1), which Section 5
+     * names as a problem of the same dynamic-programming design, aligned by the
+     * same linear-memory recursion.  Nodes (a, b), 0 <= a <= M, 0 <= b <= N,
+     * stand for a symbols of X and b of Y aligned; E(0,0) = 0 and
+     *   E(a,b) = min(E(a-1,b-1) + s, E(a-1,b) + gap, E(a,b-1) + gap)
+     * with s = 0 for X[a-1] == Y[b-1], else sub (DTW_OPT_EDIT_SUB and
+     * DTW_OPT_EDIT_GAP, default 1 and 1: Levenshtein distance).  The path is the
+     * node sequence from (0,0) to (M,N) (K <= M+N+1 pairs; path_out capacity
+     * 2*(M+N+1) int32), canonical under the tie order DIAG, UP, LEFT; the cost
+     * is exact.  Symbols may not be INT32_MIN (used as a sentinel); the call
+     * fails with DTW_EOVERFLOW unless (M+N+2) * max(sub, gap) < 2^29.  No form
+     * flags; dtw_submit and dtw_cost_noalloc do not take this kind. */
+    DTW_EDIT_I32 = 2
 };
 
 /* Form flags, OR-ed into cost_kind. */
@@ -107,8 +120,11 @@ enum dtw_status {
  *   Y        N*d row-major frames of the same type
  *   d        feature dimension (1 for DTW_ABS_I32)
  *   path_out capacity 2*(M+N-1) int32; receives K (i,j) pairs, (0,0) first
- *   cost_out host double; receives D* (exact integer value for DTW_ABS_I32)
- * Returns K (the path length, max(M,N) <= K <= M+N-1) or a negative dtw_status.
+ *            (DTW_EDIT_I32: 2*(M+N+1), K nodes (a,b) from (0,0) to (M,N))
+ *   cost_out host double; receives D* (exact integer value for DTW_ABS_I32
+ *            and DTW_EDIT_I32)
+ * Returns K (the path length, max(M,N) <= K <= M+N-1; for DTW_EDIT_I32
+ * max(M,N)+1 <= K <= M+N+1) or a negative dtw_status.
  * Blocks until the result is in path_out and *cost_out.
  */
 DTW_API int64_t dtw_align(const void* X, int64_t M, const void* Y, int64_t N, int32_t d,
@@ -252,8 +268,10 @@ enum dtw_option {
                                  graph with a device-side loop condition (no host round trip per level);
                                  0: a host loop that reads the control block back after every level.
                                  DTW_OPT_TIMING on forces the host loop (it times every level). */
-    DTW_OPT_SWEEP_VARIANT = 6 /* integer-kind sweep lane block: 0 (default) 4 rows x 4 columns per lane and
+    DTW_OPT_SWEEP_VARIANT = 6, /* integer-kind sweep lane block: 0 (default) 4 rows x 4 columns per lane and
                                  step, 1: 2 x 4, 2: 8 x 4 (chosen by the autotuner in the Python package) */
+    DTW_OPT_EDIT_SUB = 7,     /* DTW_EDIT_I32: cost of a substitution, 0 .. 2^20 (default 1) */
+    DTW_OPT_EDIT_GAP = 8      /* DTW_EDIT_I32: cost of an insertion or a deletion, 0 .. 2^20 (default 1) */
 };
 DTW_API int dtw_set_option(int32_t key, int64_t value);
 

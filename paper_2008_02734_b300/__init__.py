@@ -33,6 +33,8 @@ def _form(dp_f32: bool, cost_bf16: bool) -> int:
 
 OK, PENDING, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBUSY, EINTERNAL = 0, 1, -1, -2, -3, -4, -5, -6, -7
 OPT_TIMING, OPT_BASE_AREA, OPT_SPIN_LIMIT, OPT_SKIP_PUBLISH, OPT_GRAPH, OPT_SWEEP_VARIANT = 1, 2, 3, 4, 5, 6
+OPT_EDIT_SUB, OPT_EDIT_GAP = 7, 8
+EDIT_I32 = 2  # weighted edit distance of int32 symbol sequences (cost kind)
 
 
 class DTWError(RuntimeError):
@@ -243,6 +245,70 @@ def path_discrepancy(P1, P2, M: int, N: int):
     _check(_get_lib().dtw_path_discrepancy(P1.data_ptr(), P1.shape[0], P2.data_ptr(), P2.shape[0], int(M), int(N),
                                            err.data_ptr(), ctypes.byref(mx)), "dtw_path_discrepancy")
     return err, int(mx.value)
+
+
+def _edit_args(X, Y, sub, gap):
+    keep, xp, M, yp, N, d, kind, on_cuda, cu = _prep_pair(X, Y)
+    if kind != ABS_I32 or d != 1:
+        raise TypeError("edit distance takes 1-D int32 symbol sequences")
+    set_option(OPT_EDIT_SUB, int(sub))
+    set_option(OPT_EDIT_GAP, int(gap))
+    if cu is not None:
+        _sync_stream(cu)
+    return keep, xp, M, yp, N, cu
+
+
+def _node_path_buffer(M, N, like_cuda):
+    import torch
+    dev = like_cuda.device if like_cuda is not None else "cpu"
+    return torch.empty((M + N + 1, 2), dtype=torch.int32, device=dev)
+
+
+def edit_align(X, Y, *, sub: int = 1, gap: int = 1, path_out=None):
+    """Weighted edit distance of two int32 symbol sequences through the same
+    linear-memory recursion (Section 5): returns (node path, an int32 (K, 2)
+    tensor from (0, 0) to (M, N); exact cost).  A DIAG step is a match (cost 0) or
+    a substitution (``sub``), UP and LEFT steps are gaps (``gap``)."""
+    keep, xp, M, yp, N, cu = _edit_args(X, Y, sub, gap)
+    path = _node_path_buffer(M, N, cu) if path_out is None else path_out
+    c = ctypes.c_double()
+    K = _get_lib().dtw_align(xp, M, yp, N, 1, EDIT_I32, ctypes.c_void_p(path.data_ptr()), ctypes.byref(c))
+    _check(K, "dtw_align")
+    return path[:K], int(c.value)
+
+
+def edit_distance(X, Y, *, sub: int = 1, gap: int = 1) -> int:
+    """The weighted edit distance only (one forward sweep of the node grid)."""
+    keep, xp, M, yp, N, cu = _edit_args(X, Y, sub, gap)
+    c = ctypes.c_double()
+    _check(_get_lib().dtw_cost(xp, M, yp, N, 1, EDIT_I32, ctypes.byref(c)), "dtw_cost")
+    return int(c.value)
+
+
+def edit_align_batch(Xs, Ys, *, sub: int = 1, gap: int = 1):
+    """Edit-distance alignments of B pairs together; returns a list of (node path, cost)."""
+    B = len(Xs)
+    if B != len(Ys) or B == 0:
+        raise ValueError("need equally many, and at least one, X and Y")
+    keep, xps, yps, Ms, Ns, paths = [], [], [], [], [], []
+    cu0 = None
+    for X, Y in zip(Xs, Ys):
+        k, xp, M, yp, N, cu = _edit_args(X, Y, sub, gap)
+        cu0 = cu0 if cu0 is not None else cu
+        keep.append(k)
+        xps.append(xp)
+        yps.append(yp)
+        Ms.append(M)
+        Ns.append(N)
+        paths.append(_node_path_buffer(M, N, cu))
+    VP = ctypes.c_void_p * B
+    I64 = ctypes.c_int64 * B
+    K = I64()
+    C = (ctypes.c_double * B)()
+    rc = _get_lib().dtw_align_batch(B, VP(*xps), I64(*Ms), VP(*yps), I64(*Ns), 1, EDIT_I32,
+                                    VP(*[p.data_ptr() for p in paths]), K, C)
+    _check(rc, "dtw_align_batch")
+    return [(paths[b][:K[b]], int(C[b])) for b in range(B)]
 
 
 def align_batch(Xs, Ys, *, dp_f32: bool = False, cost_bf16: bool = False):

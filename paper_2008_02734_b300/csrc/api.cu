@@ -36,6 +36,7 @@ struct Ctx {
     dtw_stats stats = {};
     int use_graph = 1;
     int variant = 0;  // integer sweep variant (rows per lane), see sweep_band_rows
+    int32_t esub = 1, egap = 1;  // edit distance: substitution and gap costs
     // cached executable graph of the level loop and the parameters it was built for
     struct LevelGraph {
         cudaGraphExec_t exec = nullptr;
@@ -117,7 +118,7 @@ int level_graph(Ctx& c, const std::vector<long long>& key, const SweepArgs& sa, 
         lg.exec = nullptr;
     }
     if (!lg.cap && cudaStreamCreateWithFlags(&lg.cap, cudaStreamNonBlocking) != cudaSuccess) return DTW_ECUDA;
-    if (sweep_prepare(kind, d, kind == KIND_ABS, c.variant) != cudaSuccess) return DTW_ECUDA;
+    if (sweep_prepare(kind, d, int_kind(kind), c.variant) != cudaSuccess) return DTW_ECUDA;
     cudaGraph_t g = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return DTW_ECUDA;
     int rc = DTW_OK;
@@ -136,7 +137,7 @@ int level_graph(Ctx& c, const std::vector<long long>& key, const SweepArgs& sa, 
         cudaGraph_t body = np.conditional.phGraph_out[0];
         e = cudaStreamBeginCaptureToGraph(lg.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = launch_sweep(kind, d, kind == KIND_ABS, sa, c.num_sms, 0, lg.cap, c.variant);
+            cudaError_t e1 = launch_sweep(kind, d, int_kind(kind), sa, c.num_sms, 0, lg.cap, c.variant);
             if (e1 == cudaSuccess) e1 = launch_split(sp, lg.cap);
             if (e1 == cudaSuccess) e1 = launch_plan(pn, lg.cap);
             if (e1 == cudaSuccess) e1 = launch_level_cond(ctl, h, max_levels, lg.cap);
@@ -171,6 +172,12 @@ int map_device_error(int err) {
 int check_kind(int32_t cost_kind, int32_t d, int* kind, bool* plain) {
     const int k = cost_kind & 0xff;
     const int flags = cost_kind & ~0xff;
+    if (k == DTW_EDIT_I32) {  // no forms, no plain comparator; one symbol per frame
+        if (flags || d != 1) return DTW_EINVAL;
+        *kind = KIND_EDIT;
+        *plain = false;
+        return DTW_OK;
+    }
     if (k != DTW_EUCLID_F32 && k != DTW_ABS_I32) return DTW_EINVAL;
     if (flags & ~(int)(DTW_PLAIN_F64 | DTW_DP_F32_KAHAN | DTW_COST_BF16)) return DTW_EINVAL;
     if ((flags & (DTW_DP_F32_KAHAN | DTW_COST_BF16)) && (k != DTW_EUCLID_F32 || (flags & DTW_PLAIN_F64)))
@@ -211,6 +218,23 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     const size_t esize = 4;  // float or int32
     long long sumM = 0, sumN = 0, feat_bytes = 0, path_pairs = 0, maxM = 0, maxN = 0;
     std::vector<char> xdev(B), ydev(B), pdev(B);
+    // edit distance runs on its node grid: M+1 x N+1 nodes over the sequences
+    // with a sentinel at both ends (staged into the workspace for every input)
+    const bool edit = kind == KIND_EDIT;
+    const int64_t* M0 = M;
+    const int64_t* N0 = N;
+    std::vector<int64_t> Mv, Nv;
+    if (edit) {
+        for (int b = 0; b < B; ++b) {
+            if (M[b] < 1 || N[b] < 1 || M[b] >= (1LL << 30) || N[b] >= (1LL << 30)) return DTW_EINVAL;
+            // exact int32 accumulation: every node value is at most (M+N) max(sub, gap) plus a corner term
+            if ((M[b] + N[b] + 2) * (long long)std::max(c.esub, c.egap) >= (1LL << 29)) return DTW_EOVERFLOW;
+            Mv.push_back(M[b] + 1);
+            Nv.push_back(N[b] + 1);
+        }
+        M = Mv.data();
+        N = Nv.data();
+    }
     for (int b = 0; b < B; ++b) {
         if (!X[b] || !Y[b] || M[b] < 1 || N[b] < 1 || M[b] > (1LL << 30) || N[b] > (1LL << 30)) return DTW_EINVAL;
         if (B > 65535) return DTW_EINVAL;
@@ -221,8 +245,12 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         maxN = std::max<long long>(maxN, N[b]);
         xdev[b] = is_device_ptr(X[b]);
         ydev[b] = is_device_ptr(Y[b]);
-        if (!xdev[b]) feat_bytes += align_up((size_t)M[b] * d * esize);
-        if (!ydev[b]) feat_bytes += align_up((size_t)N[b] * d * esize);
+        if (edit) {
+            feat_bytes += align_up((size_t)(M[b] + 1) * esize) + align_up((size_t)(N[b] + 1) * esize);
+        } else {
+            if (!xdev[b]) feat_bytes += align_up((size_t)M[b] * d * esize);
+            if (!ydev[b]) feat_bytes += align_up((size_t)N[b] * d * esize);
+        }
         if (want_path) {
             pdev[b] = is_device_ptr(path_out[b]);
             if (!pdev[b]) path_pairs += M[b] + N[b] - 1;
@@ -248,15 +276,33 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         p.N = (int32_t)N[b];
         p.row_off = (int32_t)row_off;
         p.flags = 0;
+        p.esub = c.esub;
+        p.egap = c.egap;
         row_off += M[b];
-        if (xdev[b]) {
+        if (edit) {
+            // [pad, symbols..., pad] for X and for Y
+            const void* src[2] = {X[b], Y[b]};
+            const int64_t len[2] = {M0[b], N0[b]};
+            const bool dev[2] = {xdev[b] != 0, ydev[b] != 0};
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+                int32_t* dst = reinterpret_cast<int32_t*>(ws + fo);
+                e = launch_fill_i32(dst, len[k] + 2, kEditPad, st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(dst + 1, src[k], (size_t)len[k] * esize,
+                                        dev[k] ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+                if (k == 0) p.X = dst;
+                else p.Y = dst;
+                fo += align_up((size_t)(len[k] + 2) * esize);
+            }
+        } else if (xdev[b]) {
             p.X = X[b];
         } else {
             p.X = ws + fo;
             e = cudaMemcpyAsync(ws + fo, X[b], (size_t)M[b] * d * esize, cudaMemcpyHostToDevice, st);
             fo += align_up((size_t)M[b] * d * esize);
         }
-        if (e == cudaSuccess && !ydev[b]) {
+        if (edit) {
+        } else if (e == cudaSuccess && !ydev[b]) {
             p.Y = ws + fo;
             e = cudaMemcpyAsync(ws + fo, Y[b], (size_t)N[b] * d * esize, cudaMemcpyHostToDevice, st);
             fo += align_up((size_t)N[b] * d * esize);
@@ -335,7 +381,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     // the control block (errors, the next level's box and ticket counts, which
     // size the next sweep's grid).
     const int mode = want_path ? MODE_ALIGN : MODE_COST;
-    const int halo = kind == KIND_ABS ? kSplitHalo : 0;
+    const int halo = int_kind(kind) ? kSplitHalo : 0;
     const int U = sweep_block_cols(kind, d, c.variant);
     const int BR = sweep_band_rows(kind, d, c.variant);
     const int G = sweep_group_bands(kind);
@@ -346,7 +392,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     LevelCtl hc = ctl0;
     // every level shrinks each box's longer side to at most about half, so the
     // depth is bounded by twice the bits of the longest sequence
-    int launches = (want_path ? 1 : 0) + (kind == KIND_ABS ? 3 : 0);
+    int launches = (want_path ? 1 : 0) + (kind == KIND_ABS ? 3 : 0) + (edit ? 2 * B : 0);
     const int max_levels = 2 * (64 - __builtin_clzll((unsigned long long)std::max(maxM, sumN) + 1)) + 8;
     int* d_boxdone = reinterpret_cast<int*>(ws + L.boxdone);
     if (!roots.empty()) {
@@ -389,7 +435,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         cudaEvent_t s0 = nullptr, s1 = nullptr;
         if (c.timing) s0 = T.mark();
         // integer levels may mix tagged and untagged boxes
-        e = launch_sweep(kind, d, mode == MODE_ALIGN && kind == KIND_ABS, sa, c.num_sms, hc.n_tickets, st, c.variant);
+        e = launch_sweep(kind, d, mode == MODE_ALIGN && int_kind(kind), sa, c.num_sms, hc.n_tickets, st, c.variant);
         ++launches;
         if (c.timing) s1 = T.mark();
         ++sweeps;
@@ -420,7 +466,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         e = cudaMemcpyAsync(sr.data(), d_sres, sizeof(SweepRes) * B, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return DTW_ECUDA;
-        for (int b = 0; b < B; ++b) cost_out[b] = kind == KIND_ABS ? (double)sr[b].end_i : sr[b].end_f;
+        for (int b = 0; b < B; ++b) cost_out[b] = int_kind(kind) ? (double)sr[b].end_i : sr[b].end_f;
     }
     if (hc.err == ERR_NONE && want_path) {
         BaseArgs ba{d_base, hc.n_base, d_pairs, d_pres, d_jlo, d_jhi, d_ctl, kind, d};
@@ -436,7 +482,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         if (hc.err == ERR_NONE) {
             for (int b = 0; b < B && e == cudaSuccess; ++b) {
                 K_out[b] = pr[b].K;
-                cost_out[b] = kind == KIND_ABS ? (double)pr[b].cost_i : pr[b].cost_f;
+                cost_out[b] = int_kind(kind) ? (double)pr[b].cost_i : pr[b].cost_f;
                 if (!pdev[b])
                     e = cudaMemcpyAsync(path_out[b], pd[b].path, sizeof(int32_t) * 2 * (size_t)pr[b].K,
                                         cudaMemcpyDeviceToHost, st);
@@ -459,7 +505,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     }
     dtw_stats& s = c.stats;
     s = dtw_stats{};
-    for (int b = 0; b < B; ++b) s.problem_cells += M[b] * N[b];
+    for (int b = 0; b < B; ++b) s.problem_cells += M0[b] * N0[b];
     s.sweep_cells = (int64_t)hc.sweep_cells;
     s.tag_cells = (int64_t)hc.tag_cells;
     s.base_cells = (int64_t)hc.base_cells;
@@ -611,6 +657,12 @@ size_t dtw_footprint(int64_t M, int64_t N, int32_t d, int32_t cost_kind) {
         return align_up((size_t)(M + N) * d * 4) + 3 * 256 + align_up(8 * (size_t)(M + N)) +
                plain_workspace_bytes(M, N);
     }
+    if ((cost_kind & 0xff) == DTW_EDIT_I32) {  // the node grid over the padded sequences
+        const Layout L = make_layout(1, M + 1, N + 1,
+                                     (long long)align_up((size_t)(M + 2) * 4) + (long long)align_up((size_t)(N + 2) * 4),
+                                     M + N + 1);
+        return L.total;
+    }
     const Layout L = make_layout(1, M, N, (long long)align_up((size_t)M * d * 4) + (long long)align_up((size_t)N * d * 4),
                                  M + N - 1);
     return L.total;
@@ -694,6 +746,14 @@ int dtw_set_option(int32_t key, int64_t value) {
         case DTW_OPT_SWEEP_VARIANT:
             if (value < 0 || value >= kSweepVariants) return DTW_EINVAL;
             c.variant = (int)value;
+            return DTW_OK;
+        case DTW_OPT_EDIT_SUB:
+            if (value < 0 || value > (1 << 20)) return DTW_EINVAL;
+            c.esub = (int32_t)value;
+            return DTW_OK;
+        case DTW_OPT_EDIT_GAP:
+            if (value < 0 || value > (1 << 20)) return DTW_EINVAL;
+            c.egap = (int32_t)value;
             return DTW_OK;
         default: return DTW_EINVAL;
     }

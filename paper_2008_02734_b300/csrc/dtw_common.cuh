@@ -23,6 +23,20 @@ constexpr int KIND_ABS = 1;  // |x - y| of int32 samples, exact int32 accumulati
 constexpr int KIND_EUCF = 2; // Euclidean distance of FP32 frames, compensated FP32-pair accumulation
 constexpr int KIND_EUCB = 3; // Euclidean distance in the expanded form with BF16 products (tensor-core
                              // cost tiles), compensated FP32-pair accumulation; d = 64
+// Weighted edit distance of int32 symbol sequences (Section 5 names it as a
+// problem of the same DP design), run as the same recursion on its node grid:
+// the pair handed to the kernels is the two sequences with a sentinel symbol at
+// both ends (frames 0 .. M+1), M+1 x N+1 "cells" (the nodes), and a cell update
+//   E = min(E_diag + delta, E_up, E_left) + gap,  delta = s(x, y) - gap,
+// with s(x, y) = 0 for equal symbols, else sub.  The first node of a box takes
+// E = s of its own symbols (the corner is 0), a constant that every value of
+// the box carries; the backward sweep reads its symbols one index further (the
+// step into reversed node p consumes forward symbol p + 1).  The split sums
+// F + B with no cell term.
+constexpr int KIND_EDIT = 4;
+__host__ __device__ constexpr bool int_kind(int k) { return k == KIND_ABS || k == KIND_EDIT; }
+// The sentinel symbol at both ends of an edit pair (inputs may not contain it).
+constexpr int32_t kEditPad = (int32_t)0x80000000;
 
 // "Infinity" of the int32 accumulator: above any reachable cost (the host
 // guarantees max C * (M+N-1) < 2^29) and far from overflow when C is added.
@@ -43,6 +57,7 @@ struct PairDesc {
     int32_t row_off;    // offset of the pair's rows in the per-row path arrays
     int32_t flags;
     int32_t* path;      // device path buffer, 2*(M+N-1) int32
+    int32_t esub, egap; // KIND_EDIT: substitution and gap costs
 };
 
 struct PairRes {
@@ -94,6 +109,7 @@ struct Sweep {
     long long band_begin;  // level band number of the sweep's first band
     long long buf_off;     // boundary-row pool offset, in 64-bit words (1 or 2 per column)
     long long out_off;     // out pool offset: nout rows of ostride values, in the sweep's own frame order
+    int32_t esub, egap;    // KIND_EDIT: substitution and gap costs
 };
 
 struct SweepRes {
@@ -218,6 +234,7 @@ template <> struct AccOf<KIND_EUCF> {
     static __device__ __forceinline__ T zero() { return DF{0.f, 0.f}; }
 };
 template <> struct AccOf<KIND_EUCB> : AccOf<KIND_EUCF> {};
+template <> struct AccOf<KIND_EDIT> : AccOf<KIND_ABS> {};
 
 __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return __vimin3_s32(a, b, c); }
 // Accumulated costs are sums of nonnegative frame costs (or +infinity), and for
@@ -243,6 +260,7 @@ template <> struct Frame<KIND_ABS, 1> {
     }
     __device__ __forceinline__ void load_shared(const void* p) { v = *static_cast<const int32_t*>(p); }
 };
+template <> struct Frame<KIND_EDIT, 1> : Frame<KIND_ABS, 1> {};
 
 template <int DIM> struct Frame<KIND_EUC, DIM> {
     float v[DIM];
@@ -319,6 +337,12 @@ __device__ __forceinline__ float sqnorm(const float* v) {
 // evaluated in FP32 (sum of squares with FMA, correctly rounded sqrt) and widened.
 __device__ __forceinline__ int32_t frame_cost(const Frame<KIND_ABS, 1>& a, const Frame<KIND_ABS, 1>& b) {
     return abs(a.v - b.v);
+}
+// Edit distance: no cost sits on a node, so the split sums F + B alone; the
+// sweeps and the base case use edit_delta and the gap instead.
+__device__ __forceinline__ int32_t frame_cost(const Frame<KIND_EDIT, 1>&, const Frame<KIND_EDIT, 1>&) { return 0; }
+__device__ __forceinline__ int32_t edit_delta(int32_t x, int32_t y, int32_t sub, int32_t gap) {
+    return (x == y ? 0 : sub) - gap;
 }
 
 // Exact FP32 -> FP64 widening of a frame cost with integer operations (the

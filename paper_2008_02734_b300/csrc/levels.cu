@@ -139,14 +139,18 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
                 sw.cbase = cb0;
                 sw.cstep = 1;
             } else {  // the reversed series X_R, Y_R of Algorithm 2
-                sw.rbase = rb0 + rlen - 1;
+                // edit distance: the step into reversed node p consumes forward symbol p + 1
+                const int shift = a.kind == KIND_EDIT ? 1 : 0;
+                sw.rbase = rb0 + rlen - 1 + shift;
                 sw.rstep = -1;
-                sw.cbase = cb0 + clen - 1;
+                sw.cbase = cb0 + clen - 1 + shift;
                 sw.cstep = -1;
             }
+            sw.esub = pd.esub;
+            sw.egap = pd.egap;
             nb = sw.nbands;
             // boundary words per column: one for an untagged integer sweep, two otherwise
-            const int nw = (a.kind == KIND_ABS && sw.tag_row < 0) ? 1 : 2;
+            const int nw = (int_kind(a.kind) && sw.tag_row < 0) ? 1 : 2;
             nbuf = (long long)nw * sw.nblk * a.U;
             nout = (long long)sw.nout * sw.ostride;
             // split work: the forward slot of an aligned box owns the box's column chunks
@@ -332,7 +336,7 @@ __device__ void finish_box(const SplitArgs& a, const Box& b, const PairDesc& pd,
         int i, j;
         frame_to_global(b, g.axis, g.r, qs, i, j);
         const auto c = cell_cost<KIND, DIM>(pd, i, j, a.d);
-        if constexpr (KIND == KIND_ABS) {
+        if constexpr (int_kind(KIND)) {
             total_i = rr.end_i;
             if (b.known_i >= 0 && b.known_i != total_i) set_error(a.ctl, ERR_CONSIST, 11);
             known_l = out[qs];
@@ -349,7 +353,7 @@ __device__ void finish_box(const SplitArgs& a, const Box& b, const PairDesc& pd,
         const Acc* B = static_cast<const Acc*>(a.outpool) + bw.out_off + (size_t)(nr - 1) * bs + (g.Q - 1);
         // every split row's minimum is the box's optimal cost (Lemma 2)
         int pick = -1;
-        if constexpr (KIND == KIND_ABS) {
+        if constexpr (int_kind(KIND)) {
             for (int m = 0; m < nr; ++m) {
                 if (rm[m].v != rm[h].v) set_error(a.ctl, ERR_CONSIST, 12);
                 if (b.known_i >= 0 && rm[m].v != b.known_i) set_error(a.ctl, ERR_CONSIST, 13);
@@ -370,7 +374,7 @@ __device__ void finish_box(const SplitArgs& a, const Box& b, const PairDesc& pd,
         } else {
             row = g.r - h + pick;
             qs = rm[pick].q;
-            if constexpr (KIND == KIND_ABS) {
+            if constexpr (int_kind(KIND)) {
                 known_l = F[(size_t)pick * fs + qs];
                 known_r = B[-(long long)pick * bs - qs];
             } else {
@@ -383,10 +387,16 @@ __device__ void finish_box(const SplitArgs& a, const Box& b, const PairDesc& pd,
         a.pres[b.pair].cost_i = total_i;
         a.pres[b.pair].cost_f = total_f;
     }
+    if constexpr (KIND == KIND_EDIT) {
+        // a child's sweeps carry the symbols' costs at its own corners, which
+        // differ from the parent's: its optimum is not checked against them
+        known_l = -1;
+        known_r = -1;
+    }
     if (retag) {  // every split row tied: sweep this box again with split tags
         Box t = b;
         t.flags = BOX_TAG;
-        t.known_i = total_i;
+        t.known_i = KIND == KIND_EDIT ? -1 : total_i;  // edit: the tag sweep's end carries no backward corner term
         atomicAdd((unsigned long long*)&a.ctl->retag, 1ULL);
         emit_child(a, t);
     } else {
@@ -422,7 +432,7 @@ __device__ void finish_box(const SplitArgs& a, const Box& b, const PairDesc& pd,
 // finishes a box last (per-box counter) merges them and emits the children.
 template <int KIND, int DIM>
 __global__ void __launch_bounds__(256) split_kernel(SplitArgs a) {
-    using V = typename std::conditional<KIND == KIND_ABS, long long, double>::type;
+    using V = typename std::conditional<int_kind(KIND), long long, double>::type;
     __shared__ RowMin<V> rm[kSplitRowsMax];
     __shared__ int s_last;
     // after a planning or sweep error the sweep outputs are not valid
@@ -497,6 +507,7 @@ cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
         if (a.n_items < grid) grid = a.n_items;
     }
     if (a.kind == KIND_ABS) split_kernel<KIND_ABS, 1><<<grid, 256, 0, st>>>(a);
+    else if (a.kind == KIND_EDIT) split_kernel<KIND_EDIT, 1><<<grid, 256, 0, st>>>(a);
     else if (a.kind == KIND_EUCB) split_kernel<KIND_EUCB, 64><<<grid, 256, 0, st>>>(a);
     else if (a.kind == KIND_EUCF && a.d == 12) split_kernel<KIND_EUCF, 12><<<grid, 256, 0, st>>>(a);
     else if (a.kind == KIND_EUCF && a.d == 64) split_kernel<KIND_EUCF, 64><<<grid, 256, 0, st>>>(a);
@@ -564,11 +575,19 @@ __global__ void __launch_bounds__(32 * kBaseWarps) base_kernel(BaseArgs a) {
                 if (act) {
                     Frame<KIND, DIM> yc;
                     yc.load(cs, cbase + q, a.d);
-                    const auto c = frame_cost(xr, yc);
-                    const Acc m = min3(dprev, up, left);
+                    // edit distance: delta on the diagonal move, the gap on every move
+                    const auto c = [&]() {
+                        if constexpr (KIND == KIND_EDIT) return pd.egap;
+                        else return frame_cost(xr, yc);
+                    }();
+                    const Acc dd = [&]() {
+                        if constexpr (KIND == KIND_EDIT) return dprev + edit_delta(xr.v, yc.v, pd.esub, pd.egap);
+                        else return dprev;
+                    }();
+                    const Acc m = min3(dd, up, left);
                     uint32_t pt;
                     if (p == 0 && q == 0) pt = 3;
-                    else if (dprev == m) pt = 0;
+                    else if (dd == m) pt = 0;
                     else if (vf) pt = (up == m) ? 1 : 2;
                     else pt = (left == m) ? 2 : 1;
                     cur = m + c;
@@ -591,7 +610,7 @@ __global__ void __launch_bounds__(32 * kBaseWarps) base_kernel(BaseArgs a) {
             end_v = acc_min(end_v, t);
         }
         if (lane == 0) {
-            if constexpr (KIND == KIND_ABS) {
+            if constexpr (int_kind(KIND)) {
                 if (b.known_i >= 0 && b.known_i != (long long)end_v) set_error(a.ctl, ERR_CONSIST, 20);
                 if (b.flags & BOX_ROOT) a.pres[b.pair].cost_i = end_v;
             } else {
@@ -642,6 +661,7 @@ static cudaError_t launch_base_t(const BaseArgs& a, cudaStream_t st) {
 cudaError_t launch_base(const BaseArgs& a, cudaStream_t st) {
     if (a.n_base == 0) return cudaSuccess;
     if (a.kind == KIND_ABS) return launch_base_t<KIND_ABS, 1>(a, st);
+    if (a.kind == KIND_EDIT) return launch_base_t<KIND_EDIT, 1>(a, st);
     if (a.kind == KIND_EUCB) return launch_base_t<KIND_EUCB, 64>(a, st);
     if (a.kind == KIND_EUCF) {
         if (a.d == 12) return launch_base_t<KIND_EUCF, 12>(a, st);

@@ -73,7 +73,7 @@ namespace {
 #define DTW_SWEEP_G_EUC 4
 #endif
 template <int KIND>
-__host__ __device__ constexpr int group_of() { return KIND == KIND_ABS ? DTW_SWEEP_G_INT : DTW_SWEEP_G_EUC; }
+__host__ __device__ constexpr int group_of() { return int_kind(KIND) ? DTW_SWEEP_G_INT : DTW_SWEEP_G_EUC; }
 template <int KIND>
 __host__ __device__ constexpr int threads_of() { return 32 * (group_of<KIND>() + 1); }  // + the loader warp
 constexpr int kGMax = 8;  // the frame ring partition covers up to 8 warps
@@ -224,7 +224,7 @@ __device__ __forceinline__ int wait_counter(const int* ctr, int target, LevelCtl
 // Payload words of one column in rings and boundary rows.
 template <int KIND, int NW>
 __device__ __forceinline__ void pack(typename AccOf<KIND>::T v, int t, uint32_t* w) {
-    if constexpr (KIND == KIND_ABS) {
+    if constexpr (int_kind(KIND)) {
         w[0] = (uint32_t)v;
         if constexpr (NW == 2) w[1] = (uint32_t)t;
     } else if constexpr (std::is_same<typename AccOf<KIND>::T, DF>::value) {
@@ -237,7 +237,7 @@ __device__ __forceinline__ void pack(typename AccOf<KIND>::T v, int t, uint32_t*
 }
 template <int KIND, int NW>
 __device__ __forceinline__ void unpack(const uint32_t* w, typename AccOf<KIND>::T& v, int& t) {
-    if constexpr (KIND == KIND_ABS) {
+    if constexpr (int_kind(KIND)) {
         v = (int32_t)w[0];
         t = NW == 2 ? (int)w[1] : 0;
     } else if constexpr (std::is_same<typename AccOf<KIND>::T, DF>::value) {
@@ -255,7 +255,7 @@ __device__ __forceinline__ void unpack(const uint32_t* w, typename AccOf<KIND>::
 // global memory by every lane, the runtime-dimension variant).
 template <int KIND, int DIM>
 struct FrameWords {
-    static constexpr int v = KIND == KIND_ABS ? 1 : (KIND == KIND_EUCB ? 0 : DIM);
+    static constexpr int v = int_kind(KIND) ? 1 : (KIND == KIND_EUCB ? 0 : DIM);
 };
 
 // Per-warp shared memory of the BF16 tensor-core form: the band's 32 row frames
@@ -383,6 +383,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     const int rbase = sp->rbase, rstep = sp->rstep;
     const void* rowseq = sp->rowseq;
     const int out_row0 = sp->out_row0, nout = sp->nout, tag_row = sp->tag_row, ostride = sp->ostride;
+    const int32_t esub = sp->esub, egap = sp->egap;  // KIND_EDIT
     const uint32_t ep_out = sp->epoch0 + (uint32_t)band + 1u;
     unsigned long long* buf = A.bufpool + sp->buf_off;
     Acc* outp = static_cast<Acc*>(A.outpool) + sp->out_off;
@@ -531,7 +532,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     YF ny[U];
     // frames of the lane's block: loaded one step ahead (YPF), or at the step
     // itself for large frames (fewer registers, more resident warps)
-    constexpr bool YPF = KIND == KIND_ABS || DTW_EUC_YPREFETCH != 0 || YW == 0;
+    constexpr bool YPF = int_kind(KIND) || DTW_EUC_YPREFETCH != 0 || YW == 0;
     auto load_frames = [&](int cb, YF* dst) {
         if constexpr (YW > 0) {
             const uint32_t* ys = yr + (cb & ymask) * YSW;
@@ -547,7 +548,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         const int cb = s - lane;
         if constexpr (TC || !YPF) {
             // tensor-core form: costs come from the tiles; otherwise frames are loaded by the step itself
-        } else if constexpr (KIND == KIND_ABS && U % 4 == 0) {
+        } else if constexpr (int_kind(KIND) && U % 4 == 0) {
             uint32_t w[U];
             ld_shared_words<U>(yr + (cb & ymask) * YSW, w);
 #pragma unroll
@@ -655,19 +656,25 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                     } else {
                         c = 0.0;
                     }
+                    // edit distance: the diagonal move carries delta, every move the gap
                     const auto cc = [&]() {
                         if constexpr (TC) return c;
+                        else if constexpr (KIND == KIND_EDIT) return egap;
                         else return frame_cost(xr[k], yc[u]);
                     }();
+                    const Acc a_dd = [&]() {
+                        if constexpr (KIND == KIND_EDIT) return a_dg + edit_delta(xr[k].v, yc[u].v, esub, egap);
+                        else return a_dg;
+                    }();
                     const Acc lf = L[k];
-                    const Acc m = min3(a_dg, a_up, lf);
+                    const Acc m = min3(a_dd, a_up, lf);
                     const Acc nv = m + cc;
                     int t = 0;
                     if constexpr (TAG) {
                         const int t_lf = LT[k];
                         // tag of the backpointer: first minimum among DIAG, UP, LEFT
-                        if constexpr (VF) t = (a_dg == m) ? t_dg : ((a_up == m) ? t_up : t_lf);
-                        else t = (a_dg == m) ? t_dg : ((lf == m) ? t_lf : t_up);
+                        if constexpr (VF) t = (a_dd == m) ? t_dg : ((a_up == m) ? t_up : t_lf);
+                        else t = (a_dd == m) ? t_dg : ((lf == m) ? t_lf : t_up);
                         if constexpr (TAGM == 2) t = (p0 + k == tag_row) ? q : t;
                         t_dg = t_lf;
                         t_up = t;
@@ -716,7 +723,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         if (s0 > 0) sync_group(s0);
         if (TC && (s0 & 15) == 0 && s0 < nblk) build_tile(s0 >> 4);
         if (s0 >= 31 && s0 + KC < nblk) {
-            if constexpr (KIND == KIND_ABS) {
+            if constexpr (int_kind(KIND)) {
 #pragma unroll kGroupUnroll
                 for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{});
             } else {
@@ -733,7 +740,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     if constexpr (SPECIAL) {
         if (end_k >= 0 && end_k < R) {
             SweepRes* r = A.res + sweep_idx;
-            if constexpr (KIND == KIND_ABS) r->end_i = end_v;
+            if constexpr (int_kind(KIND)) r->end_i = end_v;
             else r->end_f = to_double(end_v);
             r->end_tag = end_t;
         }
@@ -922,7 +929,7 @@ __device__ __forceinline__ int find_sweep(const Sweep* sweeps, int n_sweeps, lon
 // two payload words per column; untagged integer sweeps use one.
 template <int KIND, int R, int U, int DIM, bool TAGS>
 __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_constant__ SweepArgs A) {
-    constexpr int NWMAX = (KIND != KIND_ABS || TAGS) ? 2 : 1;
+    constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
     constexpr int kG = group_of<KIND>();
     using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -999,7 +1006,7 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
                 const int b_lo = band * BR, b_hi = b_lo + BR;  // band rows [b_lo, b_hi)
                 const bool special =
                     (sp->nout > 0 && sp->out_row0 < b_hi && sp->out_row0 + sp->nout > b_lo) || (rows - 1 < b_hi);
-                if constexpr (KIND != KIND_ABS) {
+                if constexpr (!int_kind(KIND)) {
                     run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true>(special, sp, si, band, to_ring, to_global, A, sm,
                                                                    warp, tcw);
                 } else if (!TAGS || tag_row < 0) {
@@ -1029,7 +1036,7 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
             }
         } else {
             const int si0 = sweep_of[0];
-            if (KIND != KIND_ABS || (TAGS && si0 >= 0 && A.sweeps[si0].tag_row >= 0))
+            if (!int_kind(KIND) || (TAGS && si0 >= 0 && A.sweeps[si0].tag_row >= 0))
                 run_loader<KIND, U, DIM, NWMAX, 2>(A, sm);
             else
                 run_loader<KIND, U, DIM, NWMAX, 1>(A, sm);
@@ -1045,7 +1052,7 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
 // its warps over the schedulers of the whole GPU.
 template <int KIND, int R, int U, int DIM, bool TAGS>
 static cudaError_t setup_one(int* nb_out) {
-    constexpr int NWMAX = (KIND != KIND_ABS || TAGS) ? 2 : 1;
+    constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
     constexpr size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>();
     static int nb = 0;
     if (nb == 0) {
@@ -1062,7 +1069,7 @@ static cudaError_t setup_one(int* nb_out) {
 
 template <int KIND, int R, int U, int DIM, bool TAGS>
 static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blocks, cudaStream_t st) {
-    constexpr int NWMAX = (KIND != KIND_ABS || TAGS) ? 2 : 1;
+    constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
     constexpr size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>();
     int nb = 0;
     cudaError_t e = setup_one<KIND, R, U, DIM, TAGS>(&nb);
@@ -1083,12 +1090,13 @@ constexpr int kIntR = DTW_INT_R, kIntU = DTW_INT_U;
 constexpr int kEucR = DTW_EUC_R, kEucU = DTW_EUC_U;
 // Integer variants (selected at run time, e.g. by the autotuner): rows per lane.
 constexpr int kIntRVar[kSweepVariants] = {kIntR, 2, 8};
-int sweep_block_cols(int kind, int d, int variant) { return kind == KIND_ABS ? kIntU : (d == 12 ? kEucU : 2); }
+int sweep_block_cols(int kind, int d, int variant) { return int_kind(kind) ? kIntU : (d == 12 ? kEucU : 2); }
 int sweep_band_rows(int kind, int d, int variant) {
     if (kind == KIND_ABS) return 32 * kIntRVar[(unsigned)variant < (unsigned)kSweepVariants ? variant : 0];
+    if (kind == KIND_EDIT) return 32 * kIntR;
     return d == 12 ? 32 * kEucR : (d == 64 ? 32 : 64);
 }
-int sweep_group_bands(int kind) { return kind == KIND_ABS ? group_of<KIND_ABS>() : group_of<KIND_EUC>(); }
+int sweep_group_bands(int kind) { return int_kind(kind) ? group_of<KIND_ABS>() : group_of<KIND_EUC>(); }
 
 cudaError_t sweep_prepare(int kind, int d, bool tags, int variant) {
     int nb = 0;
@@ -1098,6 +1106,8 @@ cudaError_t sweep_prepare(int kind, int d, bool tags, int variant) {
         if (tags) return setup_one<KIND_ABS, kIntR, kIntU, 1, true>(&nb);
         return setup_one<KIND_ABS, kIntR, kIntU, 1, false>(&nb);
     }
+    if (kind == KIND_EDIT) return tags ? setup_one<KIND_EDIT, kIntR, kIntU, 1, true>(&nb)
+                                       : setup_one<KIND_EDIT, kIntR, kIntU, 1, false>(&nb);
     if (kind == KIND_EUCB) return setup_one<KIND_EUCB, 1, 2, 64, false>(&nb);
     if (kind == KIND_EUCF) {
         if (d == 12) return setup_one<KIND_EUCF, kEucR, kEucU, 12, false>(&nb);
@@ -1121,6 +1131,9 @@ cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num
         if (tags) return launch_one<KIND_ABS, kIntR, kIntU, 1, true>(A, num_sms, max_blocks, st);
         return launch_one<KIND_ABS, kIntR, kIntU, 1, false>(A, num_sms, max_blocks, st);
     }
+    if (kind == KIND_EDIT)
+        return tags ? launch_one<KIND_EDIT, kIntR, kIntU, 1, true>(A, num_sms, max_blocks, st)
+                    : launch_one<KIND_EDIT, kIntR, kIntU, 1, false>(A, num_sms, max_blocks, st);
     if (kind == KIND_EUCB) return launch_one<KIND_EUCB, 1, 2, 64, false>(A, num_sms, max_blocks, st);
     if (kind == KIND_EUCF) {
         if (d == 12) return launch_one<KIND_EUCF, kEucR, kEucU, 12, false>(A, num_sms, max_blocks, st);

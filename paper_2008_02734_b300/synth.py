@@ -165,3 +165,31 @@ def workload_serving(seed: int = 4, R: int = 2000, rate_hz: float = 100.0,
     d = np.where(rng.random(R) < 0.5, CHROMA_D, MFCC_D)
     return [Request(float(t[k]), int(M[k]), int(N[k]), int(d[k]), seed * 1000003 + k)
             for k in range(R)]
+
+
+def edit_pair(seed: int, M: int, rate: float = 0.1, alphabet: int = 4):
+    """Symbol sequences for edit distance: X uniform over ``alphabet`` symbols; Y
+    is X after random point mutations -- at each position, with probability
+    ``rate``, a substitution, a deletion or an insertion (equally likely)."""
+    rng = np.random.default_rng(seed)
+    X = rng.integers(0, alphabet, M).astype(np.int32)
+    out = []
+    for v in X:
+        if rng.random() < rate:
+            kind = rng.integers(3)
+            if kind == 0:
+                out.append(int(rng.integers(0, alphabet)))
+            elif kind == 2:
+                out.append(int(v))
+                out.append(int(rng.integers(0, alphabet)))
+            # kind == 1: deletion
+        else:
+            out.append(int(v))
+    if not out:
+        out.append(int(rng.integers(0, alphabet)))
+    return X, np.asarray(out, dtype=np.int32)
+
+
+def workload_edit_pair(seed: int = 4, M: int = 20000):
+    """A 20000-symbol sequence over 4 symbols against a 10%-mutated copy."""
+    return edit_pair(seed, M)
