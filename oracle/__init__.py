@@ -21,6 +21,9 @@ Wraps ``dtw_oracle.c`` (plain C, FP64 / int64):
                        backtrace (``edit_oracle.c``).
 * :func:`edit_table`-- the whole edit-distance table, forward or of the reversed
                        sequences (the recursion's split identity).
+* :func:`local`     -- local alignment (Smith-Waterman, named in Section 5 beside
+                       edit distance): score, the canonical end, start and path
+                       (``edit_oracle.c`` states the definition).
 * :func:`path_discrepancy` -- the alignment discrepancy of two warping paths
                        (Section 4.3, Results): per cell of the first path, its
                        distance along its row and along its column to the
@@ -73,8 +76,9 @@ def _L():
         lib.oracle_path_cost.argtypes = [p, i64, p, i64, i32, i32, p, i64, p, p]
         lib.oracle_edit.argtypes = [p, i64, p, i64, i64, i64, p, p, p]
         lib.oracle_edit_table.argtypes = [p, i64, p, i64, i64, i64, i32, p]
+        lib.oracle_local.argtypes = [p, i64, p, i64, i64, i64, i64, p, p, p, p]
         for f in (lib.oracle_dtw, lib.oracle_linmdtw, lib.oracle_acc_matrix, lib.oracle_path_cost, lib.oracle_edit,
-                  lib.oracle_edit_table):
+                  lib.oracle_edit_table, lib.oracle_local):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -232,3 +236,19 @@ def edit_path_cost(X, Y, path, sub: int = 1, gap: int = 1):
         else:
             total += gap
     return int(total)
+
+
+def local(X, Y, match: int = 2, mismatch: int = 1, gap: int = 1):
+    """Local alignment of int32 symbol sequences (scores +match, -mismatch,
+    -gap): returns (node path (K, 2) from the start to the end node, empty when
+    the score is 0; score; (a_s, b_s, a_e, b_e))."""
+    X, Y = _int_seq(X), _int_seq(Y)
+    M, N = len(X), len(Y)
+    path = np.empty((M + N + 1, 2), dtype=np.int32)
+    K, sc = ctypes.c_int64(), ctypes.c_int64()
+    se = np.zeros(4, dtype=np.int64)
+    rc = _L().oracle_local(_ptr(X), M, _ptr(Y), N, int(match), int(mismatch), int(gap), _ptr(path),
+                           ctypes.byref(K), ctypes.byref(sc), _ptr(se))
+    if rc != 0:
+        raise RuntimeError(f"oracle_local failed: {rc}")
+    return path[:K.value].copy(), int(sc.value), tuple(int(v) for v in se)

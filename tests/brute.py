@@ -145,3 +145,47 @@ def edit_solve(X, Y, S, G):
         elif c == best:
             cands.append(p)
     return best, min(cands, key=backward_moves)
+
+
+# ---------------------------------------------------------------- local alignment
+
+def node_paths(s, e):
+    """Every node path from node s to node e (steps (1,1), (1,0), (0,1))."""
+    (a0, b0), (a1, b1) = s, e
+    return [[(a0 + a, b0 + b) for a, b in p] for p in edit_all_paths(a1 - a0, b1 - b0)] if (a1 - a0) + (b1 - b0) else [[s]]
+
+
+def local_path_score(X, Y, path, MA, MM, G):
+    total = 0
+    for (a0, b0), (a1, b1) in zip(path[:-1], path[1:]):
+        if a1 == a0 + 1 and b1 == b0 + 1:
+            total += MA if X[a1 - 1] == Y[b1 - 1] else -MM
+        else:
+            total -= G
+    return total
+
+
+def local_solve(X, Y, MA, MM, G):
+    """(score, (a_s, b_s, a_e, b_e) or None, path) by enumeration: the best score
+    over every pair of nodes s <= e and every node path between them; the end is
+    the first node in row-major order whose best alignment ending there reaches
+    the score, the start the largest node in row-major order from which a path to
+    that end reaches it, the path the lexicographically smallest backward move
+    sequence (DIAG < UP < LEFT) among those paths."""
+    M, N = len(X), len(Y)
+    nodes = [(a, b) for a in range(M + 1) for b in range(N + 1)]
+
+    def best(s, e):
+        return max(local_path_score(X, Y, p, MA, MM, G) for p in node_paths(s, e))
+
+    H = {}
+    for e in nodes:
+        H[e] = max([0] + [best(s, e) for s in nodes if s[0] <= e[0] and s[1] <= e[1] and s != e])
+    S = max(H.values())
+    if S == 0:
+        return 0, None, []
+    e = min(n for n in nodes if H[n] == S)
+    starts = [s for s in nodes if s[0] <= e[0] and s[1] <= e[1] and s != e and best(s, e) == S]
+    s = max(starts)
+    cands = [p for p in node_paths(s, e) if local_path_score(X, Y, p, MA, MM, G) == S]
+    return S, (s[0], s[1], e[0], e[1]), min(cands, key=backward_moves)

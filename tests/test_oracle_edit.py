@@ -105,3 +105,51 @@ def test_split_identity_and_path(seed):
     steps = np.diff(p, axis=0)
     assert p[0].tolist() == [0, 0] and p[-1].tolist() == [M, N]
     assert all(tuple(s) in ((1, 1), (1, 0), (0, 1)) for s in steps)
+
+
+# ---------------------------------------------------------------- local alignment
+# (Smith-Waterman, named in Section 5 beside edit distance): pins of oracle.local
+
+
+@pytest.mark.parametrize("alphabet,MA,MM,G", [(2, 2, 1, 1), (3, 2, 1, 1), (3, 3, 2, 2), (4, 1, 1, 1), (2, 5, 3, 1)])
+def test_local_vs_brute_force(alphabet, MA, MM, G):
+    rng = np.random.default_rng(alphabet * 1000 + MA * 100 + MM * 10 + G)
+    for _ in range(25):
+        M, N = int(rng.integers(1, 5)), int(rng.integers(1, 5))
+        X = rng.integers(0, alphabet, M).tolist()
+        Y = rng.integers(0, alphabet, N).tolist()
+        S, se, path = brute.local_solve(X, Y, MA, MM, G)
+        p, sc, se_o = oracle.local(X, Y, MA, MM, G)
+        assert sc == S
+        if S == 0:
+            assert len(p) == 0
+        else:
+            assert se_o == se
+            assert [tuple(r) for r in p.tolist()] == path
+
+
+def test_local_closed_forms():
+    # identical sequences: the whole diagonal
+    X = [3, 1, 4, 1, 5, 9, 2, 6]
+    p, sc, se = oracle.local(X, X, 2, 1, 1)
+    assert sc == 2 * len(X) and se == (0, 0, len(X), len(X))
+    assert p.tolist() == [[k, k] for k in range(len(X) + 1)]
+    # no common symbol: score 0, empty alignment
+    p, sc, se = oracle.local([1, 2, 3], [4, 5], 2, 1, 1)
+    assert sc == 0 and len(p) == 0
+    # a single common symbol: one match step
+    p, sc, se = oracle.local([5, 1, 1], [2, 2, 5], 2, 1, 1)
+    assert sc == 2 and se == (0, 2, 1, 3) and p.tolist() == [[0, 2], [1, 3]]
+
+
+def test_local_properties():
+    rng = np.random.default_rng(5)
+    for _ in range(30):
+        X = rng.integers(0, 4, int(rng.integers(1, 40)))
+        Y = rng.integers(0, 4, int(rng.integers(1, 40)))
+        p, sc, se = oracle.local(X, Y, 2, 1, 1)
+        assert sc == oracle.local(Y, X, 2, 1, 1)[1]
+        assert sc >= (2 if set(X.tolist()) & set(Y.tolist()) else 0)
+        if sc:
+            assert p[0].tolist() == [se[0], se[1]] and p[-1].tolist() == [se[2], se[3]]
+            assert brute.local_path_score(X, Y, [tuple(r) for r in p.tolist()], 2, 1, 1) == sc
