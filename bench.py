@@ -530,6 +530,66 @@ def run_edit_workload(args):
     return 0
 
 
+def run_local_workload(args):
+    """Local alignment (Smith-Waterman, Section 5) in linear memory: 20000 vs 24000
+    random symbols over 4 sharing a mutated 5000-symbol stretch, scores +2 / -3 /
+    gap -3.  GCUPS = M N / time (three passes: end search over the whole grid,
+    start search over the box before the end, global alignment of the pieces);
+    the local oracle on one core as the CPU baseline."""
+    import torch
+
+    import oracle
+    import paper_2008_02734_b300 as dtw
+
+    X, Y = synth.workload_local_pair()
+    M, N = len(X), len(Y)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    path = torch.empty((M + N + 1, 2), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sc = dict(match=2, mismatch=3, gap=3)
+    for _ in range(max(args.warmup, 3)):
+        dtw.local_align(Xd, Yd, path_out=path, **sc)
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        p, score, se = dtw.local_align(Xd, Yd, path_out=path, **sc)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    Xh, Yh = torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()
+    Ph = torch.empty((M + N + 1, 2), dtype=torch.int32).pin_memory()
+    e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ph, _, _ = dtw.local_align(Xh, Yh, path_out=Ph, **sc)
+        e2e.append(1e3 * (time.perf_counter() - t))
+    cpu = None
+    if not args.no_cpu:
+        t = time.perf_counter()
+        _, s_ref, se_ref = oracle.local(X, Y, 2, 3, 3)
+        dt = time.perf_counter() - t
+        cpu = {"value": M * N / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+               "sample": f"one whole {M}x{N} pair through the local oracle (full tables), {dt:.1f} s",
+               "result_equal": bool(s_ref == score and tuple(se_ref) == tuple(se))}
+    line = {"metric": METRIC, "value": M * N / (np.mean(ms) / 1e3) / 1e9, "unit": "GCUPS", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": float(np.mean(ms)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+            "config": {"workload": "local alignment: 20000 vs 24000 symbols over 4 sharing a 10%-mutated "
+                                   "5000-symbol stretch, scores +2/-3/-3", "M": M, "N": N, "score": score,
+                       "start_end": list(se), "path_nodes": int(p.shape[0]), "l2": "flushed between steps"},
+            "latency_ms": _percentiles(ms),
+            "e2e": {"value": M * N / (np.mean(e2e) / 1e3) / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": 4 * (M + N),
+                    "d2h_bytes_per_step": 8 * int(ph.shape[0]) + 48},
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving_workload(args):
     """The serving stream: Poisson arrivals, lengths log-uniform in [500, max_len],
     d = 12 (FP32 frames) or 64 with equal probability, submitted at their arrival
@@ -598,7 +658,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "precision", "serving", "edit"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "precision", "serving", "edit", "local"],
                     default="int_pair")
     ap.add_argument("--batch", type=int, default=256, help="pairs of the batch workload")
     ap.add_argument("--requests", type=int, default=200, help="requests of the serving workload")
@@ -623,6 +683,8 @@ def main():
         return run_serving_workload(args)
     if args.workload == "edit":
         return run_edit_workload(args)
+    if args.workload == "local":
+        return run_local_workload(args)
     return run_ours(args)
 
 

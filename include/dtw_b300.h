@@ -191,6 +191,35 @@ DTW_API size_t dtw_footprint(int64_t M, int64_t N, int32_t d, int32_t cost_kind)
 DTW_API const char* dtw_strerror(int status);
 
 /*
+ * dtw_local_align -- local alignment (Smith-Waterman; Section 5 names it beside
+ * edit distance as a problem of the same dynamic-programming design) of two
+ * int32 symbol sequences, in linear memory on the same kernels.  Scores: +match
+ * for equal symbols, -mismatch otherwise, -gap per gap (each 0 .. 2^20);
+ *   H(a,b) = max(0, H(a-1,b-1) + score, H(a-1,b) - gap, H(a,b-1) - gap)
+ * over nodes (a, b) as in DTW_EDIT_I32, H = 0 on row 0 and column 0; the local
+ * score is S = max H.  The alignment returned (S > 0) is canonical:
+ *   end    the first node in row-major order with H = S;
+ *   start  among the nodes from which a global alignment to the end scores S,
+ *          the largest in row-major order (the shortest such alignment);
+ *   path   the canonical global alignment between them (tie order DIAG, UP,
+ *          LEFT, as for DTW_EDIT_I32), K nodes from the start to the end.
+ * Three passes: a forward sweep with the local floor (score and end), a sweep
+ * of the reversed box from the end (start), and the edit-distance recursion on
+ * the substrings between them.
+ *   X, Y       int32 symbols (host or device), none equal to INT32_MIN or
+ *              INT32_MIN + 1 (sentinels)
+ *   path_out   capacity 2*(M+N+1) int32 (host or device); K (a,b) pairs
+ *   K_out      host; the path length (0 when S = 0)
+ *   score_out  host; S
+ *   se_out     host, 4 int64: start a, start b, end a, end b (zeros when S = 0)
+ * Returns DTW_OK, DTW_EINVAL, DTW_EOVERFLOW ((M+N+2) * max(match, mismatch, gap)
+ * must stay below 2^29), DTW_ENOMEM, DTW_ECUDA or DTW_ETIMEOUT.  Blocks.
+ */
+DTW_API int dtw_local_align(const int32_t* X, int64_t M, const int32_t* Y, int64_t N, int32_t match,
+                            int32_t mismatch, int32_t gap, int32_t* path_out, int64_t* K_out, int64_t* score_out,
+                            int64_t* se_out);
+
+/*
  * dtw_path_discrepancy -- the alignment discrepancy of two warping paths of the
  * same M x N problem (Section 4.3, Results): for every cell (i, j) of path 1,
  * its row error min |j - k| over the cells (i, k) of path 2 and its column error

@@ -82,6 +82,7 @@ def _load():
         "dtw_set_option": (ctypes.c_int, [i32, i64]),
         "dtw_cost_noalloc": (ctypes.c_int, [vp, i64, vp, i64, i32, i32, vp, vp]),
         "dtw_path_discrepancy": (ctypes.c_int, [vp, i64, vp, i64, i64, i64, vp, vp]),
+        "dtw_local_align": (ctypes.c_int, [vp, i64, vp, i64, i32, i32, i32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -110,7 +111,7 @@ def __getattr__(name):
 # exported names of the C ABI, for the symbol check
 ABI_FUNCTIONS = ("dtw_align", "dtw_cost", "dtw_align_batch", "dtw_submit", "dtw_poll", "dtw_set_stream",
                  "dtw_set_budget", "dtw_set_arena", "dtw_footprint", "dtw_strerror", "dtw_get_stats",
-                 "dtw_set_option", "dtw_cost_noalloc", "dtw_path_discrepancy")
+                 "dtw_set_option", "dtw_cost_noalloc", "dtw_path_discrepancy", "dtw_local_align")
 
 
 def _strerror(status: int) -> str:
@@ -275,6 +276,24 @@ def edit_align(X, Y, *, sub: int = 1, gap: int = 1, path_out=None):
     K = _get_lib().dtw_align(xp, M, yp, N, 1, EDIT_I32, ctypes.c_void_p(path.data_ptr()), ctypes.byref(c))
     _check(K, "dtw_align")
     return path[:K], int(c.value)
+
+
+def local_align(X, Y, *, match: int = 2, mismatch: int = 1, gap: int = 1, path_out=None):
+    """Local alignment (Smith-Waterman, Section 5) of two int32 symbol sequences
+    in linear memory: returns (node path from the start to the end node, an int32
+    (K, 2) tensor, empty when the score is 0; score; (a_s, b_s, a_e, b_e))."""
+    keep, xp, M, yp, N, d, kind, on_cuda, cu = _prep_pair(X, Y)
+    if kind != ABS_I32 or d != 1:
+        raise TypeError("local alignment takes 1-D int32 symbol sequences")
+    if cu is not None:
+        _sync_stream(cu)
+    path = _node_path_buffer(M, N, cu) if path_out is None else path_out
+    K, sc = ctypes.c_int64(), ctypes.c_int64()
+    se = (ctypes.c_int64 * 4)()
+    _check(_get_lib().dtw_local_align(xp, M, yp, N, int(match), int(mismatch), int(gap),
+                                      ctypes.c_void_p(path.data_ptr()), ctypes.byref(K), ctypes.byref(sc), se),
+           "dtw_local_align")
+    return path[:K.value], int(sc.value), tuple(int(v) for v in se)
 
 
 def edit_distance(X, Y, *, sub: int = 1, gap: int = 1) -> int:

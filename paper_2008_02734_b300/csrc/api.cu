@@ -4,6 +4,7 @@
 // and reads back one small control block to learn whether another level exists.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <unordered_map>
@@ -37,6 +38,7 @@ struct Ctx {
     int use_graph = 1;
     int variant = 0;  // integer sweep variant (rows per lane), see sweep_band_rows
     int32_t esub = 1, egap = 1;  // edit distance: substitution and gap costs
+    int32_t ematch = 0;          // and the match cost (local alignment's passes set it negative)
     // cached executable graph of the level loop and the parameters it was built for
     struct LevelGraph {
         cudaGraphExec_t exec = nullptr;
@@ -228,7 +230,8 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         for (int b = 0; b < B; ++b) {
             if (M[b] < 1 || N[b] < 1 || M[b] >= (1LL << 30) || N[b] >= (1LL << 30)) return DTW_EINVAL;
             // exact int32 accumulation: every node value is at most (M+N) max(sub, gap) plus a corner term
-            if ((M[b] + N[b] + 2) * (long long)std::max(c.esub, c.egap) >= (1LL << 29)) return DTW_EOVERFLOW;
+            const long long cmax = std::max<long long>(std::max(c.esub, c.egap), std::llabs((long long)c.ematch));
+            if ((M[b] + N[b] + 2) * cmax >= (1LL << 29)) return DTW_EOVERFLOW;
             Mv.push_back(M[b] + 1);
             Nv.push_back(N[b] + 1);
         }
@@ -278,6 +281,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         p.flags = 0;
         p.esub = c.esub;
         p.egap = c.egap;
+        p.ematch = c.ematch;
         row_off += M[b];
         if (edit) {
             // [pad, symbols..., pad] for X and for Y
@@ -521,6 +525,159 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     return map_device_error(hc.err);
 }
 
+// Local alignment (Smith-Waterman) in linear memory, three passes on the node
+// grid of the padded sequences (X padded with one sentinel, Y with another, so
+// that the corner node never counts as a match):
+//   1. a forward KIND_LOCAL sweep with the local floor finds the best score S
+//      and the first node e in row-major order that reaches it;
+//   2. a sweep of the reversed box (0,0)..e without the floor finds, among the
+//      nodes from which a global alignment to e scores S, the largest in
+//      row-major order: the start s;
+//   3. the edit-kind recursion aligns the substrings between s and e with the
+//      scores as costs (match -match, mismatch, gap), canonically; its node path
+//      is shifted to the whole grid.
+int run_local(Ctx& c, const int32_t* X, int64_t M, const int32_t* Y, int64_t N, int32_t ma, int32_t mm, int32_t g,
+              int32_t* path_out, int64_t* K_out, int64_t* score_out, int64_t* se_out) {
+    const int64_t Mn = M + 1, Nn = N + 1;
+    const int U = sweep_block_cols(KIND_LOCAL, 1), BR = sweep_band_rows(KIND_LOCAL, 1), G = sweep_group_bands(KIND_LOCAL);
+    const long long nb_max = (Mn + BR - 1) / BR + 1;
+    const size_t fx = align_up((size_t)(M + 2) * 4), fy = align_up((size_t)(N + 2) * 4);
+    const Layout L = make_layout(1, Mn, Nn, (long long)(fx + fy), 0);
+    const size_t best_off = align_up((size_t)L.total);
+    void* wsv = nullptr;
+    int rc = workspace(c, best_off + align_up(16 * (size_t)nb_max), &wsv);
+    if (rc) return rc;
+    char* ws = static_cast<char*>(wsv);
+    cudaStream_t st = c.stream;
+    const bool xd = is_device_ptr(X), yd = is_device_ptr(Y);
+    int32_t* Xp = reinterpret_cast<int32_t*>(ws + L.feat);
+    int32_t* Yp = reinterpret_cast<int32_t*>(ws + L.feat + fx);
+    cudaError_t e = launch_fill_i32(Xp, M + 2, kEditPad, st);
+    if (e == cudaSuccess) e = launch_fill_i32(Yp, N + 2, kEditPad + 1, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(Xp + 1, X, 4 * (size_t)M, xd ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(Yp + 1, Y, 4 * (size_t)N, yd ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    PairDesc pd{};
+    pd.X = Xp;
+    pd.Y = Yp;
+    pd.M = (int32_t)Mn;
+    pd.N = (int32_t)Nn;
+    pd.esub = mm;
+    pd.egap = g;
+    pd.ematch = -ma;
+    PairDesc* d_pairs = reinterpret_cast<PairDesc*>(ws + L.pairs);
+    Box* d_box = reinterpret_cast<Box*>(ws + L.boxA);
+    Sweep* d_sweeps = reinterpret_cast<Sweep*>(ws + L.sweeps);
+    SweepRes* d_sres = reinterpret_cast<SweepRes*>(ws + L.sres);
+    LevelCtl* d_ctl = reinterpret_cast<LevelCtl*>(ws + L.ctl);
+    int32_t* d_best = reinterpret_cast<int32_t*>(ws + best_off);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_pairs, &pd, sizeof(pd), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return DTW_ECUDA;
+
+    // one KIND_LOCAL sweep of box (0,0) .. (H-1, W-1): the best node's value and frame cell
+    auto pass = [&](int32_t H, int32_t W, int local, int32_t* v, int32_t* p, int32_t* q) -> int {
+        Box root{};
+        root.pair = 0;
+        root.H = H;
+        root.W = W;
+        root.flags = BOX_ROOT;
+        root.known_i = -1;
+        root.known_f = NAN;
+        LevelCtl ctl0{};
+        ctl0.epoch_base = c.epoch;
+        cudaError_t err = cudaMemcpyAsync(d_box, &root, sizeof(root), cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(d_ctl, &ctl0, sizeof(ctl0), cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess) err = cudaMemsetAsync(ws + L.bufpool, 0, 8 * (size_t)L.cap_buf, st);
+        if (err == cudaSuccess) err = cudaMemsetAsync(d_best, 0, 16 * (size_t)nb_max, st);
+        PlanArgs pa{d_box, 1, d_pairs, MODE_COST, KIND_LOCAL, 0, U, BR, G, d_sweeps, d_ctl,
+                    L.cap_sweeps, L.cap_buf, L.cap_out, nullptr, 0, false, nullptr};
+        pa.local = local;
+        if (err == cudaSuccess) err = launch_plan(pa, st);
+        LevelCtl hc{};
+        if (err == cudaSuccess) err = cudaMemcpyAsync(&hc, d_ctl, sizeof(hc), cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+        if (err != cudaSuccess) return DTW_ECUDA;
+        if (hc.err != ERR_NONE) return map_device_error(hc.err);
+        c.epoch = hc.epoch_base;
+        if (hc.n_bands > nb_max) return DTW_EINTERNAL;
+        SweepArgs sa{d_sweeps, d_ctl, reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres,
+                     1, c.spin_limit, -1};
+        sa.best = d_best;
+        err = launch_sweep(KIND_LOCAL, 1, false, sa, c.num_sms, hc.n_tickets, st, 0);
+        std::vector<int32_t> hb(4 * (size_t)hc.n_bands);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(hb.data(), d_best, hb.size() * 4, cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(&hc, d_ctl, sizeof(hc), cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+        if (err != cudaSuccess) return DTW_ECUDA;
+        if (hc.err != ERR_NONE) return map_device_error(hc.err);
+        // bands run down the frame rows: the lexicographic minimum of (value, row, column)
+        bool any = false;
+        for (long long b = 0; b < hc.n_bands; ++b) {
+            const int32_t* r = &hb[4 * b];
+            if (!r[3]) return DTW_EINTERNAL;
+            if (!any || r[0] < *v || (r[0] == *v && (r[1] < *p || (r[1] == *p && r[2] < *q)))) {
+                *v = r[0];
+                *p = r[1];
+                *q = r[2];
+                any = true;
+            }
+        }
+        return any ? DTW_OK : DTW_EINTERNAL;
+    };
+    int32_t v1 = 0, p1 = 0, q1 = 0;
+    rc = pass((int32_t)Mn, (int32_t)Nn, 1, &v1, &p1, &q1);
+    if (rc) return rc;
+    const int64_t S = -(int64_t)v1;
+    *score_out = S;
+    for (int k = 0; k < 4; ++k) se_out[k] = 0;
+    if (S <= 0) {  // no positive local alignment
+        *K_out = 0;
+        return DTW_OK;
+    }
+    const int32_t ae = p1, be = q1;
+    int32_t v2 = 0, p2 = 0, q2 = 0;
+    rc = pass(ae + 1, be + 1, 2, &v2, &p2, &q2);
+    if (rc) return rc;
+    // the reversed sweep's values carry the cost of the step out of e: -match or mismatch
+    if (v2 + S != -(int64_t)ma && v2 + S != (int64_t)mm) return DTW_EINTERNAL;
+    const int32_t as = ae - p2, bs = be - q2;
+    if (as < 0 || bs < 0 || as >= ae || bs >= be) return DTW_EINTERNAL;
+    // 3. the canonical global alignment of the substrings between s and e
+    const int32_t sv[3] = {c.esub, c.egap, c.ematch};
+    c.esub = mm;
+    c.egap = g;
+    c.ematch = -ma;
+    const void* xs[1] = {X + as};
+    const void* ys[1] = {Y + bs};
+    const int64_t ms[1] = {ae - as}, ns[1] = {be - bs};
+    int32_t* ps[1] = {path_out};
+    int64_t K = 0;
+    double cost = 0;
+    rc = run_batch(c, 1, xs, ms, ys, ns, 1, KIND_EDIT, true, ps, &K, &cost);
+    c.esub = sv[0];
+    c.egap = sv[1];
+    c.ematch = sv[2];
+    if (rc) return rc;
+    if (is_device_ptr(path_out)) {
+        e = launch_offset_path(path_out, K, as, bs, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return DTW_ECUDA;
+    } else {
+        for (int64_t t = 0; t < K; ++t) {
+            path_out[2 * t] += as;
+            path_out[2 * t + 1] += bs;
+        }
+    }
+    *K_out = K;
+    se_out[0] = as;
+    se_out[1] = bs;
+    se_out[2] = ae;
+    se_out[3] = be;
+    return DTW_OK;
+}
+
 int run_plain(Ctx& c, const void* X, int64_t M, const void* Y, int64_t N, int d, int kind, int32_t* path_out,
               int64_t* K_out, double* cost_out) {
     const size_t esize = 4;
@@ -666,6 +823,21 @@ size_t dtw_footprint(int64_t M, int64_t N, int32_t d, int32_t cost_kind) {
     const Layout L = make_layout(1, M, N, (long long)align_up((size_t)M * d * 4) + (long long)align_up((size_t)N * d * 4),
                                  M + N - 1);
     return L.total;
+}
+
+int dtw_local_align(const int32_t* X, int64_t M, const int32_t* Y, int64_t N, int32_t match, int32_t mismatch,
+                    int32_t gap, int32_t* path_out, int64_t* K_out, int64_t* score_out, int64_t* se_out) {
+    if (!X || !Y || !path_out || !K_out || !score_out || !se_out || M < 1 || N < 1 || M >= (1LL << 30) ||
+        N >= (1LL << 30))
+        return DTW_EINVAL;
+    if (match < 0 || mismatch < 0 || gap < 0 || match > (1 << 20) || mismatch > (1 << 20) || gap > (1 << 20))
+        return DTW_EINVAL;
+    if ((M + N + 2) * (long long)std::max(match, std::max(mismatch, gap)) >= (1LL << 29)) return DTW_EOVERFLOW;
+    Ctx& c = ctx();
+    std::lock_guard<std::mutex> g(c.mu);
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    return run_local(c, X, M, Y, N, match, mismatch, gap, path_out, K_out, score_out, se_out);
 }
 
 int dtw_path_discrepancy(const int32_t* P1, int64_t K1, const int32_t* P2, int64_t K2, int64_t M, int64_t N,

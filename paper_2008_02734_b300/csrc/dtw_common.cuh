@@ -34,7 +34,14 @@ constexpr int KIND_EUCB = 3; // Euclidean distance in the expanded form with BF1
 // step into reversed node p consumes forward symbol p + 1).  The split sums
 // F + B with no cell term.
 constexpr int KIND_EDIT = 4;
-__host__ __device__ constexpr bool int_kind(int k) { return k == KIND_ABS || k == KIND_EDIT; }
+// Local alignment (Smith-Waterman, named in Section 5 beside edit distance):
+// the edit update on the node grid with scores turned into costs (match cost
+// -match, mismatch cost mismatch, gap cost gap), and for the end search the
+// local floor E = min(E, 0) (H = max(H, 0)).  Its sweeps also keep each band's
+// best node (lowest value, then first in row-major order of the sweep frame).
+constexpr int KIND_LOCAL = 5;
+__host__ __device__ constexpr bool int_kind(int k) { return k == KIND_ABS || k == KIND_EDIT || k == KIND_LOCAL; }
+__host__ __device__ constexpr bool edit_kind(int k) { return k == KIND_EDIT || k == KIND_LOCAL; }
 // The sentinel symbol at both ends of an edit pair (inputs may not contain it).
 constexpr int32_t kEditPad = (int32_t)0x80000000;
 
@@ -57,7 +64,8 @@ struct PairDesc {
     int32_t row_off;    // offset of the pair's rows in the per-row path arrays
     int32_t flags;
     int32_t* path;      // device path buffer, 2*(M+N-1) int32
-    int32_t esub, egap; // KIND_EDIT: substitution and gap costs
+    int32_t esub, egap; // KIND_EDIT / KIND_LOCAL: substitution and gap costs
+    int32_t ematch;     // and the cost of a match (0 for edit distance, negative for local scores)
 };
 
 struct PairRes {
@@ -109,7 +117,9 @@ struct Sweep {
     long long band_begin;  // level band number of the sweep's first band
     long long buf_off;     // boundary-row pool offset, in 64-bit words (1 or 2 per column)
     long long out_off;     // out pool offset: nout rows of ostride values, in the sweep's own frame order
-    int32_t esub, egap;    // KIND_EDIT: substitution and gap costs
+    int32_t esub, egap;    // KIND_EDIT / KIND_LOCAL: substitution and gap costs
+    int32_t ematch;        // match cost
+    int32_t floor;         // KIND_LOCAL: the local floor E = min(E, 0) applies
 };
 
 struct SweepRes {
@@ -235,6 +245,7 @@ template <> struct AccOf<KIND_EUCF> {
 };
 template <> struct AccOf<KIND_EUCB> : AccOf<KIND_EUCF> {};
 template <> struct AccOf<KIND_EDIT> : AccOf<KIND_ABS> {};
+template <> struct AccOf<KIND_LOCAL> : AccOf<KIND_ABS> {};
 
 __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return __vimin3_s32(a, b, c); }
 // Accumulated costs are sums of nonnegative frame costs (or +infinity), and for
@@ -261,6 +272,7 @@ template <> struct Frame<KIND_ABS, 1> {
     __device__ __forceinline__ void load_shared(const void* p) { v = *static_cast<const int32_t*>(p); }
 };
 template <> struct Frame<KIND_EDIT, 1> : Frame<KIND_ABS, 1> {};
+template <> struct Frame<KIND_LOCAL, 1> : Frame<KIND_ABS, 1> {};
 
 template <int DIM> struct Frame<KIND_EUC, DIM> {
     float v[DIM];
@@ -341,8 +353,9 @@ __device__ __forceinline__ int32_t frame_cost(const Frame<KIND_ABS, 1>& a, const
 // Edit distance: no cost sits on a node, so the split sums F + B alone; the
 // sweeps and the base case use edit_delta and the gap instead.
 __device__ __forceinline__ int32_t frame_cost(const Frame<KIND_EDIT, 1>&, const Frame<KIND_EDIT, 1>&) { return 0; }
-__device__ __forceinline__ int32_t edit_delta(int32_t x, int32_t y, int32_t sub, int32_t gap) {
-    return (x == y ? 0 : sub) - gap;
+__device__ __forceinline__ int32_t frame_cost(const Frame<KIND_LOCAL, 1>&, const Frame<KIND_LOCAL, 1>&) { return 0; }
+__device__ __forceinline__ int32_t edit_delta(int32_t x, int32_t y, int32_t match, int32_t sub, int32_t gap) {
+    return (x == y ? match : sub) - gap;
 }
 
 // Exact FP32 -> FP64 widening of a frame cost with integer operations (the

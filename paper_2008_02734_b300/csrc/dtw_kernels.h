@@ -18,6 +18,7 @@ struct SweepArgs {
     int d;
     int spin_limit;
     long long skip_ticket;  // test hook: this level band never publishes (-1: none)
+    int32_t* best = nullptr;  // KIND_LOCAL: 4 int32 per level band (value, frame row, column, written)
 };
 
 // Sweep variants
@@ -51,6 +52,8 @@ struct PlanArgs {
     long long cap_items;
     bool reset_base;  // also empty the base list (its boxes have been finished)
     Box* copy_to;     // non-null: the planned boxes are also copied here (same index)
+    int local = 0;    // KIND_LOCAL, MODE_COST: 1 forward sweep with the local floor,
+                      // 2 sweep of the reversed box without it; frame rows along X
 };
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st);
 
@@ -103,6 +106,7 @@ struct AssembleArgs {
 };
 cudaError_t launch_assemble(const AssembleArgs& a, cudaStream_t st);
 cudaError_t launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st);
+cudaError_t launch_offset_path(int32_t* p, long long K, int32_t da, int32_t db, cudaStream_t st);
 // minmax: 4 int32 per pair of scratch (min X, max X, min Y, max Y).  pair_err
 // (optional): per-pair flags set to 1 instead of failing the whole call.
 cudaError_t launch_int_range_check(const PairDesc* pairs, int n_pairs, int max_len, int32_t* minmax, LevelCtl* ctl,

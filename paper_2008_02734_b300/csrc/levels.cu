@@ -103,7 +103,13 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             const Box b = a.boxes[bi];
             if (a.copy_to && dir == 0) a.copy_to[bi] = b;
             const PairDesc pd = a.pairs[b.pair];
-            const Geom g = geom_of(b);
+            Geom g = geom_of(b);
+            if (a.local) {  // local sweeps keep frame rows along X (row-major order of the best node)
+                g.axis = 0;
+                g.P = b.H;
+                g.Q = b.W;
+                g.r = (g.P - 1) / 2;
+            }
             sw.box = bi;
             sw.dir = dir;
             sw.axis = g.axis;
@@ -133,14 +139,14 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             sw.colseq = g.axis ? pd.X : pd.Y;
             const int rb0 = g.axis ? b.j0 : b.i0, rlen = g.axis ? b.W : b.H;
             const int cb0 = g.axis ? b.i0 : b.j0, clen = g.axis ? b.H : b.W;
-            if (dir == 0) {
+            if (dir == 0 && a.local != 2) {
                 sw.rbase = rb0;
                 sw.rstep = 1;
                 sw.cbase = cb0;
                 sw.cstep = 1;
             } else {  // the reversed series X_R, Y_R of Algorithm 2
                 // edit distance: the step into reversed node p consumes forward symbol p + 1
-                const int shift = a.kind == KIND_EDIT ? 1 : 0;
+                const int shift = edit_kind(a.kind) ? 1 : 0;
                 sw.rbase = rb0 + rlen - 1 + shift;
                 sw.rstep = -1;
                 sw.cbase = cb0 + clen - 1 + shift;
@@ -148,6 +154,8 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             }
             sw.esub = pd.esub;
             sw.egap = pd.egap;
+            sw.ematch = pd.ematch;
+            sw.floor = a.local == 1 ? 1 : 0;
             nb = sw.nbands;
             // boundary words per column: one for an untagged integer sweep, two otherwise
             const int nw = (int_kind(a.kind) && sw.tag_row < 0) ? 1 : 2;
@@ -577,11 +585,12 @@ __global__ void __launch_bounds__(32 * kBaseWarps) base_kernel(BaseArgs a) {
                     yc.load(cs, cbase + q, a.d);
                     // edit distance: delta on the diagonal move, the gap on every move
                     const auto c = [&]() {
-                        if constexpr (KIND == KIND_EDIT) return pd.egap;
+                        if constexpr (edit_kind(KIND)) return pd.egap;
                         else return frame_cost(xr, yc);
                     }();
                     const Acc dd = [&]() {
-                        if constexpr (KIND == KIND_EDIT) return dprev + edit_delta(xr.v, yc.v, pd.esub, pd.egap);
+                        if constexpr (edit_kind(KIND))
+                            return dprev + edit_delta(xr.v, yc.v, pd.ematch, pd.esub, pd.egap);
                         else return dprev;
                     }();
                     const Acc m = min3(dd, up, left);
@@ -741,6 +750,22 @@ cudaError_t launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t st)
     if (n <= 0) return cudaSuccess;
     long long g = (n + 255) / 256;
     fill_i32_kernel<<<(int)(g < 4096 ? g : 4096), 256, 0, st>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+// Node path of a local alignment: the global alignment of the substrings gives
+// nodes relative to the start node; shift them to the whole problem's grid.
+__global__ void offset_path_kernel(int32_t* p, long long K, int32_t da, int32_t db) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < K; t += (long long)gridDim.x * blockDim.x) {
+        p[2 * t] += da;
+        p[2 * t + 1] += db;
+    }
+}
+
+cudaError_t launch_offset_path(int32_t* p, long long K, int32_t da, int32_t db, cudaStream_t st) {
+    if (K <= 0) return cudaSuccess;
+    long long g = (K + 255) / 256;
+    offset_path_kernel<<<(int)(g < 4096 ? g : 4096), 256, 0, st>>>(p, K, da, db);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@
 // cell copies the tag of its backpointer (first minimum in the order DIAG, UP,
 // LEFT).  The tag reaching the last cell names the column where the canonical
 // backtrace meets the split row, so that cell lies on the canonical path.
+#include <climits>
 #include <type_traits>
 
 #include "dtw_common.cuh"
@@ -383,7 +384,8 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     const int rbase = sp->rbase, rstep = sp->rstep;
     const void* rowseq = sp->rowseq;
     const int out_row0 = sp->out_row0, nout = sp->nout, tag_row = sp->tag_row, ostride = sp->ostride;
-    const int32_t esub = sp->esub, egap = sp->egap;  // KIND_EDIT
+    const int32_t esub = sp->esub, egap = sp->egap, ematch = sp->ematch;  // edit kinds
+    const bool lfloor = sp->floor != 0;                                      // KIND_LOCAL
     const uint32_t ep_out = sp->epoch0 + (uint32_t)band + 1u;
     unsigned long long* buf = A.bufpool + sp->buf_off;
     Acc* outp = static_cast<Acc*>(A.outpool) + sp->out_off;
@@ -508,6 +510,14 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
 
     Acc L[R];  // D(p0+k, q-1): the column left of the current one
     int LT[R];
+    // KIND_LOCAL: per row of the lane, the lowest value and its first column
+    Acc bestv[KIND == KIND_LOCAL ? R : 1];
+    int bestq[KIND == KIND_LOCAL ? R : 1];
+#pragma unroll
+    for (int k = 0; k < (KIND == KIND_LOCAL ? R : 1); ++k) {
+        bestv[k] = INF;
+        bestq[k] = -1;
+    }
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         L[k] = INF;
@@ -659,16 +669,27 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                     // edit distance: the diagonal move carries delta, every move the gap
                     const auto cc = [&]() {
                         if constexpr (TC) return c;
-                        else if constexpr (KIND == KIND_EDIT) return egap;
+                        else if constexpr (edit_kind(KIND)) return egap;
                         else return frame_cost(xr[k], yc[u]);
                     }();
                     const Acc a_dd = [&]() {
-                        if constexpr (KIND == KIND_EDIT) return a_dg + edit_delta(xr[k].v, yc[u].v, esub, egap);
+                        if constexpr (edit_kind(KIND))
+                            return a_dg + edit_delta(xr[k].v, yc[u].v, ematch, esub, egap);
                         else return a_dg;
                     }();
                     const Acc lf = L[k];
                     const Acc m = min3(a_dd, a_up, lf);
-                    const Acc nv = m + cc;
+                    Acc nv = m + cc;
+                    if constexpr (KIND == KIND_LOCAL) {
+                        // local floor (end search), then the row's best node: the first
+                        // column attaining the lowest value (q < Q: the last block may
+                        // be partial)
+                        if (lfloor) nv = min(nv, 0);
+                        if ((!CHECK || q < Q) && nv < bestv[k]) {
+                            bestv[k] = nv;
+                            bestq[k] = q;
+                        }
+                    }
                     int t = 0;
                     if constexpr (TAG) {
                         const int t_lf = LT[k];
@@ -737,6 +758,36 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         }
     }
     if (to_ring && lane == 31) st_release_cta(&sm.uprog[g + 1], nblk);
+    if constexpr (KIND == KIND_LOCAL) {
+        // the band's best node: lowest value, then lowest frame row, then column
+        Acc v = INF;
+        int bp = INT_MAX, bq = INT_MAX;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (p0 + k < rows && bestq[k] >= 0 && bestv[k] < v) {
+                v = bestv[k];
+                bp = p0 + k;
+                bq = bestq[k];
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const Acc ov = __shfl_xor_sync(kFull, v, o);
+            const int op = __shfl_xor_sync(kFull, bp, o), oq = __shfl_xor_sync(kFull, bq, o);
+            if (ov < v || (ov == v && (op < bp || (op == bp && oq < bq)))) {
+                v = ov;
+                bp = op;
+                bq = oq;
+            }
+        }
+        if (lane == 0 && A.best) {
+            int32_t* b = A.best + 4 * (sp->band_begin + band);
+            b[0] = v;
+            b[1] = bp;
+            b[2] = bq;
+            b[3] = 1;
+        }
+    }
     if constexpr (SPECIAL) {
         if (end_k >= 0 && end_k < R) {
             SweepRes* r = A.res + sweep_idx;
@@ -1093,7 +1144,7 @@ constexpr int kIntRVar[kSweepVariants] = {kIntR, 2, 8};
 int sweep_block_cols(int kind, int d, int variant) { return int_kind(kind) ? kIntU : (d == 12 ? kEucU : 2); }
 int sweep_band_rows(int kind, int d, int variant) {
     if (kind == KIND_ABS) return 32 * kIntRVar[(unsigned)variant < (unsigned)kSweepVariants ? variant : 0];
-    if (kind == KIND_EDIT) return 32 * kIntR;
+    if (edit_kind(kind)) return 32 * kIntR;
     return d == 12 ? 32 * kEucR : (d == 64 ? 32 : 64);
 }
 int sweep_group_bands(int kind) { return int_kind(kind) ? group_of<KIND_ABS>() : group_of<KIND_EUC>(); }
@@ -1108,6 +1159,7 @@ cudaError_t sweep_prepare(int kind, int d, bool tags, int variant) {
     }
     if (kind == KIND_EDIT) return tags ? setup_one<KIND_EDIT, kIntR, kIntU, 1, true>(&nb)
                                        : setup_one<KIND_EDIT, kIntR, kIntU, 1, false>(&nb);
+    if (kind == KIND_LOCAL) return setup_one<KIND_LOCAL, kIntR, kIntU, 1, false>(&nb);
     if (kind == KIND_EUCB) return setup_one<KIND_EUCB, 1, 2, 64, false>(&nb);
     if (kind == KIND_EUCF) {
         if (d == 12) return setup_one<KIND_EUCF, kEucR, kEucU, 12, false>(&nb);
@@ -1134,6 +1186,7 @@ cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num
     if (kind == KIND_EDIT)
         return tags ? launch_one<KIND_EDIT, kIntR, kIntU, 1, true>(A, num_sms, max_blocks, st)
                     : launch_one<KIND_EDIT, kIntR, kIntU, 1, false>(A, num_sms, max_blocks, st);
+    if (kind == KIND_LOCAL) return launch_one<KIND_LOCAL, kIntR, kIntU, 1, false>(A, num_sms, max_blocks, st);
     if (kind == KIND_EUCB) return launch_one<KIND_EUCB, 1, 2, 64, false>(A, num_sms, max_blocks, st);
     if (kind == KIND_EUCF) {
         if (d == 12) return launch_one<KIND_EUCF, kEucR, kEucU, 12, false>(A, num_sms, max_blocks, st);

@@ -193,3 +193,34 @@ def edit_pair(seed: int, M: int, rate: float = 0.1, alphabet: int = 4):
 def workload_edit_pair(seed: int = 4, M: int = 20000):
     """A 20000-symbol sequence over 4 symbols against a 10%-mutated copy."""
     return edit_pair(seed, M)
+
+
+def local_pair(seed: int, M: int, N: int, core: int, rate: float = 0.1, alphabet: int = 4):
+    """Sequences for local alignment: X and Y uniform over ``alphabet`` symbols,
+    with a ``core``-symbol stretch of X planted, after point mutations (as in
+    edit_pair), at a random place in Y."""
+    rng = np.random.default_rng(seed)
+    X = rng.integers(0, alphabet, M).astype(np.int32)
+    Y = rng.integers(0, alphabet, N).astype(np.int32)
+    core = max(1, min(core, M, N // 2))
+    i0 = int(rng.integers(0, M - core + 1))
+    mut = []
+    for v in X[i0:i0 + core]:
+        if rng.random() < rate:
+            kind = rng.integers(3)
+            if kind == 0:
+                mut.append(int(rng.integers(0, alphabet)))
+            elif kind == 2:
+                mut.append(int(v))
+                mut.append(int(rng.integers(0, alphabet)))
+        else:
+            mut.append(int(v))
+    mut = np.asarray(mut[: N], dtype=np.int32)
+    j0 = int(rng.integers(0, N - len(mut) + 1))
+    Y[j0:j0 + len(mut)] = mut
+    return X, Y
+
+
+def workload_local_pair(seed: int = 5):
+    """20000 vs 24000 random symbols sharing a mutated 5000-symbol stretch."""
+    return local_pair(seed, 20000, 24000, 5000)
