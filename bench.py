@@ -157,7 +157,7 @@ def cpu_oracle_baseline(name: str, budget_s: float = 20.0):
             break
     return {"value": cells / spent / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
             "sample": f"{runs} whole {len(X)}x{len(Y)} pair(s) through oracle 1 (textbook DTW with "
-                      f"backpointers, int64), {spent:.1f} s"}
+                      f"backpointers, {'int64' if X.dtype == np.int32 else 'FP64'}), {spent:.1f} s"}
 
 
 def run_reference(args):
@@ -317,6 +317,16 @@ def run_ours(args):
                 "sweep_ms_per_step": sweep_ms / args.steps, "sweep_launches_per_step": sweep_launches / args.steps,
                 "processed_cells_per_step": cells_proc / args.steps}
     cpu = None if args.no_cpu else cpu_oracle_baseline(args.workload, budget_s=args.cpu_budget)
+    disc = None
+    if args.workload == "plain_float" and not args.no_cpu:
+        # Section 4.3's discrepancy of the GPU path against the oracle's: float
+        # costs may tie differently, so the two optimal paths need not coincide
+        import oracle
+        p_ref, _ = oracle.dtw(X, Y)
+        err, emax = dtw.path_discrepancy(step()[0], p_ref, M, N)
+        e = err.cpu().numpy().ravel()
+        disc = {"of": "GPU path vs oracle 1 path", "max_frames": emax,
+                "within_frames": {str(f): float(np.mean(e <= f)) for f in (0, 1, 2)}}
     line = {
         "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total / args.steps, "higher_is_better": True,
@@ -334,6 +344,7 @@ def run_ours(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "vs_plain_gpu": None if plain is None else {"plain": plain, "speedup": value / ws / plain["gcups"]},
+        "path_discrepancy_vs_oracle": disc,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
