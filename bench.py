@@ -160,6 +160,22 @@ def cpu_oracle_baseline(name: str, budget_s: float = 20.0):
                       f"backpointers, {'int64' if X.dtype == np.int32 else 'FP64'}), {spent:.1f} s"}
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks: the whole job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gcups(cells_per_rank: float, ranks: int, steps: int, total_ms: float) -> float:
+    """Cells of every rank's steps over the slowest rank's time (replicas: weak scaling)."""
+    return ranks * cells_per_rank * steps / (total_ms / 1e3) / 1e9
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -256,13 +272,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     dtw.set_option(dtw.OPT_TIMING, 0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    my_total = sum(step_ms)
-    total = my_total
-    if ws > 1:
-        t = torch.tensor([my_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = ws * M * N * args.steps / (total / 1e3) / 1e9
+    total = max_over_ranks(sum(step_ms), dev)
+    value = whole_job_gcups(M * N, ws, args.steps, total)
 
     # end to end: pinned host inputs and outputs through the same public call
     Xh = torch.from_numpy(X).pin_memory()
@@ -278,12 +289,8 @@ def run_ours(args):
         p, c = dtw.align(Xh, Yh, path_out=Ph)
         e2e_ms.append(1e3 * (time.perf_counter() - t))
         Kh = p.shape[0]
-    e2e_total = sum(e2e_ms)
-    if ws > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = ws * M * N * args.steps / (e2e_total / 1e3) / 1e9
+    e2e_total = max_over_ranks(sum(e2e_ms), dev)
+    e2e_value = whole_job_gcups(M * N, ws, args.steps, e2e_total)
 
     # the paper's plain FP64 GPU form on the same pair (one run; its own clock)
     plain = None
