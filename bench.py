@@ -95,7 +95,10 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples: DTW_CLOCKS_DIR if set (to keep them), else the temp directory
+        import tempfile
+        d = os.environ.get("DTW_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"dtw_clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
