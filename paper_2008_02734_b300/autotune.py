@@ -50,3 +50,33 @@ def tune(M: int, N: int, *, variants=VARIANTS, base_areas=BASE_AREAS, reps: int 
     set_option(OPT_SWEEP_VARIANT, best["variant"] if apply else 0)
     set_option(OPT_BASE_AREA, best["base_area"] if apply else 16384)
     return {"variant": best["variant"], "base_area": best["base_area"], "ms": best["ms"], "table": table}
+
+
+def tune_batch(Xs, Ys, *, base_areas=BASE_AREAS, reps: int = 2, apply: bool = True, **align_kw) -> dict:
+    """The base-case cutoff for a batch: times align_batch on the caller's own
+    pairs (device tensors) for every candidate area (median of ``reps`` after
+    one warm-up) and returns {"base_area", "ms", "table"}; with ``apply`` the
+    fastest is set.  Results do not depend on the cutoff (integer paths are
+    canonical; float paths are optimal within the float tolerance)."""
+    import torch
+
+    from . import align_batch
+
+    stream = torch.cuda.current_stream()
+    table = []
+    for a in base_areas:
+        set_option(OPT_BASE_AREA, a)
+        align_batch(Xs, Ys, **align_kw)
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            align_batch(Xs, Ys, **align_kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        ms.sort()
+        table.append({"base_area": a, "ms": ms[len(ms) // 2]})
+    best = min(table, key=lambda r: r["ms"])
+    set_option(OPT_BASE_AREA, best["base_area"] if apply else 16384)
+    return {"base_area": best["base_area"], "ms": best["ms"], "table": table}

@@ -364,6 +364,19 @@ def test_autotuner_applies_a_candidate():
     check_int(X, Y)
 
 
+def test_batch_autotuner_applies_a_candidate():
+    """The batch tuner sets one of its cutoffs, and the batch still matches the oracle."""
+    from paper_2008_02734_b300 import autotune
+    pairs = [synth.chroma_pair(60 + k, 300 + 40 * k, 280 + 50 * k) for k in range(5)]
+    Xs, Ys = [_cuda(x) for x, _ in pairs], [_cuda(y) for _, y in pairs]
+    r = autotune.tune_batch(Xs, Ys, base_areas=(4096, 16384))
+    assert r["base_area"] in (4096, 16384) and len(r["table"]) == 2
+    for (x, y), (p, c) in zip(pairs, dtw.align_batch(Xs, Ys)):
+        c_ref = oracle.dtw(x, y)[1]
+        assert c == pytest.approx(c_ref, rel=REL_TOL, abs=1e-9)
+        assert oracle.path_cost(x, y, p.cpu().numpy()) == pytest.approx(c_ref, rel=REL_TOL, abs=1e-9)
+
+
 def _golden_mfcc():
     with open(GOLDEN_MFCC) as f:
         rows = [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")]
