@@ -399,9 +399,12 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     int launches = (want_path ? 1 : 0) + (kind == KIND_ABS ? 3 : 0) + (edit ? 2 * B : 0);
     const int max_levels = 2 * (64 - __builtin_clzll((unsigned long long)std::max(maxM, sumN) + 1)) + 8;
     int* d_boxdone = reinterpret_cast<int*>(ws + L.boxdone);
+    int2* d_tmap = reinterpret_cast<int2*>(ws + L.tmap);
     if (!roots.empty()) {
         PlanArgs pa{cur, (int)roots.size(), d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
                     L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
+        pa.tmap = d_tmap;
+        pa.cap_tickets = L.cap_tickets;
         e = launch_plan(pa, st);
         ++launches;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
@@ -415,11 +418,14 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     if (graph) {
         SweepArgs sa{d_sweeps, d_ctl, reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres, d,
                      c.spin_limit, c.skip_publish};
+        sa.tmap = d_tmap;
         SplitArgs sp{cur,       -1,   d_pairs, d_pres, kind,     d,          halo,    d_sweeps,
                      d_sres,    ws + L.outpool, nxt, d_base,  d_ctl,      base_area, (int)L.cap_box,
                      (int)L.cap_base, d_boxdone, ws + L.partials, -1, c.num_sms};
         PlanArgs pn{nxt, -1, d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
                     L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, cur};
+        pn.tmap = d_tmap;
+        pn.cap_tickets = L.cap_tickets;
         const std::vector<long long> key{(long long)(uintptr_t)ws, (long long)L.total, L.cap_box, L.cap_base,
                                          L.cap_sweeps, L.cap_buf, L.cap_out, L.cap_items, kind, d, base_area,
                                          c.spin_limit, c.skip_publish, c.num_sms, max_levels, (long long)L.ctl,
@@ -436,6 +442,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         const int n_cur = hc.n_cur;
         SweepArgs sa{d_sweeps, d_ctl,        reinterpret_cast<unsigned long long*>(ws + L.bufpool),
                      ws + L.outpool, d_sres, d, c.spin_limit, c.skip_publish};
+        sa.tmap = d_tmap;
         cudaEvent_t s0 = nullptr, s1 = nullptr;
         if (c.timing) s0 = T.mark();
         // integer levels may mix tagged and untagged boxes
@@ -453,6 +460,8 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
             // plan the next level from the boxes the split appended (count read on the device)
             PlanArgs pa{nxt, -1, d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
                         L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
+            pa.tmap = d_tmap;
+            pa.cap_tickets = L.cap_tickets;
             if (e == cudaSuccess) e = launch_plan(pa, st);
             ++launches;
         }
@@ -593,6 +602,8 @@ int run_local(Ctx& c, const int32_t* X, int64_t M, const int32_t* Y, int64_t N, 
         PlanArgs pa{d_box, 1, d_pairs, MODE_COST, KIND_LOCAL, 0, U, BR, G, d_sweeps, d_ctl,
                     L.cap_sweeps, L.cap_buf, L.cap_out, nullptr, 0, false, nullptr};
         pa.local = local;
+        pa.tmap = reinterpret_cast<int2*>(ws + L.tmap);
+        pa.cap_tickets = L.cap_tickets;
         if (err == cudaSuccess) err = launch_plan(pa, st);
         LevelCtl hc{};
         if (err == cudaSuccess) err = cudaMemcpyAsync(&hc, d_ctl, sizeof(hc), cudaMemcpyDeviceToHost, st);
@@ -604,6 +615,7 @@ int run_local(Ctx& c, const int32_t* X, int64_t M, const int32_t* Y, int64_t N, 
         SweepArgs sa{d_sweeps, d_ctl, reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres,
                      1, c.spin_limit, -1};
         sa.best = d_best;
+        sa.tmap = reinterpret_cast<const int2*>(ws + L.tmap);
         err = launch_sweep(KIND_LOCAL, 1, false, sa, c.num_sms, hc.n_tickets, st, 0);
         std::vector<int32_t> hb(4 * (size_t)hc.n_bands);
         if (err == cudaSuccess)

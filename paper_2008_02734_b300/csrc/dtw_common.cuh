@@ -150,7 +150,7 @@ struct LevelCtl {
     unsigned long long resyncs;  // prefetch-ring refills in the sweeps
     unsigned long long polls;    // failed polls of boundary words
     int32_t levels;              // levels planned on the device (graph-driven level loop)
-    int32_t pad1;
+    int32_t tmap_on;             // the current level's tickets follow the ticket map (group-major order)
 };
 
 // ---------------------------------------------------------------- memory order

@@ -19,6 +19,7 @@ struct SweepArgs {
     int spin_limit;
     long long skip_ticket;  // test hook: this level band never publishes (-1: none)
     int32_t* best = nullptr;  // KIND_LOCAL: 4 int32 per level band (value, frame row, column, written)
+    const int2* tmap = nullptr;  // ticket -> (sweep, band group), when the plan wrote it (ctl->tmap_on)
 };
 
 // Sweep variants
@@ -54,6 +55,8 @@ struct PlanArgs {
     Box* copy_to;     // non-null: the planned boxes are also copied here (same index)
     int local = 0;    // KIND_LOCAL, MODE_COST: 1 forward sweep with the local floor,
                       // 2 sweep of the reversed box without it; frame rows along X
+    int2* tmap = nullptr;      // non-null: write the ticket map (group-major ticket order)
+    long long cap_tickets = 0; // its capacity; a level that needs more uses the plain order
 };
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st);
 

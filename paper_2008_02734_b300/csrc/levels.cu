@@ -71,6 +71,10 @@ __device__ long long block_excl_scan(long long v, long long* total) {
 
 // ---------------------------------------------------------------- plan
 
+// Largest band-group count per sweep the ticket map handles (one bucket per
+// plan thread); longer sweeps use the plain ticket order.
+constexpr int kTmapBuckets = 1024;
+
 // One block of 1024 threads.  Every box owns two sweep slots.  An aligned box
 // gets a forward half sweep (frame rows 0..r+h) and a backward half sweep
 // (rows r-h..P-1 of the reversed box), both ending on the window of split rows
@@ -195,6 +199,55 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
     atomicAdd(&cells_sh[0], my_cells);
     atomicAdd(&cells_sh[1], my_tag);
     __syncthreads();
+    // Ticket map, group-major: ticket t -> (sweep, band group j), every sweep's
+    // first group of G bands first, then every sweep's second group, and so on
+    // (sweeps with more groups first within a round).  A block then takes a
+    // group whose band above started about one round earlier, instead of a
+    // group far down a sweep whose first band has only just started.
+    __shared__ int tm_hist[kTmapBuckets];  // sweeps per group count; later per-bucket fill counters
+    __shared__ int tm_cnt[kTmapBuckets];   // tm_cnt[j]: sweeps with more than j groups
+    __shared__ int tm_off[kTmapBuckets];   // first ticket of round j
+    __shared__ int tm_ok;
+    __shared__ long long tm_total;
+    bool map_on = false;
+    if (a.tmap != nullptr && (long long)nsw <= a.cap_sweeps) {
+        for (int i = threadIdx.x; i < kTmapBuckets; i += blockDim.x) tm_hist[i] = 0;
+        if (threadIdx.x == 0) tm_ok = 1;
+        __syncthreads();
+        for (int s = threadIdx.x; s < nsw; s += blockDim.x) {
+            const int ng = (a.sweeps[s].nbands + a.G - 1) / a.G;
+            if (ng >= kTmapBuckets) tm_ok = 0;
+            else if (ng > 0) atomicAdd(&tm_hist[ng], 1);
+        }
+        __syncthreads();
+        if (tm_ok) {
+            long long tot;
+            // suffix sums of the histogram: a scan of it reversed (one bucket per thread)
+            const int r = threadIdx.x;
+            const long long e = block_excl_scan(tm_hist[kTmapBuckets - 1 - r], &tot);
+            tm_cnt[kTmapBuckets - 1 - r] = (int)e;
+            __syncthreads();
+            const long long o = block_excl_scan(tm_cnt[threadIdx.x], &tot);
+            tm_off[threadIdx.x] = (int)o;
+            tm_hist[threadIdx.x] = 0;
+            if (threadIdx.x == 0) {
+                tm_total = tot;
+                if (tot > a.cap_tickets) tm_ok = 0;
+            }
+            __syncthreads();
+            if (tm_ok) {
+                for (int s = threadIdx.x; s < nsw; s += blockDim.x) {
+                    const int ng = (a.sweeps[s].nbands + a.G - 1) / a.G;
+                    if (ng == 0) continue;
+                    // descending group count: bucket ng starts after every sweep with more groups
+                    const int pos = tm_cnt[ng] + atomicAdd(&tm_hist[ng], 1);
+                    for (int j = 0; j < ng; ++j) a.tmap[tm_off[j] + pos] = make_int2(s, j);
+                }
+            }
+        }
+        __syncthreads();
+        map_on = tm_ok != 0;
+    }
     if (threadIdx.x == 0) {
         const long long total_bands = carry[0];
         const bool fits = (long long)nsw <= a.cap_sweeps && carry[1] <= a.cap_buf && carry[2] <= a.cap_out &&
@@ -210,7 +263,8 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             c->n_sweeps = nsw;
             c->n_items = (int)carry[3];
             c->n_bands = total_bands;
-            c->n_tickets = (total_bands + a.G - 1) / a.G;
+            c->n_tickets = map_on ? tm_total : (total_bands + a.G - 1) / a.G;
+            c->tmap_on = map_on ? 1 : 0;
             c->sweep_cells += cells_sh[0];
             c->tag_cells += cells_sh[1];
         } else {
@@ -218,6 +272,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             c->n_items = 0;
             c->n_bands = 0;
             c->n_tickets = 0;
+            c->tmap_on = 0;
             set_error(c, ERR_CAPACITY, 0);
         }
     }

@@ -358,9 +358,12 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
     if (n_cur > 0) {
         PlanArgs pa{cur, n_cur, pairs(), MODE_ALIGN, kind, halo, U, BR, G, d_sweeps, ctl(),
                     L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
+        pa.tmap = reinterpret_cast<int2*>(ws + L.tmap);
+        pa.cap_tickets = L.cap_tickets;
         e = launch_plan(pa, st);
         SweepArgs sa{d_sweeps, ctl(), reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres,
                      d, spin_limit, -1};
+        sa.tmap = reinterpret_cast<const int2*>(ws + L.tmap);
         if (e == cudaSuccess) e = launch_sweep(kind, d, kind == KIND_ABS, sa, num_sms, 0, st);
         SplitArgs sp{cur, n_cur, pairs(), pres(), kind, d, halo, d_sweeps, d_sres, ws + L.outpool, nxt, d_base,
                      ctl(), base_area, (int)L.cap_box, (int)L.cap_base, d_boxdone, ws + L.partials, -1, num_sms};
@@ -370,6 +373,8 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
     if (e == cudaSuccess) e = launch_base(ba, st);
     PlanArgs pn{nxt, -1, pairs(), MODE_ALIGN, kind, halo, U, BR, G, d_sweeps, ctl(),
                 L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, true, nullptr};
+    pn.tmap = reinterpret_cast<int2*>(ws + L.tmap);
+    pn.cap_tickets = L.cap_tickets;
     if (e == cudaSuccess) e = launch_plan(pn, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_flags, 0, 4 * kSlots, st);
     if (e == cudaSuccess) e = launch_mark_pairs(nxt, ctl(), d_flags, st);

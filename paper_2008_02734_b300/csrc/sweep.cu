@@ -995,6 +995,7 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
     const int n_sweeps = A.ctl->n_sweeps;
     const long long n_tickets = A.ctl->n_tickets;
     const long long n_bands = A.ctl->n_bands;
+    const bool tmap_on = A.ctl->tmap_on != 0 && A.tmap != nullptr;
     // with fewer tickets than blocks only the first n_tickets blocks work: a grid
     // fixed in advance then still puts a level's few strips on separate SMs
     if ((long long)blockIdx.x >= n_tickets) return;
@@ -1013,12 +1014,22 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
         const long long t = sm.ticket;
         if (t >= n_tickets || sm.stop) break;
         if (warp < kG) {
-            // the warp's band and sweep, also published for the loader
-            const long long gb = t * kG + warp;
+            // the warp's band and sweep, also published for the loader: from the
+            // ticket map (group j of one sweep), or consecutive level bands
             int si = -1, band = 0;
-            if (gb < n_bands) {
-                si = find_sweep(A.sweeps, n_sweeps, gb);
-                band = (int)(gb - A.sweeps[si].band_begin);
+            if (tmap_on) {
+                const int2 m = A.tmap[t];
+                const int b = m.y * kG + warp;
+                if (b < A.sweeps[m.x].nbands) {
+                    si = m.x;
+                    band = b;
+                }
+            } else {
+                const long long gb = t * kG + warp;
+                if (gb < n_bands) {
+                    si = find_sweep(A.sweeps, n_sweeps, gb);
+                    band = (int)(gb - A.sweeps[si].band_begin);
+                }
             }
             if ((threadIdx.x & 31) == 0) {
                 sweep_of[warp] = si;
@@ -1046,9 +1057,9 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
         if (warp < kG) {
             const int si = sweep_of[warp];
             if (si >= 0) {
-                const long long gb = t * kG + warp;
                 const Sweep* sp = A.sweeps + si;
                 const int band = band_of[warp];
+                const long long gb = sp->band_begin + band;  // level band number
                 const int nbands = sp->nbands, rows = sp->rows, tag_row = sp->tag_row;
                 const bool below = band + 1 < nbands && gb != A.skip_ticket;
                 const bool to_ring = below && warp + 1 < kG;

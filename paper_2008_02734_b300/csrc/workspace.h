@@ -14,8 +14,8 @@ inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
     size_t feat, pairs, pres, boxA, boxB, base, sweeps, sres, bufpool, outpool, boxdone, partials, minmax, jlo, jhi,
-        off, path, ctl, total;
-    long long cap_box, cap_base, cap_sweeps, cap_buf, cap_out, cap_items;
+        off, path, ctl, tmap, total;
+    long long cap_box, cap_base, cap_sweeps, cap_buf, cap_out, cap_items, cap_tickets;
 };
 
 inline Layout make_layout(int B, long long sumM, long long sumN, long long feat_bytes, long long path_pairs) {
@@ -30,6 +30,9 @@ inline Layout make_layout(int B, long long sumM, long long sumN, long long feat_
     L.cap_out = kSplitRowsMax * (S + 2 * L.cap_box * 8);
     // split work items: column chunks of every box's split rows
     L.cap_items = S / kSplitChunk + L.cap_box + 16;
+    // ticket map: band groups of a level (bands are at least 32 rows); a level
+    // that needs more falls back to the plain ticket order
+    L.cap_tickets = S / 32 + 4096;
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t r = o;
@@ -54,6 +57,7 @@ inline Layout make_layout(int B, long long sumM, long long sumN, long long feat_
     L.off = take(4 * (size_t)sumM);
     L.path = take(8 * (size_t)path_pairs);
     L.ctl = take(sizeof(LevelCtl));
+    L.tmap = take(8 * (size_t)L.cap_tickets);
     L.total = o;
     return L;
 }
