@@ -1116,6 +1116,7 @@ template <int KIND, int R, int U, int DIM, bool TAGS>
 static cudaError_t setup_one(int* nb_out) {
     constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
     constexpr size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>();
+    static_assert(smem <= 227 * 1024, "the block's rings exceed the shared memory of an SM (see yslots)");
     static int nb = 0;
     if (nb == 0) {
         cudaError_t e = cudaFuncSetAttribute(sweep_kernel<KIND, R, U, DIM, TAGS>,
