@@ -165,6 +165,31 @@ def test_batch_matches_single():
         assert np.array_equal(path.cpu().numpy(), p_ref)
 
 
+def test_batch_many_uneven_pairs():
+    """Many pairs of very different shapes in one batch, with a small base-case
+    cutoff: many sweeps per level, most of them a band or two, a few long ones
+    (the group-major ticket map interleaves them)."""
+    dtw.set_option(dtw.OPT_BASE_AREA, 64)
+    rng = np.random.default_rng(123)
+    shapes = [(1, 1), (1, 300), (300, 1), (2, 2), (3, 5000), (5000, 3), (129, 129), (257, 130)]
+    shapes += [(int(rng.integers(1, 2500)), int(rng.integers(1, 2500))) for _ in range(30)]
+    pairs = [synth.int_pair(900 + k, m, n) for k, (m, n) in enumerate(shapes)]
+    res = dtw.align_batch([_cuda(x) for x, _ in pairs], [_cuda(y) for _, y in pairs])
+    for (X, Y), (path, cost) in zip(pairs, res):
+        p_ref, c_ref = oracle.dtw(X, Y)
+        assert cost == c_ref
+        assert np.array_equal(path.cpu().numpy(), p_ref)
+
+
+def test_long_thin_pair_plain_ticket_order():
+    """A 600000 x 40 pair: its top-level sweeps have more than 1024 groups of
+    bands, so those levels use the plain ticket order (the deeper ones the map)."""
+    X, Y = synth.int_pair(77, 600000, 40)
+    c_ref = oracle.dtw(X, Y)[1]
+    assert dtw.cost(_cuda(X), _cuda(Y)) == c_ref
+    check_int(X, Y)
+
+
 def test_batch_float():
     pairs = [synth.chroma_pair(60 + k, m, n) for k, (m, n) in enumerate([(500, 600), (800, 700), (40, 30)])]
     res = dtw.align_batch([_cuda(x) for x, _ in pairs], [_cuda(y) for _, y in pairs])
