@@ -13,9 +13,11 @@
 // memory, Section 3.2).
 //
 // Strips.  A thread block has G compute warps and one loader warp.  It takes
-// tickets of G consecutive bands of the level (band numbering runs through
-// the level's sweeps in order, top band first), so a block usually holds G
-// adjacent bands of one sweep, or several short sweeps side by side.  Warp g
+// tickets, each a group of G consecutive bands of one sweep: group j of a
+// sweep is bands jG .. jG+G-1.  The plan writes the ticket map in group-major
+// order (every sweep's group 0, then every sweep's group 1, ...); without a map
+// (a sweep of 1024 groups or more) tickets are G consecutive bands of the
+// level's band numbering, which may put short sweeps side by side.  Warp g
 // hands its band's last row to warp g+1 through a ring of column blocks in
 // shared memory, published with release/acquire progress counters: the
 // hand-off costs one shared store per step on the producer side and one shared
@@ -28,9 +30,10 @@
 // needed in global memory: stale words from earlier bands, levels or calls
 // carry other epochs and are not accepted.
 //
-// Scheduling.  The kernel is persistent.  Tickets are issued in band order, so
-// the band a warp waits on belongs to the same block or to a block that took an
-// earlier ticket and is already running: no deadlock, whatever the grid.  Every
+// Scheduling.  The kernel is persistent.  In both orders the band a warp waits
+// on (the band above, of the same sweep) belongs to the same block or to an
+// earlier ticket, whose block is already running: no deadlock, whatever the
+// grid.  Every
 // wait is bounded; on expiry the kernel records ERR_TIMEOUT, the waiting warp
 // finishes on garbage, and the host turns it into DTW_ETIMEOUT.
 //
