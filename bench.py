@@ -398,14 +398,15 @@ def run_batch_workload(args):
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
     st = dtw.get_stats()
-    # end to end from host arrays
-    Xh = [x for x, _ in pairs]
-    Yh = [y for _, y in pairs]
+    # end to end from pinned host buffers (paths come back to host buffers too)
+    Xh = [torch.from_numpy(x).pin_memory() for x, _ in pairs]
+    Yh = [torch.from_numpy(y).pin_memory() for _, y in pairs]
+    Ph = [torch.empty((len(x) + len(y) - 1, 2), dtype=torch.int32).pin_memory() for x, y in pairs]
     e2e = []
     for _ in range(max(1, args.steps // 2)):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        dtw.align_batch(Xh, Yh)
+        dtw.align_batch(Xh, Yh, paths_out=Ph)
         e2e.append(1e3 * (time.perf_counter() - t))
     h2d = int(sum(x.nbytes + y.nbytes for x, y in pairs))
     d2h = int(sum(8 * (len(x) + len(y) - 1) for x, y in pairs))

@@ -330,8 +330,9 @@ def edit_align_batch(Xs, Ys, *, sub: int = 1, gap: int = 1):
     return [(paths[b][:K[b]], int(C[b])) for b in range(B)]
 
 
-def align_batch(Xs, Ys, *, dp_f32: bool = False, cost_bf16: bool = False):
-    """Aligns B pairs together; returns a list of (path, D*)."""
+def align_batch(Xs, Ys, *, dp_f32: bool = False, cost_bf16: bool = False, paths_out=None):
+    """Aligns B pairs together; returns a list of (path, D*).  ``paths_out`` may
+    supply the B (M+N-1, 2) int32 output buffers (host or device)."""
     B = len(Xs)
     if B != len(Ys) or B == 0:
         raise ValueError("need equally many, and at least one, X and Y")
@@ -350,7 +351,7 @@ def align_batch(Xs, Ys, *, dp_f32: bool = False, cost_bf16: bool = False):
         yps.append(yp)
         Ms.append(M)
         Ns.append(N)
-        paths.append(_path_buffer(M, N, cu))
+        paths.append(_path_buffer(M, N, cu) if paths_out is None else paths_out[len(paths)])
     if cu0 is not None:
         _sync_stream(cu0)
     VP = ctypes.c_void_p * B
