@@ -654,7 +654,8 @@ __global__ void __launch_bounds__(32 * kBaseWarps) base_kernel(BaseArgs a) {
                     else if (dd == m) pt = 0;
                     else if (vf) pt = (up == m) ? 1 : 2;
                     else pt = (left == m) ? 2 : 1;
-                    cur = m + c;
+                    if constexpr (KIND == KIND_ABS) cur = (Acc)__sad(xr.v, yc.v, (unsigned)m);  // |x - y| + m
+                    else cur = m + c;
                     left = cur;
                     dprev = up;
                     word |= pt << (2 * (q & 15));

@@ -682,7 +682,11 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                     }();
                     const Acc lf = L[k];
                     const Acc m = min3(a_dd, a_up, lf);
-                    Acc nv = m + cc;
+                    // integer kind: |x - y| + m in one sum-of-absolute-difference
+                    // (m and every accumulated cost are nonnegative and below 2^29)
+                    Acc nv;
+                    if constexpr (KIND == KIND_ABS) nv = (Acc)__sad(xr[k].v, yc[u].v, (unsigned)m);
+                    else nv = m + cc;
                     if constexpr (KIND == KIND_LOCAL) {
                         // local floor (end search), then the row's best node: the first
                         // column attaining the lowest value (q < Q: the last block may
