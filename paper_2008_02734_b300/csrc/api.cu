@@ -405,6 +405,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
                     L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
         pa.tmap = d_tmap;
         pa.cap_tickets = L.cap_tickets;
+        pa.map_min = c.num_sms;
         e = launch_plan(pa, st);
         ++launches;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
@@ -426,6 +427,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
                     L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, cur};
         pn.tmap = d_tmap;
         pn.cap_tickets = L.cap_tickets;
+        pn.map_min = c.num_sms;
         const std::vector<long long> key{(long long)(uintptr_t)ws, (long long)L.total, L.cap_box, L.cap_base,
                                          L.cap_sweeps, L.cap_buf, L.cap_out, L.cap_items, kind, d, base_area,
                                          c.spin_limit, c.skip_publish, c.num_sms, max_levels, (long long)L.ctl,
@@ -462,6 +464,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
                         L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
             pa.tmap = d_tmap;
             pa.cap_tickets = L.cap_tickets;
+            pa.map_min = c.num_sms;
             if (e == cudaSuccess) e = launch_plan(pa, st);
             ++launches;
         }
@@ -604,6 +607,7 @@ int run_local(Ctx& c, const int32_t* X, int64_t M, const int32_t* Y, int64_t N, 
         pa.local = local;
         pa.tmap = reinterpret_cast<int2*>(ws + L.tmap);
         pa.cap_tickets = L.cap_tickets;
+        pa.map_min = c.num_sms;
         if (err == cudaSuccess) err = launch_plan(pa, st);
         LevelCtl hc{};
         if (err == cudaSuccess) err = cudaMemcpyAsync(&hc, d_ctl, sizeof(hc), cudaMemcpyDeviceToHost, st);

@@ -57,6 +57,8 @@ struct PlanArgs {
                       // 2 sweep of the reversed box without it; frame rows along X
     int2* tmap = nullptr;      // non-null: write the ticket map (group-major ticket order)
     long long cap_tickets = 0; // its capacity; a level that needs more uses the plain order
+    long long map_min = 0;     // levels with at most this many plain tickets skip the map (all
+                               // their tickets run at once, so their order does not matter)
 };
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st);
 

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
     __shared__ int tm_ok;
     __shared__ long long tm_total;
     bool map_on = false;
-    if (a.tmap != nullptr && (long long)nsw <= a.cap_sweeps) {
+    if (a.tmap != nullptr && (long long)nsw <= a.cap_sweeps && (carry[0] + a.G - 1) / a.G > a.map_min) {
         for (int i = threadIdx.x; i < kTmapBuckets; i += blockDim.x) tm_hist[i] = 0;
         if (threadIdx.x == 0) tm_ok = 1;
         __syncthreads();

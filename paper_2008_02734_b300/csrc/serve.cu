@@ -360,6 +360,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
                     L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
         pa.tmap = reinterpret_cast<int2*>(ws + L.tmap);
         pa.cap_tickets = L.cap_tickets;
+        pa.map_min = num_sms;
         e = launch_plan(pa, st);
         SweepArgs sa{d_sweeps, ctl(), reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres,
                      d, spin_limit, -1};
@@ -375,6 +376,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
                 L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, true, nullptr};
     pn.tmap = reinterpret_cast<int2*>(ws + L.tmap);
     pn.cap_tickets = L.cap_tickets;
+    pn.map_min = num_sms;
     if (e == cudaSuccess) e = launch_plan(pn, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_flags, 0, 4 * kSlots, st);
     if (e == cudaSuccess) e = launch_mark_pairs(nxt, ctl(), d_flags, st);
