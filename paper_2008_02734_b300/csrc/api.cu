@@ -1,7 +1,9 @@
 // C ABI of the library: argument checks, workspace, staging of host buffers,
 // and the host side of the level loop of Algorithm 2 (Section 3.2).  The device
-// does all the arithmetic; per level the host launches plan -> sweep -> split
-// and reads back one small control block to learn whether another level exists.
+// does all the arithmetic.  The level loop (plan -> sweep -> split per level)
+// runs as one CUDA graph whose continuation the device decides, or, with
+// per-level timing or DTW_OPT_GRAPH = 0, from the host, which then reads back one
+// small control block per level to learn whether another level exists.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
