@@ -651,7 +651,14 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                 upt[u] = 0;
             }
         }
-        if (!CHECK || (unsigned)cb < (unsigned)nblk) {
+        // checked steps: a lane without a block (cb outside [0, nblk)) evaluates its
+        // cells on whatever inputs it holds (its rings and frame slots are addressed
+        // modulo their sizes) and then resets what it carries to the next step, its
+        // left column and its last row, to +infinity: the warp runs the step
+        // without a divergent branch.  The tensor-core form indexes its tiles by cb
+        // and branches instead.
+        const bool act = !CHECK || (unsigned)cb < (unsigned)nblk;
+        if (!CHECK || !TC || act) {
             Acc rowv[SPECIAL ? R : 1][U];  // the block's cells, for out rows and the last cell
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -692,7 +699,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                         // column attaining the lowest value (q < Q: the last block may
                         // be partial)
                         if (lfloor) nv = min(nv, 0);
-                        if ((!CHECK || q < Q) && nv < bestv[k]) {
+                        if ((!CHECK || (act && q < Q)) && nv < bestv[k]) {
                             bestv[k] = nv;
                             bestq[k] = q;
                         }
@@ -720,15 +727,19 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                     a_up = nv;
                     L[k] = nv;
                 }
-                bot[u] = a_up;
+                bot[u] = (!CHECK || TC || act) ? a_up : INF;
                 bott[u] = t_up;
+            }
+            if constexpr (CHECK && !TC) {
+#pragma unroll
+                for (int k = 0; k < R; ++k) L[k] = act ? L[k] : INF;
             }
             dprev = upv[U - 1];
             dprevt = upt[U - 1];
             if constexpr (SPECIAL) {
 #pragma unroll
                 for (int k = 0; k < R; ++k)
-                    if (orow_ptr[k]) store_row<Acc, U>(orow_ptr[k] + (size_t)cb * U, rowv[k]);
+                    if (orow_ptr[k] && act) store_row<Acc, U>(orow_ptr[k] + (size_t)cb * U, rowv[k]);
             }
         }
         // lane 31: the band's last row over block s-31, for the band below
@@ -813,9 +824,10 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
 // with room in its ring, cp.async copies of the next CHB column blocks of the
 // sweep's column frames, (b) for warp 0, when its band continues a band of an
 // earlier block, polls the next 32 columns of that band's boundary row in
-// global memory and, once every word bears the expected epoch, copies the
-// payloads into row ring 0, and (c) waits for the previous round's copies and
-// publishes them (copies stay one round in flight).  Nothing blocks on another
+// global memory and copies into row ring 0 the longest run of whole blocks,
+// from the first column, whose words all bear the expected epoch, and (c)
+// waits for the previous round's copies and publishes them (copies stay one
+// round in flight).  Nothing blocks on another
 // warp: a round that can do nothing sleeps briefly, and a bounded number of
 // idle rounds ends in ERR_TIMEOUT.
 template <int KIND, int U, int DIM, int NWMAX, int NW>
@@ -900,16 +912,23 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
 #pragma unroll
                     for (int i = 0; i < NW; ++i) ok = ok && word_epoch(w[i]) == uep;
                 }
-                if (__all_sync(kFull, ok) || gave_up) {
-                    if (col < uend) {
+                // publish the longest run of ready columns from unext, cut to whole
+                // blocks: the band below can go on as soon as its next blocks are
+                // there, not only when all 32 columns of the window are
+                const unsigned bal = __ballot_sync(kFull, ok);
+                const int n = (gave_up || bal == kFull) ? 32 : __ffs(~bal) - 1;
+                const int newb = min((unext + n) / U, nblk);
+                if (newb > unext / U) {
+                    const int lim = newb * U;
+                    if (col < lim) {
                         uint32_t* dst = sm.uring[0] + ((col / U) & (URS - 1)) * SLOT + (col % U) * NW;
 #pragma unroll
                         for (int i = 0; i < NW; ++i) dst[i] = word_payload(w[i]);
                     }
                     __threadfence_block();
                     __syncwarp();
-                    if (lane == 0) st_release_cta(&sm.uprog[0], b1);
-                    unext += 32;
+                    if (lane == 0) st_release_cta(&sm.uprog[0], newb);
+                    unext = lim;
                     progress = true;
                 } else {
                     ++ws.polls;
