@@ -154,6 +154,22 @@ __device__ __forceinline__ void st_shared_words(uint32_t* p, const uint32_t* w) 
         for (int i = 0; i < N; ++i) p[i] = w[i];
     }
 }
+// The same store, executed only where pred holds (predicated instructions for
+// whole 16-byte units).
+template <int N>
+__device__ __forceinline__ void st_shared_words_if(bool pred, uint32_t* p, const uint32_t* w) {
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < N; i += 4)
+            asm volatile(
+                "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t@q st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n\t}" ::"r"(
+                    smem_addr(p + i)),
+                "r"(w[i]), "r"(w[i + 1]), "r"(w[i + 2]), "r"(w[i + 3]), "r"((int)pred)
+                : "memory");
+    } else {
+        if (pred) st_shared_words<N>(p, w);
+    }
+}
 template <int N>
 __device__ __forceinline__ void ld_shared_words(const uint32_t* p, uint32_t* w) {
     if constexpr (N % 4 == 0) {
@@ -196,6 +212,31 @@ __device__ __forceinline__ void store_row(T* p, const T* v) {
     } else {
 #pragma unroll
         for (int i = 0; i < U; ++i) p[i] = v[i];
+    }
+}
+
+// The same store, executed only where pred holds: predicated instructions for
+// the vector forms, so that a step with one out row among its lanes carries no
+// divergent branch.
+template <typename T, int U>
+__device__ __forceinline__ void store_row_if(bool pred, T* p, const T* v) {
+    if constexpr (sizeof(T) == 4 && U % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < U; i += 4)
+            asm volatile(
+                "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t@q st.global.v4.b32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(
+                    p + i),
+                "r"((int)v[i]), "r"((int)v[i + 1]), "r"((int)v[i + 2]), "r"((int)v[i + 3]), "r"((int)pred)
+                : "memory");
+    } else if constexpr (std::is_same<T, double>::value && U % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < U; i += 2)
+            asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q st.global.v2.f64 [%0], {%1, %2};\n\t}" ::"l"(
+                             p + i),
+                         "d"(v[i]), "d"(v[i + 1]), "r"((int)pred)
+                         : "memory");
+    } else {
+        if (pred) store_row<T, U>(p, v);
     }
 }
 
@@ -619,8 +660,11 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         }
     };
 
-    auto step = [&](int s, auto checked) {
+    // checked: some lane may lie outside [0, nblk); capture: some lane may hold the
+    // sweep's last block (only groups that reach it take its last cell)
+    auto step = [&](int s, auto checked, auto capture) {
         constexpr bool CHECK = decltype(checked)::value;
+        constexpr bool CAP = CHECK && decltype(capture)::value;
         uint32_t cw[BW];
 #pragma unroll
         for (int i = 0; i < BW; ++i) cw[i] = nwd[i];
@@ -717,10 +761,12 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                     }
                     if constexpr (SPECIAL) {
                         rowv[k][u] = nv;
-                        // the sweep's last cell lies in the lane's last block (a checked group)
-                        if (CHECK && k == end_k && u == end_u && cb == nblk - 1) {
-                            end_v = nv;
-                            end_t = t;
+                        // the sweep's last cell lies in the lane's last block (a checked
+                        // group that reaches it); taken with selects, not a branch
+                        if constexpr (CAP) {
+                            const bool hit = k == end_k && u == end_u && cb == nblk - 1;
+                            end_v = hit ? nv : end_v;
+                            end_t = hit ? t : end_t;
                         }
                     }
                     a_dg = lf;
@@ -739,20 +785,22 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
             if constexpr (SPECIAL) {
 #pragma unroll
                 for (int k = 0; k < R; ++k)
-                    if (orow_ptr[k] && act) store_row<Acc, U>(orow_ptr[k] + (size_t)cb * U, rowv[k]);
+                    store_row_if<Acc, U>(orow_ptr[k] != nullptr && act, orow_ptr[k] + (size_t)cb * U, rowv[k]);
             }
         }
         // lane 31: the band's last row over block s-31, for the band below
+        // (predicated stores: a checked step outside [0, nblk) stores nothing)
         const int ob = s - 31;
-        if (!CHECK || ob >= 0) {
+        const bool obok = !CHECK || (ob >= 0 && ob < nblk);
+        {
             uint32_t w[BW];
 #pragma unroll
             for (int u = 0; u < U; ++u) pack<KIND, NW>(bot[u], bott[u], w + u * NW);
-            if (w31_ring) st_shared_words<BW>(rout + (ob & (URS - 1)) * SLOT, w);
-            unsigned long long* dst = buf + (size_t)ob * BW;
+            st_shared_words_if<BW>(w31_ring && obok, rout + (ob & (URS - 1)) * SLOT, w);
+            unsigned long long* dst = buf + (long long)ob * BW;
 #pragma unroll
             for (int i = 0; i < BW / 2; ++i)
-                st_words2_if(w31_global, dst + 2 * i, mkword(w[2 * i], ep_out), mkword(w[2 * i + 1], ep_out));
+                st_words2_if(w31_global && obok, dst + 2 * i, mkword(w[2 * i], ep_out), mkword(w[2 * i + 1], ep_out));
         }
     };
 
@@ -764,15 +812,21 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         if (s0 >= 31 && s0 + KC < nblk) {
             if constexpr (int_kind(KIND)) {
 #pragma unroll kGroupUnroll
-                for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{});
+                for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{}, std::false_type{});
             } else {
 #pragma unroll kGroupUnrollEuc
-                for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{});
+                for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{}, std::false_type{});
             }
         } else {
+            // the group may run past nsteps: those steps have no lane with a block
+            // and store nothing (a per-step test would split the group)
+            if (SPECIAL && s0 + KC < nblk) {
 #pragma unroll
-            for (int i = 0; i < KC; ++i)
-                if (s0 + i < nsteps) step(s0 + i, std::true_type{});
+                for (int i = 0; i < KC; ++i) step(s0 + i, std::true_type{}, std::false_type{});
+            } else {
+#pragma unroll
+                for (int i = 0; i < KC; ++i) step(s0 + i, std::true_type{}, std::true_type{});
+            }
         }
     }
     if (to_ring && lane == 31) st_release_cta(&sm.uprog[g + 1], nblk);
