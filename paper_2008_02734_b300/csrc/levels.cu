@@ -322,7 +322,9 @@ __device__ __forceinline__ V as_v(A x) {
 // Partial minima of the window of split rows over one chunk of columns: for
 // every row m, S = F + B - C (Lemma 2) minimised over the chunk, with the number
 // of columns attaining the minimum and the lowest of them.  Block of 256 threads;
-// thread 0 ends up with the merged values in rm[].
+// rm[m] ends up with row m's merged values (rows m < nout).  A thread issues all
+// loads of its column before it combines them (rows past the window repeat its
+// last row and are dropped), so that one memory latency covers the column.
 template <int KIND, int DIM, typename V>
 __device__ void chunk_minima(const SplitArgs& a, const Box& b, const PairDesc& pd, const Geom& g, const Sweep& fw,
                              const Sweep& bw, int q0, int q1, RowMin<V>* rm) {
@@ -337,15 +339,33 @@ __device__ void chunk_minima(const SplitArgs& a, const Box& b, const PairDesc& p
     RowMin<V> part[kSplitRowsMax];
 #pragma unroll
     for (int m = 0; m < kSplitRowsMax; ++m) part[m] = RowMin<V>{(V)0, 0, INT_MAX};
+    // integer symbols are loaded with the rows; float frames row by row (their
+    // registers)
+    constexpr bool kHoist = int_kind(KIND);
     for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        V fb[kSplitRowsMax], cc[kSplitRowsMax];
+#pragma unroll
+        for (int m = 0; m < kSplitRowsMax; ++m) {
+            const int mm = min(m, nr - 1);
+            fb[m] = as_v<V>(F[(size_t)mm * fs + q]) + as_v<V>(B[-(long long)mm * bs - q]);
+            if constexpr (kHoist) {
+                int i, j;
+                frame_to_global(b, g.axis, g.r - h + mm, q, i, j);
+                cc[m] = (V)cell_cost<KIND, DIM>(pd, i, j, a.d);
+            }
+        }
 #pragma unroll
         for (int m = 0; m < kSplitRowsMax; ++m) {
             if (m < nr) {
-                int i, j;
-                frame_to_global(b, g.axis, g.r - h + m, q, i, j);
-                const V c = (V)cell_cost<KIND, DIM>(pd, i, j, a.d);
-                const V S = as_v<V>(F[(size_t)m * fs + q]) + as_v<V>(B[-(long long)m * bs - q]) - c;
-                const RowMin<V> x{S, 1, q};
+                V c;
+                if constexpr (kHoist) {
+                    c = cc[m];
+                } else {
+                    int i, j;
+                    frame_to_global(b, g.axis, g.r - h + m, q, i, j);
+                    c = (V)cell_cost<KIND, DIM>(pd, i, j, a.d);
+                }
+                const RowMin<V> x{fb[m] - c, 1, q};
                 part[m] = part[m].n == 0 ? x : merge(part[m], x);
             }
         }
@@ -363,15 +383,14 @@ __device__ void chunk_minima(const SplitArgs& a, const Box& b, const PairDesc& p
         if (lane == 0) s_part[m][wid] = x;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int m = 0; m < nr; ++m) {
-            RowMin<V> x = s_part[m][0];
-            for (int w = 1; w < nw; ++w) {
-                const RowMin<V> y = s_part[m][w];
-                x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
-            }
-            rm[m] = x;
+    if (threadIdx.x < nr) {  // one thread per row
+        const int m = threadIdx.x;
+        RowMin<V> x = s_part[m][0];
+        for (int w = 1; w < nw; ++w) {
+            const RowMin<V> y = s_part[m][w];
+            x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
         }
+        rm[m] = x;
     }
     __syncthreads();
 }
@@ -497,21 +516,42 @@ template <int KIND, int DIM>
 __global__ void __launch_bounds__(256) split_kernel(SplitArgs a) {
     using V = typename std::conditional<int_kind(KIND), long long, double>::type;
     __shared__ RowMin<V> rm[kSplitRowsMax];
-    __shared__ int s_last;
+    __shared__ int s_last, s_box;
     // after a planning or sweep error the sweep outputs are not valid
     if (ld_relaxed(&a.ctl->err) != ERR_NONE) return;
     RowMin<V>* partials = static_cast<RowMin<V>*>(a.partials);
     const int n_items = a.n_items >= 0 ? a.n_items : a.ctl->n_items;
     const int n_boxes = a.n_boxes >= 0 ? a.n_boxes : a.ctl->n_cur;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        // the box of item it: the last box whose first item is <= it
-        int lo = 0, hi = n_boxes - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.sweeps[2 * mid].item0 <= it) lo = mid;
-            else hi = mid - 1;
+        // the box of item it: the last box whose first item is <= it (item0
+        // rises with the box index).  Up to 8 boxes a thread, the block tests
+        // every box at once; beyond that, a binary search.
+        int bi;
+        if (n_boxes <= 8 * (int)blockDim.x) {
+            if (threadIdx.x == 0) s_box = 0;
+            __syncthreads();
+            int first[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int x = threadIdx.x + k * blockDim.x;
+                first[k] = x < n_boxes ? a.sweeps[2 * x].item0 : INT_MAX;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int x = threadIdx.x + k * blockDim.x;
+                if (first[k] <= it) atomicMax(&s_box, x);
+            }
+            __syncthreads();
+            bi = s_box;
+        } else {
+            int lo = 0, hi = n_boxes - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.sweeps[2 * mid].item0 <= it) lo = mid;
+                else hi = mid - 1;
+            }
+            bi = lo;
         }
-        const int bi = lo;
         const Box b = a.boxes[bi];
         const PairDesc pd = a.pairs[b.pair];
         const Geom g = geom_of(b);
@@ -526,15 +566,12 @@ __global__ void __launch_bounds__(256) split_kernel(SplitArgs a) {
         const int q0 = chunk * kSplitChunk, q1 = min(q0 + kSplitChunk, g.Q);
         chunk_minima<KIND, DIM, V>(a, b, pd, g, fw, bw, q0, q1, rm);
         const int nr = fw.nout;
-        if (threadIdx.x == 0) {
-            if (nitems == 1) {
-                s_last = 1;
-            } else {
-                for (int m = 0; m < nr; ++m) partials[(size_t)it * kSplitRowsMax + m] = rm[m];
-                __threadfence();
-                s_last = atomicAdd(&a.box_done[bi], 1) == nitems - 1;
-            }
+        if (nitems > 1 && threadIdx.x < nr) {  // each writer fences its own row
+            partials[(size_t)it * kSplitRowsMax + threadIdx.x] = rm[threadIdx.x];
+            __threadfence();
         }
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = nitems == 1 || atomicAdd(&a.box_done[bi], 1) == nitems - 1;
         __syncthreads();
         if (s_last && nitems > 1) {
             // merge the box's partial minima: one warp per split row, lanes over items
