@@ -119,8 +119,10 @@ __device__ __forceinline__ void st_words2_if(bool pred, unsigned long long* p, u
         "l"(a), "l"(b), "r"((int)pred)
         : "memory");
 }
-__device__ __forceinline__ void st_release_cta_if(bool pred, int* p, int v) {
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.release.cta.shared.b32 [%0], %1;\n\t}" ::"r"(
+// A relaxed store of a progress counter, executed only where pred holds; after a
+// fence.acq_rel.cta of the storing thread it publishes like a release.
+__device__ __forceinline__ void st_relaxed_cta_if(bool pred, int* p, int v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.relaxed.cta.shared.b32 [%0], %1;\n\t}" ::"r"(
                      smem_addr(p)),
                  "r"(v), "r"((int)pred)
                  : "memory");
@@ -631,19 +633,18 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     int uavail = 0, yavail = 0;  // blocks known to be in the row ring / the frame ring
     auto sync_group = [&](int s0) {
         if (s0 > 0) {
-            // row ring: only lane 0's part of each (warp-wide) slot load is used, and
-            // its own release orders it
-            st_release_cta_if(lane == 0 && has_above, &sm.ucons[g], min(s0 + 1, nblk));
-            // frame ring: every lane reads slots, so the warp synchronises first;
-            // every 16 steps (the rings leave room for that staleness)
-            if constexpr (YW > 0) {
-                if ((s0 & 15) == 0 && s0 > 31) {
-                    __syncwarp();
-                    st_release_cta_if(lane == 0, &sm.ycons[g], min(s0 - 30, nblk));
-                }
-            }
-            st_release_cta_if(w31_ring && s0 > 31, &sm.uprog[g + 1 < kG ? g + 1 : g],
-                              min(s0 - 31, nblk));
+            // One fence of the whole warp, then relaxed counter stores: each is a
+            // release of its lane (one fence instead of one per counter).  Row
+            // ring: only lane 0's part of each (warp-wide) slot load is used.  Frame
+            // ring: every lane reads slots, so the warp synchronises before the
+            // fence; every 16 steps (the rings leave room for that staleness).
+            // Lane 31 publishes the blocks it wrote.
+            const bool yrel = YW > 0 && (s0 & 15) == 0 && s0 > 31;
+            if (yrel) __syncwarp();
+            asm volatile("fence.acq_rel.cta;" ::: "memory");
+            st_relaxed_cta_if(lane == 0 && has_above, &sm.ucons[g], min(s0 + 1, nblk));
+            if constexpr (YW > 0) st_relaxed_cta_if(lane == 0 && yrel, &sm.ycons[g], min(s0 - 30, nblk));
+            st_relaxed_cta_if(w31_ring && s0 > 31, &sm.uprog[g + 1 < kG ? g + 1 : g], min(s0 - 31, nblk));
         }
         if (s0 < nblk) {  // lane 0 reads blocks up to s0 + KC (the last one ahead of time)
             const int need = min(s0 + KC + 1, nblk);
@@ -979,7 +980,7 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
 #pragma unroll
                         for (int i = 0; i < NW; ++i) dst[i] = word_payload(w[i]);
                     }
-                    __threadfence_block();
+                    // the warp barrier orders every lane's copy before lane 0's release
                     __syncwarp();
                     if (lane == 0) st_release_cta(&sm.uprog[0], newb);
                     unext = lim;
@@ -992,8 +993,7 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
         if constexpr (YW > 0) {
             // the previous round's copies are complete: publish them
             asm volatile("cp.async.wait_group 1;" ::: "memory");
-            __threadfence_block();
-            __syncwarp();
+            __syncwarp();  // orders every lane's completed copies before lane 0's releases
             inflight = false;
 #pragma unroll
             for (int j = 0; j < kG; ++j) {
