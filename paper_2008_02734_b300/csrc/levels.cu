@@ -69,6 +69,51 @@ __device__ long long block_excl_scan(long long v, long long* total) {
     return base + x - v;
 }
 
+// Four exclusive scans at once (one long long of each per thread), with the
+// barriers of one.
+__device__ void block_excl_scan4(const long long (&v)[4], long long (&e)[4], long long (&total)[4]) {
+    __shared__ long long warp_sums4[32][4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = v[k];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long y = __shfl_up_sync(kFull, x[k], o);
+            if (lane >= o) x[k] += y;
+        }
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) warp_sums4[wid][k] = x[k];
+    }
+    __syncthreads();
+    if (wid == 0) {
+        long long w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = lane < nw ? warp_sums4[lane][k] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const long long y = __shfl_up_sync(kFull, w[k], o);
+                if (lane >= o) w[k] += y;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) warp_sums4[lane][k] = w[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        e[k] = (wid ? warp_sums4[wid - 1][k] : 0) + x[k] - v[k];
+        total[k] = warp_sums4[nw - 1][k];
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- plan
 
 // Largest band-group count per sweep the ticket map handles (one bucket per
@@ -174,26 +219,19 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             my_cells += (unsigned long long)sw.rows * (unsigned long long)g.Q;
             if (sw.tag_row >= 0) my_tag += (unsigned long long)(sw.rows - sw.tag_row) * g.Q;
         }
-        long long t0, t1, t2, t3;
-        const long long e0 = block_excl_scan(nb, &t0);
-        const long long e1 = block_excl_scan(nbuf, &t1);
-        const long long e2 = block_excl_scan(nout, &t2);
-        const long long e3 = block_excl_scan(nit, &t3);
+        const long long v4[4] = {nb, nbuf, nout, nit};
+        long long e4[4], t4[4];
+        block_excl_scan4(v4, e4, t4);  // ends with a barrier: carry[] is read by all
         if (valid) {
-            sw.band_begin = carry[0] + e0;
-            sw.epoch0 = ep_base + (uint32_t)(carry[0] + e0);
-            sw.buf_off = carry[1] + e1;
-            sw.out_off = carry[2] + e2;
-            sw.item0 = (int)(carry[3] + e3);
+            sw.band_begin = carry[0] + e4[0];
+            sw.epoch0 = ep_base + (uint32_t)(carry[0] + e4[0]);
+            sw.buf_off = carry[1] + e4[1];
+            sw.out_off = carry[2] + e4[2];
+            sw.item0 = (int)(carry[3] + e4[3]);
             if (s < a.cap_sweeps) a.sweeps[s] = sw;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            carry[0] += t0;
-            carry[1] += t1;
-            carry[2] += t2;
-            carry[3] += t3;
-        }
+        if (threadIdx.x < 4) carry[threadIdx.x] += t4[threadIdx.x];
         __syncthreads();
     }
     atomicAdd(&cells_sh[0], my_cells);
@@ -780,34 +818,47 @@ cudaError_t launch_base(const BaseArgs& a, cudaStream_t st) {
 // One block per pair: lengths of the per-row column runs, their exclusive scan
 // (the row offsets in the path) and the structural checks of a warping path.
 __global__ void __launch_bounds__(1024) assemble_scan_kernel(AssembleArgs a) {
-    __shared__ long long carry;
     const int pb = a.idx ? a.idx[blockIdx.x] : blockIdx.x;
     const PairDesc pd = a.pairs[pb];
     const int32_t* jlo = a.jlo + pd.row_off;
     const int32_t* jhi = a.jhi + pd.row_off;
     int32_t* off = a.off + pd.row_off;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < pd.M; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        long long len = 0;
-        if (i < pd.M) {
-            const int lo = jlo[i], hi = jhi[i];
-            bool ok = lo <= hi && lo >= 0 && hi < pd.N;
-            if (i == 0) ok = ok && lo == 0;
-            else ok = ok && (lo == jhi[i - 1] || lo == jhi[i - 1] + 1);
-            if (i == pd.M - 1) ok = ok && hi == pd.N - 1;
-            if (!ok) set_error(a.ctl, ERR_PATH, i);
-            len = ok ? hi - lo + 1 : 0;
-        }
-        long long tot;
-        const long long e = block_excl_scan(len, &tot);
-        if (i < pd.M) off[i] = (int32_t)(carry + e);
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
+    // each thread a run of consecutive rows: their checks and lengths, one scan
+    // of the run totals, then the rows' offsets (the loads of a run are
+    // independent, so they overlap instead of one block-wide round per 1024 rows)
+    const int M = pd.M;
+    const int per = (M + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int i0 = min(M, (int)threadIdx.x * per), i1 = min(M, i0 + per);
+    // row i's cells on the path (0 for a row that breaks the staircase)
+    auto row_len = [&](int i, int lo, int hi, int prev_hi) -> long long {
+        bool ok = lo <= hi && lo >= 0 && hi < pd.N;
+        if (i == 0) ok = ok && lo == 0;
+        else ok = ok && (lo == prev_hi || lo == prev_hi + 1);
+        if (i == M - 1) ok = ok && hi == pd.N - 1;
+        return ok ? hi - lo + 1 : 0;
+    };
+    long long run = 0;
+    const int hi0 = i0 > 0 && i0 < M ? jhi[i0 - 1] : 0;
+    int prev_hi = hi0;
+#pragma unroll 4
+    for (int i = i0; i < i1; ++i) {
+        const int lo = jlo[i], hi = jhi[i];
+        const long long len = row_len(i, lo, hi, prev_hi);
+        if (len == 0) set_error(a.ctl, ERR_PATH, i);
+        run += len;
+        prev_hi = hi;
     }
-    if (threadIdx.x == 0) a.pres[pb].K = (int32_t)carry;
+    long long tot;
+    long long o = block_excl_scan(run, &tot);
+    prev_hi = hi0;
+#pragma unroll 4
+    for (int i = i0; i < i1; ++i) {
+        off[i] = (int32_t)o;
+        const int lo = jlo[i], hi = jhi[i];
+        o += row_len(i, lo, hi, prev_hi);
+        prev_hi = hi;
+    }
+    if (threadIdx.x == 0) a.pres[pb].K = (int32_t)tot;
 }
 
 __global__ void assemble_scatter_kernel(AssembleArgs a) {
