@@ -455,6 +455,21 @@ __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, DIM>& a, cons
     return widen_cost(__fsqrt_rn(sumsq8<DIM>(a.v, y)));
 }
 
+// Out rows of a sweep (its window of split rows), nout rows of Q columns:
+// element (m, q) lives at ((q / C) * nout + m) * C + q % C, C the accumulators in
+// 16 bytes.  The rows of one column chunk are consecutive, so a lane of the sweep
+// stores its rows of a column block from one address with constant offsets; with
+// nout = 1 this is the plain row.
+template <typename Acc>
+__host__ __device__ constexpr int out_chunk() {
+    return 16 / (int)sizeof(Acc);
+}
+template <typename Acc>
+__host__ __device__ __forceinline__ long long out_index(int m, int q, int nout) {
+    constexpr int C = out_chunk<Acc>();
+    return ((long long)(q / C) * nout + m) * C + q % C;
+}
+
 // Cost of global cell (i, j) of a pair, for the split and checks.
 template <int KIND, int DIM>
 __device__ __forceinline__ auto cell_cost(const PairDesc& pd, int i, int j, int d) {

@@ -13,7 +13,7 @@ struct SweepArgs {
     const Sweep* sweeps;
     LevelCtl* ctl;
     unsigned long long* bufpool;  // boundary rows: 1 or 2 epoch-stamped words per column
-    void* outpool;                // split rows (Acc), forward row and column order
+    void* outpool;                // split rows (Acc), each sweep's frame order, laid out by out_index
     SweepRes* res;                // per-sweep last-cell results
     int d;
     int spin_limit;

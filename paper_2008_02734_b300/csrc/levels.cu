@@ -368,12 +368,11 @@ __device__ void chunk_minima(const SplitArgs& a, const Box& b, const PairDesc& p
                              const Sweep& bw, int q0, int q1, RowMin<V>* rm) {
     using Acc = typename AccOf<KIND>::T;
     __shared__ RowMin<V> s_part[kSplitRowsMax][8];
-    // out rows are stored in each sweep's frame order: the backward sweep's
-    // rows and columns run the other way
+    // out rows are stored in each sweep's frame order (out_index): the backward
+    // sweep's rows and columns run the other way
     const int nr = fw.nout, h = nr / 2;
-    const int fs = fw.ostride, bs = bw.ostride;
     const Acc* F = static_cast<const Acc*>(a.outpool) + fw.out_off;
-    const Acc* B = static_cast<const Acc*>(a.outpool) + bw.out_off + (size_t)(nr - 1) * bs + (g.Q - 1);
+    const Acc* B = static_cast<const Acc*>(a.outpool) + bw.out_off;
     RowMin<V> part[kSplitRowsMax];
 #pragma unroll
     for (int m = 0; m < kSplitRowsMax; ++m) part[m] = RowMin<V>{(V)0, 0, INT_MAX};
@@ -385,7 +384,7 @@ __device__ void chunk_minima(const SplitArgs& a, const Box& b, const PairDesc& p
 #pragma unroll
         for (int m = 0; m < kSplitRowsMax; ++m) {
             const int mm = min(m, nr - 1);
-            fb[m] = as_v<V>(F[(size_t)mm * fs + q]) + as_v<V>(B[-(long long)mm * bs - q]);
+            fb[m] = as_v<V>(F[out_index<Acc>(mm, q, nr)]) + as_v<V>(B[out_index<Acc>(nr - 1 - mm, g.Q - 1 - q, nr)]);
             if constexpr (kHoist) {
                 int i, j;
                 frame_to_global(b, g.axis, g.r - h + mm, q, i, j);
@@ -448,7 +447,7 @@ __device__ void finish_box(const SplitArgs& a, const Box& b, const PairDesc& pd,
         // canonical pivot: the tag that reached the box's last cell
         const SweepRes rr = a.res[2 * bi];
         qs = rr.end_tag;
-        const Acc* out = static_cast<const Acc*>(a.outpool) + fw.out_off;
+        const Acc* out = static_cast<const Acc*>(a.outpool) + fw.out_off;  // one out row
         if (qs < 0 || qs >= g.Q) {
             set_error(a.ctl, ERR_CONSIST, 10);
             qs = 0;
@@ -459,18 +458,17 @@ __device__ void finish_box(const SplitArgs& a, const Box& b, const PairDesc& pd,
         if constexpr (int_kind(KIND)) {
             total_i = rr.end_i;
             if (b.known_i >= 0 && b.known_i != total_i) set_error(a.ctl, ERR_CONSIST, 11);
-            known_l = out[qs];
+            known_l = out[out_index<Acc>(0, qs, 1)];
             known_r = total_i - known_l + c;
         } else {
             total_f = rr.end_f;
-            kl_f = as_v<double>(out[qs]);
+            kl_f = as_v<double>(out[out_index<Acc>(0, qs, 1)]);
             kr_f = total_f - kl_f + (double)c;
         }
     } else {
         const int nr = fw.nout, h = nr / 2;
-        const int fs = fw.ostride, bs = bw.ostride;
         const Acc* F = static_cast<const Acc*>(a.outpool) + fw.out_off;
-        const Acc* B = static_cast<const Acc*>(a.outpool) + bw.out_off + (size_t)(nr - 1) * bs + (g.Q - 1);
+        const Acc* B = static_cast<const Acc*>(a.outpool) + bw.out_off;
         // every split row's minimum is the box's optimal cost (Lemma 2)
         int pick = -1;
         if constexpr (int_kind(KIND)) {
@@ -495,11 +493,11 @@ __device__ void finish_box(const SplitArgs& a, const Box& b, const PairDesc& pd,
             row = g.r - h + pick;
             qs = rm[pick].q;
             if constexpr (int_kind(KIND)) {
-                known_l = F[(size_t)pick * fs + qs];
-                known_r = B[-(long long)pick * bs - qs];
+                known_l = F[out_index<Acc>(pick, qs, nr)];
+                known_r = B[out_index<Acc>(nr - 1 - pick, g.Q - 1 - qs, nr)];
             } else {
-                kl_f = as_v<double>(F[(size_t)pick * fs + qs]);
-                kr_f = as_v<double>(B[-(long long)pick * bs - qs]);
+                kl_f = as_v<double>(F[out_index<Acc>(pick, qs, nr)]);
+                kr_f = as_v<double>(B[out_index<Acc>(nr - 1 - pick, g.Q - 1 - qs, nr)]);
             }
         }
     }

@@ -196,50 +196,32 @@ __device__ __forceinline__ void ld_shared_words(const uint32_t* p, uint32_t* w) 
     }
 }
 
-// Stores U consecutive accumulators (an out row's cells of one column block).
-template <typename T, int U>
-__device__ __forceinline__ void store_row(T* p, const T* v) {
-    if constexpr (sizeof(T) == 4 && U % 4 == 0) {
+// Stores one 16-byte chunk of out-row accumulators (out_chunk of them), only
+// where pred holds: a predicated instruction, so that a step with out rows in
+// some of its lanes carries no divergent branch.
+template <typename T>
+__device__ __forceinline__ void store_chunk_if(bool pred, T* p, const T* v) {
+    static_assert(sizeof(T) * out_chunk<T>() == 16, "16-byte chunks");
+    uint32_t w[4];
+    if constexpr (sizeof(T) == 4) {
 #pragma unroll
-        for (int i = 0; i < U; i += 4)
-            *reinterpret_cast<int4*>(p + i) = make_int4((int)v[i], (int)v[i + 1], (int)v[i + 2], (int)v[i + 3]);
-    } else if constexpr (std::is_same<T, double>::value && U % 2 == 0) {
+        for (int i = 0; i < 4; ++i) w[i] = (uint32_t)v[i];
+    } else if constexpr (std::is_same<T, double>::value) {
 #pragma unroll
-        for (int i = 0; i < U; i += 2) {
-            double2 t;
-            t.x = (double)v[i];
-            t.y = (double)v[i + 1];
-            *reinterpret_cast<double2*>(p + i) = t;
+        for (int i = 0; i < 2; ++i) {
+            w[2 * i] = (uint32_t)__double2loint(v[i]);
+            w[2 * i + 1] = (uint32_t)__double2hiint(v[i]);
         }
-    } else {
+    } else {  // DF: hi, lo
 #pragma unroll
-        for (int i = 0; i < U; ++i) p[i] = v[i];
+        for (int i = 0; i < 2; ++i) {
+            w[2 * i] = __float_as_uint(v[i].hi);
+            w[2 * i + 1] = __float_as_uint(v[i].lo);
+        }
     }
-}
-
-// The same store, executed only where pred holds: predicated instructions for
-// the vector forms, so that a step with one out row among its lanes carries no
-// divergent branch.
-template <typename T, int U>
-__device__ __forceinline__ void store_row_if(bool pred, T* p, const T* v) {
-    if constexpr (sizeof(T) == 4 && U % 4 == 0) {
-#pragma unroll
-        for (int i = 0; i < U; i += 4)
-            asm volatile(
-                "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t@q st.global.v4.b32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(
-                    p + i),
-                "r"((int)v[i]), "r"((int)v[i + 1]), "r"((int)v[i + 2]), "r"((int)v[i + 3]), "r"((int)pred)
-                : "memory");
-    } else if constexpr (std::is_same<T, double>::value && U % 2 == 0) {
-#pragma unroll
-        for (int i = 0; i < U; i += 2)
-            asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q st.global.v2.f64 [%0], {%1, %2};\n\t}" ::"l"(
-                             p + i),
-                         "d"(v[i]), "d"(v[i + 1]), "r"((int)pred)
-                         : "memory");
-    } else {
-        if (pred) store_row<T, U>(p, v);
-    }
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t@q st.global.v4.b32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(p),
+                 "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"((int)pred)
+                 : "memory");
 }
 
 // Per-warp wait statistics, flushed once per band.
@@ -429,7 +411,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     const int rows = sp->rows, Q = sp->Q, nblk = sp->nblk;
     const int rbase = sp->rbase, rstep = sp->rstep;
     const void* rowseq = sp->rowseq;
-    const int out_row0 = sp->out_row0, nout = sp->nout, tag_row = sp->tag_row, ostride = sp->ostride;
+    const int out_row0 = sp->out_row0, nout = sp->nout, tag_row = sp->tag_row;
     const int32_t esub = sp->esub, egap = sp->egap, ematch = sp->ematch;  // edit kinds
     const bool lfloor = sp->floor != 0;                                      // KIND_LOCAL
     const uint32_t ep_out = sp->epoch0 + (uint32_t)band + 1u;
@@ -439,14 +421,15 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     const int end_k = rows - 1 - p0;
     const int end_u = (Q - 1) % U;  // the last cell's column within the last block
     const bool has_above = band > 0;
-    // out rows of this lane: row k goes to orow_ptr[k] (null: not an out row),
-    // U columns per step with one vector store
-    Acc* orow_ptr[R];
+    // out rows of this lane: row k is out row mo0 + k where that lies in
+    // [0, nout); in the out-row layout (out_index) the lane's rows of column
+    // block cb start at element mo0 * OC + cb * U * nout, row k OC further each
+    constexpr int OC = out_chunk<Acc>();
+    static_assert(U % OC == 0, "a lane's column block covers whole out-row chunks");
+    const int mo0 = p0 - out_row0;
+    bool ovalid[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const int orow = p0 + k - out_row0;
-        orow_ptr[k] = (SPECIAL && (unsigned)orow < (unsigned)nout) ? outp + (size_t)orow * ostride : nullptr;
-    }
+    for (int k = 0; k < R; ++k) ovalid[k] = SPECIAL && (unsigned)(mo0 + k) < (unsigned)nout;
 
     uint32_t* rin = sm.uring[g];
     constexpr int kG = group_of<KIND>();
@@ -784,9 +767,14 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
             dprev = upv[U - 1];
             dprevt = upt[U - 1];
             if constexpr (SPECIAL) {
+                // element offsets stay in 64 bits; only valid rows are stored
+                const long long ob = (long long)mo0 * OC + (long long)cb * U * nout;
 #pragma unroll
                 for (int k = 0; k < R; ++k)
-                    store_row_if<Acc, U>(orow_ptr[k] != nullptr && act, orow_ptr[k] + (size_t)cb * U, rowv[k]);
+#pragma unroll
+                    for (int j = 0; j < U / OC; ++j)
+                        store_chunk_if<Acc>(ovalid[k] && act, outp + (ob + (long long)(k + j * nout) * OC),
+                                            rowv[k] + j * OC);
             }
         }
         // lane 31: the band's last row over block s-31, for the band below
