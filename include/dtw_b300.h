@@ -298,7 +298,8 @@ enum dtw_option {
                                  0: a host loop that reads the control block back after every level.
                                  DTW_OPT_TIMING on forces the host loop (it times every level). */
     DTW_OPT_SWEEP_VARIANT = 6, /* integer-kind sweep lane block: 0 (default) 4 rows x 4 columns per lane and
-                                 step, 1: 2 x 4, 2: 8 x 4 (chosen by the autotuner in the Python package) */
+                                 step, 1: 2 x 4, 2: 8 x 4, 3: 4 x 4 with each 8-step group as straight-line
+                                 code (faster on long bands) (chosen by the autotuner in the Python package) */
     DTW_OPT_EDIT_SUB = 7,     /* DTW_EDIT_I32: cost of a substitution, 0 .. 2^20 (default 1) */
     DTW_OPT_EDIT_GAP = 8      /* DTW_EDIT_I32: cost of an insertion or a deletion, 0 .. 2^20 (default 1) */
 };

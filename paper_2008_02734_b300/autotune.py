@@ -17,7 +17,7 @@ import itertools
 from . import OPT_BASE_AREA, OPT_SWEEP_VARIANT, align, set_option
 from . import synth
 
-VARIANTS = (0, 1, 2)
+VARIANTS = (0, 1, 2, 3)
 BASE_AREAS = (4096, 16384, 32768)
 
 

@@ -23,8 +23,10 @@ struct SweepArgs {
 };
 
 // Sweep variants
-// variant (integer kind): 0 R=4 (default), 1 R=2, 2 R=8 rows per lane; U=4 columns.
-constexpr int kSweepVariants = 3;
+// variant (integer kind): 0 R=4 (default), 1 R=2, 2 R=8 rows per lane; U=4 columns;
+// 3 R=4 with fully unrolled steady groups (longer code: faster on long bands, slower
+// where many blocks share an SM's instruction cache).
+constexpr int kSweepVariants = 4;
 int sweep_block_cols(int kind, int d, int variant = 0);  // U
 int sweep_band_rows(int kind, int d, int variant = 0);   // 32*R
 int sweep_group_bands(int kind);  // bands per ticket (compute warps per block)

@@ -391,7 +391,7 @@ struct ColFrame<KIND_EUCF, 64> {
 // shuffles, evaluates its R x U cells and lets lane 31 store its last row.
 // Groups in which every lane has a block (the band's steady state) run without
 // per-lane activity tests.
-template <int KIND, int R, int U, int DIM, int NWMAX, int NW, int TAGM, bool VF, bool SPECIAL>
+template <int KIND, int R, int U, int DIM, int NWMAX, int NW, int TAGM, bool VF, bool SPECIAL, bool FULL>
 __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_idx, int band, bool to_ring,
                                       bool to_global, const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>& sm,
                                       int g, TcWarp* tc) {
@@ -799,7 +799,11 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         if (s0 > 0) sync_group(s0);
         if (TC && (s0 & 15) == 0 && s0 < nblk) build_tile(s0 >> 4);
         if (s0 >= 31 && s0 + KC < nblk) {
-            if constexpr (int_kind(KIND)) {
+            if constexpr (FULL) {
+                // the whole group as straight-line code: steps overlap across it
+#pragma unroll
+                for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{}, std::false_type{});
+            } else if constexpr (int_kind(KIND)) {
 #pragma unroll kGroupUnroll
                 for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{}, std::false_type{});
             } else {
@@ -1016,12 +1020,12 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
     }
 }
 
-template <int KIND, int R, int U, int DIM, int NWMAX, int NW, int TAGM, bool VF>
+template <int KIND, int R, int U, int DIM, int NWMAX, int NW, int TAGM, bool VF, bool FULL>
 __device__ __forceinline__ void run_band_s(bool special, const Sweep* sp, int si, int band, bool to_ring,
                                            bool to_global, const SweepArgs& A,
                                            StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>& sm, int g, TcWarp* tc) {
-    if (special) run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, true>(sp, si, band, to_ring, to_global, A, sm, g, tc);
-    else run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, false>(sp, si, band, to_ring, to_global, A, sm, g, tc);
+    if (special) run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, true, FULL>(sp, si, band, to_ring, to_global, A, sm, g, tc);
+    else run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, false, FULL>(sp, si, band, to_ring, to_global, A, sm, g, tc);
 }
 
 // Dynamic shared memory of a block: the strip state, then (tensor-core form)
@@ -1045,8 +1049,9 @@ __device__ __forceinline__ int find_sweep(const Sweep* sweeps, int n_sweeps, lon
 }
 
 // TAGS: the launch may contain tagged sweeps (integer kind), whose rows carry
-// two payload words per column; untagged integer sweeps use one.
-template <int KIND, int R, int U, int DIM, bool TAGS>
+// two payload words per column; untagged integer sweeps use one.  FULL: steady
+// groups run fully unrolled (integer variant 3).
+template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL>
 __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_constant__ SweepArgs A) {
     constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
     constexpr int kG = group_of<KIND>();
@@ -1137,29 +1142,29 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
                 const bool special =
                     (sp->nout > 0 && sp->out_row0 < b_hi && sp->out_row0 + sp->nout > b_lo) || (rows - 1 < b_hi);
                 if constexpr (!int_kind(KIND)) {
-                    run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true>(special, sp, si, band, to_ring, to_global, A, sm,
+                    run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true, FULL>(special, sp, si, band, to_ring, to_global, A, sm,
                                                                    warp, tcw);
                 } else if (!TAGS || tag_row < 0) {
-                    run_band_s<KIND, R, U, DIM, NWMAX, 1, 0, true>(special, sp, si, band, to_ring, to_global, A, sm,
+                    run_band_s<KIND, R, U, DIM, NWMAX, 1, 0, true, FULL>(special, sp, si, band, to_ring, to_global, A, sm,
                                                                    warp, tcw);
                 } else if constexpr (TAGS) {
                     const bool vf = sp->axis == 0;
                     if (b_hi <= tag_row) {
-                        run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true>(special, sp, si, band, to_ring, to_global, A,
+                        run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true, FULL>(special, sp, si, band, to_ring, to_global, A,
                                                                        sm, warp, tcw);
                     } else if (b_lo > tag_row) {
                         if (vf)
-                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 1, true>(special, sp, si, band, to_ring, to_global,
+                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 1, true, FULL>(special, sp, si, band, to_ring, to_global,
                                                                            A, sm, warp, tcw);
                         else
-                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 1, false>(special, sp, si, band, to_ring, to_global,
+                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 1, false, FULL>(special, sp, si, band, to_ring, to_global,
                                                                             A, sm, warp, tcw);
                     } else {
                         if (vf)
-                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 2, true>(special, sp, si, band, to_ring, to_global,
+                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 2, true, FULL>(special, sp, si, band, to_ring, to_global,
                                                                            A, sm, warp, tcw);
                         else
-                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 2, false>(special, sp, si, band, to_ring, to_global,
+                            run_band_s<KIND, R, U, DIM, NWMAX, 2, 2, false, FULL>(special, sp, si, band, to_ring, to_global,
                                                                             A, sm, warp, tcw);
                     }
                 }
@@ -1180,35 +1185,35 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
 // Grid: one block per ticket up to a full persistent grid.  With fewer tickets
 // than SMs every block gets an SM of its own, so a level with few bands spreads
 // its warps over the schedulers of the whole GPU.
-template <int KIND, int R, int U, int DIM, bool TAGS>
+template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL = false>
 static cudaError_t setup_one(int* nb_out) {
     constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
     constexpr size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>();
     static_assert(smem <= 227 * 1024, "the block's rings exceed the shared memory of an SM (see yslots)");
     static int nb = 0;
     if (nb == 0) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<KIND, R, U, DIM, TAGS>,
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<KIND, R, U, DIM, TAGS, FULL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<KIND, R, U, DIM, TAGS>, threads_of<KIND>(), smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<KIND, R, U, DIM, TAGS, FULL>, threads_of<KIND>(), smem);
         nb = n < 1 ? 1 : n;
     }
     *nb_out = nb;
     return cudaSuccess;
 }
 
-template <int KIND, int R, int U, int DIM, bool TAGS>
+template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL = false>
 static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blocks, cudaStream_t st) {
     constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
     constexpr size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>();
     int nb = 0;
-    cudaError_t e = setup_one<KIND, R, U, DIM, TAGS>(&nb);
+    cudaError_t e = setup_one<KIND, R, U, DIM, TAGS, FULL>(&nb);
     if (e != cudaSuccess) return e;
     long long grid = (long long)num_sms * nb;
     if (max_blocks > 0 && max_blocks < grid) grid = max_blocks;
     if (max_blocks < 0 || grid < 1) grid = 1;
-    sweep_kernel<KIND, R, U, DIM, TAGS><<<(unsigned)grid, threads_of<KIND>(), smem, st>>>(A);
+    sweep_kernel<KIND, R, U, DIM, TAGS, FULL><<<(unsigned)grid, threads_of<KIND>(), smem, st>>>(A);
     return cudaGetLastError();
 }
 
@@ -1219,8 +1224,9 @@ static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blo
 // hand-off work (shuffles, ring, boundary stores) is paid once per block.
 constexpr int kIntR = DTW_INT_R, kIntU = DTW_INT_U;
 constexpr int kEucR = DTW_EUC_R, kEucU = DTW_EUC_U;
-// Integer variants (selected at run time, e.g. by the autotuner): rows per lane.
-constexpr int kIntRVar[kSweepVariants] = {kIntR, 2, 8};
+// Integer variants (selected at run time, e.g. by the autotuner): rows per lane
+// (variant 3: the default lane block with fully unrolled steady groups).
+constexpr int kIntRVar[kSweepVariants] = {kIntR, 2, 8, kIntR};
 int sweep_block_cols(int kind, int d, int variant) { return int_kind(kind) ? kIntU : (d == 12 ? kEucU : 2); }
 int sweep_band_rows(int kind, int d, int variant) {
     if (kind == KIND_ABS) return 32 * kIntRVar[(unsigned)variant < (unsigned)kSweepVariants ? variant : 0];
@@ -1234,6 +1240,9 @@ cudaError_t sweep_prepare(int kind, int d, bool tags, int variant) {
     if (kind == KIND_ABS) {
         if (variant == 1) return tags ? setup_one<KIND_ABS, 2, kIntU, 1, true>(&nb) : setup_one<KIND_ABS, 2, kIntU, 1, false>(&nb);
         if (variant == 2) return tags ? setup_one<KIND_ABS, 8, kIntU, 1, true>(&nb) : setup_one<KIND_ABS, 8, kIntU, 1, false>(&nb);
+        if (variant == 3)
+            return tags ? setup_one<KIND_ABS, kIntR, kIntU, 1, true, true>(&nb)
+                        : setup_one<KIND_ABS, kIntR, kIntU, 1, false, true>(&nb);
         if (tags) return setup_one<KIND_ABS, kIntR, kIntU, 1, true>(&nb);
         return setup_one<KIND_ABS, kIntR, kIntU, 1, false>(&nb);
     }
@@ -1260,6 +1269,9 @@ cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num
         if (variant == 2)
             return tags ? launch_one<KIND_ABS, 8, kIntU, 1, true>(A, num_sms, max_blocks, st)
                         : launch_one<KIND_ABS, 8, kIntU, 1, false>(A, num_sms, max_blocks, st);
+        if (variant == 3)
+            return tags ? launch_one<KIND_ABS, kIntR, kIntU, 1, true, true>(A, num_sms, max_blocks, st)
+                        : launch_one<KIND_ABS, kIntR, kIntU, 1, false, true>(A, num_sms, max_blocks, st);
         if (tags) return launch_one<KIND_ABS, kIntR, kIntU, 1, true>(A, num_sms, max_blocks, st);
         return launch_one<KIND_ABS, kIntR, kIntU, 1, false>(A, num_sms, max_blocks, st);
     }
