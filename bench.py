@@ -223,7 +223,11 @@ def run_ours(args):
     if args.no_graph:
         dtw.set_option(dtw.OPT_GRAPH, 0)
     tuned = None
-    if args.workload == "int_pair" and not args.no_tune:
+    if args.variant is not None:
+        dtw.set_option(dtw.OPT_SWEEP_VARIANT, args.variant)
+    if args.base_area is not None:
+        dtw.set_option(dtw.OPT_BASE_AREA, args.base_area)
+    if args.workload == "int_pair" and not args.no_tune and args.variant is None and args.base_area is None:
         # the library's autotuner picks the lane block and the base-case cutoff for this size
         from paper_2008_02734_b300 import autotune
         tuned = autotune.tune(WORKLOADS["int_pair"][1], WORKLOADS["int_pair"][2], reps=3)
@@ -345,7 +349,9 @@ def run_ours(args):
         "config": {"workload": WORKLOADS[args.workload][0], "M": M, "N": N, "pairs_per_rank": 1,
                    "parallelism": f"replicas{ws}", "l2": "flushed between steps (256 MiB write outside the events)",
                    "autotuned": None if tuned is None else {"sweep_variant": tuned["variant"],
-                                                           "base_area": tuned["base_area"]}},
+                                                           "base_area": tuned["base_area"]},
+                   "fixed": None if args.variant is None and args.base_area is None else
+                   {"sweep_variant": args.variant, "base_area": args.base_area}},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "host_p50": float(np.percentile(host_ms, 50))},
         "e2e": {"value": e2e_value, "unit": "GCUPS", "h2d_bytes_per_step": (M + N) * 4,
@@ -699,6 +705,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default lane block and cutoff)")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="integer sweep variant (lane block) to use instead of the autotuner's choice")
+    ap.add_argument("--base-area", type=int, default=None,
+                    help="base-case cutoff (cells) to use instead of the autotuner's choice")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the level loop from the host (the same kernels; profilers list every launch)")
     args = ap.parse_args()
