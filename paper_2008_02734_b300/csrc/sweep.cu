@@ -420,6 +420,9 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     const int p0 = band * (32 * R) + lane * R;
     const int end_k = rows - 1 - p0;
     const int end_u = (Q - 1) % U;  // the last cell's column within the last block
+    // the last cell is read back only by cost sweeps (no out rows) and tag sweeps;
+    // the half sweeps of an aligned box hand their last row over as out rows
+    const bool need_end = nout == 0 || tag_row >= 0;
     const bool has_above = band > 0;
     // out rows of this lane: row k is out row mo0 + k where that lies in
     // [0, nout); in the out-row layout (out_index) the lane's rows of column
@@ -813,7 +816,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         } else {
             // the group may run past nsteps: those steps have no lane with a block
             // and store nothing (a per-step test would split the group)
-            if (SPECIAL && s0 + KC < nblk) {
+            if (SPECIAL && (s0 + KC < nblk || !need_end)) {
 #pragma unroll
                 for (int i = 0; i < KC; ++i) step(s0 + i, std::true_type{}, std::false_type{});
             } else {
@@ -854,7 +857,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         }
     }
     if constexpr (SPECIAL) {
-        if (end_k >= 0 && end_k < R) {
+        if (need_end && end_k >= 0 && end_k < R) {
             SweepRes* r = A.res + sweep_idx;
             if constexpr (int_kind(KIND)) r->end_i = end_v;
             else r->end_f = to_double(end_v);
