@@ -402,6 +402,11 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     const int max_levels = 2 * (64 - __builtin_clzll((unsigned long long)std::max(maxM, sumN) + 1)) + 8;
     int* d_boxdone = reinterpret_cast<int*>(ws + L.boxdone);
     int2* d_tmap = reinterpret_cast<int2*>(ws + L.tmap);
+    // The graph runs the level loop on the device: it needs no level counters on
+    // the host, so the root plan is not read back (no host round trip before the
+    // first sweep); an error the plan records stops the loop on the device and is
+    // returned from the counters read after the base case.
+    const bool graph = c.use_graph && !c.timing && mode == MODE_ALIGN && !roots.empty();
     if (!roots.empty()) {
         PlanArgs pa{cur, (int)roots.size(), d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
                     L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
@@ -410,14 +415,15 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         pa.map_min = c.num_sms;
         e = launch_plan(pa, st);
         ++launches;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (!graph) {
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, d_ctl, sizeof(LevelCtl), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        }
         if (e != cudaSuccess) return DTW_ECUDA;
-        c.epoch = hc.epoch_base;
+        if (!graph) c.epoch = hc.epoch_base;
     } else {
         hc.n_cur = 0;
     }
-    const bool graph = c.use_graph && !c.timing && mode == MODE_ALIGN && !roots.empty() && hc.err == ERR_NONE;
     if (graph) {
         SweepArgs sa{d_sweeps, d_ctl, reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres, d,
                      c.spin_limit, c.skip_publish};
