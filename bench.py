@@ -687,6 +687,28 @@ def run_serving_workload(args):
     return 0
 
 
+def run_pipes():
+    """Issue rates of the cell update's instructions on this GPU (dtw_pipe_rates),
+    as thread instructions per second and per SM and clock at the measured clock."""
+    import torch
+
+    import paper_2008_02734_b300 as dtw
+
+    torch.cuda.init()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    with ClockSampler(0) as cs:
+        rates = dtw.pipe_rates()
+    clocks = cs.summary()
+    # the measurement lasts a fraction of a second, so the median of the clock
+    # samples mixes in idle readings; the kernels themselves run at the SM clock's
+    # maximum (no throttle reason), which converts the rates
+    mhz = clocks.get("sm_max_mhz") or measured_peaks()[0].get("sm_max_mhz", 2032.0)
+    per = {k: v / (sms * mhz * 1e6) for k, v in rates.items()}
+    print(json.dumps({"pipes_per_s": rates, "pipes_per_sm_clock": per, "sms": sms, "sm_mhz": mhz,
+                      "clocks": clocks}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -711,7 +733,11 @@ def main():
                     help="base-case cutoff (cells) to use instead of the autotuner's choice")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the level loop from the host (the same kernels; profilers list every launch)")
+    ap.add_argument("--pipes", action="store_true",
+                    help="measure the issue rates of the instructions the per-cell roofline counts and exit")
     args = ap.parse_args()
+    if args.pipes:
+        return run_pipes()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":

@@ -287,6 +287,25 @@ typedef struct dtw_stats {
 
 DTW_API int dtw_get_stats(dtw_stats* out);
 
+/*
+ * dtw_pipe_rates -- measured issue rates of the instructions that the per-cell
+ * roofline counts (the cell update of the recurrence, Section 2.1): for each, the
+ * whole device's thread-instruction rate per second, timed alone at full
+ * occupancy with eight independent chains per thread on the current device:
+ *   [0] three-way signed 32-bit minimum (__vimin3_s32; the chains also issue one
+ *       XOR per eight minima, so this is a lower bound)
+ *   [1] 32-bit sum of absolute difference (__sad: |x - y| + z)
+ *   [2] FP32 fused multiply-add
+ *   [3] packed FP32x2 fused multiply-add (one instruction, two lanes of work)
+ *   [4] correctly rounded FP32 square root (__fsqrt_rn; several instructions)
+ *   [5] FP64 add
+ *   rates_out  host, n doubles; entries past the sixth are not written
+ * Returns the number of entries written, DTW_EINVAL (NULL or n < 1), DTW_ENOMEM
+ * or DTW_ECUDA.  Allocates and frees a small device buffer and a stream of its
+ * own; blocks for some tens of milliseconds.
+ */
+DTW_API int dtw_pipe_rates(double* rates_out, int32_t n);
+
 /* Tuning and instrumentation switches (dtw_set_option keys). */
 enum dtw_option {
     DTW_OPT_TIMING = 1,      /* 1: record CUDA events around each launch (default 0) */

@@ -79,6 +79,7 @@ def _load():
         "dtw_footprint": (ctypes.c_size_t, [i64, i64, i32, i32]),
         "dtw_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "dtw_get_stats": (ctypes.c_int, [vp]),
+        "dtw_pipe_rates": (ctypes.c_int, [vp, i32]),
         "dtw_set_option": (ctypes.c_int, [i32, i64]),
         "dtw_cost_noalloc": (ctypes.c_int, [vp, i64, vp, i64, i32, i32, vp, vp]),
         "dtw_path_discrepancy": (ctypes.c_int, [vp, i64, vp, i64, i64, i64, vp, vp]),
@@ -110,7 +111,7 @@ def __getattr__(name):
 
 # exported names of the C ABI, for the symbol check
 ABI_FUNCTIONS = ("dtw_align", "dtw_cost", "dtw_align_batch", "dtw_submit", "dtw_poll", "dtw_set_stream",
-                 "dtw_set_budget", "dtw_set_arena", "dtw_footprint", "dtw_strerror", "dtw_get_stats",
+                 "dtw_set_budget", "dtw_set_arena", "dtw_footprint", "dtw_strerror", "dtw_get_stats", "dtw_pipe_rates",
                  "dtw_set_option", "dtw_cost_noalloc", "dtw_path_discrepancy", "dtw_local_align")
 
 
@@ -419,6 +420,19 @@ def set_option(key: int, value: int) -> None:
 
 def set_stream(stream) -> None:
     _get_lib().dtw_set_stream(ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream))
+
+
+PIPE_OPS = ("min3_s32", "sad_u32", "ffma_f32", "ffma2_f32x2", "sqrt_rn_f32", "dadd_f64")
+
+
+def pipe_rates() -> dict:
+    """Issue rates (thread instructions per second, whole device) of the
+    instructions the per-cell roofline counts, measured on the current device."""
+    out = (ctypes.c_double * len(PIPE_OPS))()
+    n = _get_lib().dtw_pipe_rates(out, len(PIPE_OPS))
+    if n < 0:
+        raise DTWError(n, "dtw_pipe_rates")
+    return {PIPE_OPS[i]: out[i] for i in range(n)}
 
 
 def get_stats() -> dict:

@@ -55,6 +55,12 @@ def test_strerror_and_options(lib):
     assert lib.lib.dtw_set_option(lib.OPT_BASE_AREA, 1 << 20) == lib.EINVAL
 
 
+def test_pipe_rates_checks_arguments_on_host(lib):
+    out = (ctypes.c_double * 6)()
+    assert lib.lib.dtw_pipe_rates(None, 6) == lib.EINVAL
+    assert lib.lib.dtw_pipe_rates(out, 0) == lib.EINVAL
+
+
 def test_invalid_arguments_rejected_on_host(lib):
     X = np.zeros(4, np.int32)
     p = np.zeros(16, np.int32)
