@@ -163,6 +163,32 @@ def cpu_oracle_baseline(name: str, budget_s: float = 20.0):
                       f"backpointers, {'int64' if X.dtype == np.int32 else 'FP64'}), {spent:.1f} s"}
 
 
+def _oracle_pair_timed(name: str):
+    """One whole pair of the workload through oracle 1 in this process: (wall-clock
+    start, end, cells).  Runs in a spawned worker of cpu_oracle_all_cores."""
+    import oracle
+    X, Y = make_inputs(name)
+    t0 = time.time()
+    oracle.dtw(X, Y)
+    return t0, time.time(), len(X) * len(Y)
+
+
+def cpu_oracle_all_cores(name: str, max_workers: int = 64):
+    """Oracle 1 (unchanged, single-threaded) on the host's cores at once: one whole
+    pair of the workload per spawned process; GCUPS = all cells over the span from
+    the first start to the last end (the host's aggregate throughput)."""
+    import multiprocessing as mp
+    n = max(1, min(os.cpu_count() or 1, max_workers))
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_pair_timed, [name] * n)
+    span = max(r[1] for r in res) - min(r[0] for r in res)
+    cells = sum(r[2] for r in res)
+    return {"value": cells / span / 1e9, "unit": "GCUPS", "cores": n, "kind": "oracle",
+            "sample": f"{n} whole pairs of the workload through oracle 1, one per process (spawned), "
+                      f"concurrently; {span:.1f} s from the first start to the last end; host has "
+                      f"{os.cpu_count()} logical CPUs"}
+
+
 def max_over_ranks(x: float, device) -> float:
     """The largest x over all ranks: the whole job's time is its slowest rank's."""
     import torch
@@ -331,6 +357,7 @@ def run_ours(args):
                 "sweep_ms_per_step": sweep_ms / args.steps, "sweep_launches_per_step": sweep_launches / args.steps,
                 "processed_cells_per_step": cells_proc / args.steps}
     cpu = None if args.no_cpu else cpu_oracle_baseline(args.workload, budget_s=args.cpu_budget)
+    cpu_all = None if args.no_cpu else cpu_oracle_all_cores(args.workload)
     disc = None
     if args.workload == "plain_float" and not args.no_cpu:
         # Section 4.3's discrepancy of the GPU path against the oracle's: float
@@ -359,6 +386,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
         "vs_plain_gpu": None if plain is None else {"plain": plain, "speedup": value / ws / plain["gcups"]},
         "path_discrepancy_vs_oracle": disc,
         "clocks": clk.summary(),
