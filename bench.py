@@ -356,8 +356,10 @@ def run_ours(args):
                                "op = one 32-bit lane instruction of the per-cell count (5 per cell, 7 tagged)",
                 "sweep_ms_per_step": sweep_ms / args.steps, "sweep_launches_per_step": sweep_launches / args.steps,
                 "processed_cells_per_step": cells_proc / args.steps}
-    cpu = None if args.no_cpu else cpu_oracle_baseline(args.workload, budget_s=args.cpu_budget)
-    cpu_all = None if args.no_cpu else cpu_oracle_all_cores(args.workload)
+    # the CPU baselines: rank 0 of a single-GPU run only (N > 1 runs report the GPU job)
+    cpu_on = not args.no_cpu and ws == 1
+    cpu = cpu_oracle_baseline(args.workload, budget_s=args.cpu_budget) if cpu_on else None
+    cpu_all = cpu_oracle_all_cores(args.workload) if cpu_on else None
     disc = None
     if args.workload == "plain_float" and not args.no_cpu:
         # Section 4.3's discrepancy of the GPU path against the oracle's: float
