@@ -24,6 +24,13 @@ Wraps ``dtw_oracle.c`` (plain C, FP64 / int64):
 * :func:`local`     -- local alignment (Smith-Waterman, named in Section 5 beside
                        edit distance): score, the canonical end, start and path
                        (``edit_oracle.c`` states the definition).
+* :func:`dtw_given` -- oracle 1 on an explicit FP64 cost matrix (the textbook DP
+                       and backtrace unchanged; only C(i, j) is supplied).
+* :func:`bf16_round` / :func:`bf16_form_costs` -- the cost matrix of the BF16
+                       tensor-core form: the Euclidean cost of Section 4.1 in its
+                       expanded form sqrt(max(0, |x|^2 + |y|^2 - 2 x.y)), with the
+                       dot product taken over the frames rounded to BF16 (round to
+                       nearest, ties to even) and everything else in FP64.
 * :func:`path_discrepancy` -- the alignment discrepancy of two warping paths
                        (Section 4.3, Results): per cell of the first path, its
                        distance along its row and along its column to the
@@ -77,7 +84,8 @@ def _L():
         lib.oracle_edit.argtypes = [p, i64, p, i64, i64, i64, p, p, p]
         lib.oracle_edit_table.argtypes = [p, i64, p, i64, i64, i64, i32, p]
         lib.oracle_local.argtypes = [p, i64, p, i64, i64, i64, i64, p, p, p, p]
-        for f in (lib.oracle_dtw, lib.oracle_linmdtw, lib.oracle_acc_matrix, lib.oracle_path_cost, lib.oracle_edit,
+        lib.oracle_dtw_given.argtypes = [p, i64, i64, p, p, p]
+        for f in (lib.oracle_dtw_given, lib.oracle_dtw, lib.oracle_linmdtw, lib.oracle_acc_matrix, lib.oracle_path_cost, lib.oracle_edit,
                   lib.oracle_edit_table, lib.oracle_local):
             f.restype = ctypes.c_int
         _lib = lib
@@ -132,6 +140,45 @@ def dtw(X, Y):
     if rc != 0:
         raise RuntimeError(f"oracle_dtw failed: {rc}")
     return path[:K.value].copy(), _cost(kind, c, ci)
+
+
+def dtw_given(C):
+    """Oracle 1 on a given cost matrix C (M x N, converted to FP64): returns
+    (path as int32 (K, 2), optimal cost)."""
+    C = np.ascontiguousarray(np.asarray(C, dtype=np.float64))
+    if C.ndim != 2 or C.shape[0] < 1 or C.shape[1] < 1:
+        raise ValueError("C must be a non-empty 2-D matrix")
+    M, N = C.shape
+    path = np.empty((M + N - 1, 2), dtype=np.int32)
+    K, c = ctypes.c_int64(), ctypes.c_double()
+    rc = _L().oracle_dtw_given(_ptr(C), M, N, _ptr(path), ctypes.byref(K), ctypes.byref(c))
+    if rc != 0:
+        raise RuntimeError(f"oracle_dtw_given failed: {rc}")
+    return path[:K.value].copy(), float(c.value)
+
+
+def bf16_round(a):
+    """FP32 values rounded to BF16 (the upper 16 bits of the FP32 encoding: 8
+    significant bits), round to nearest with ties to even, returned as FP32.
+    Finite inputs only."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1  # ties go to the even upper half
+    u = ((u + 0x7FFF + lsb) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32)
+
+
+def bf16_form_costs(X, Y):
+    """The BF16 form's M x N cost matrix in FP64: squared norms of the FP32
+    frames, the dot product of their BF16 roundings, then
+    sqrt(max(0, |x|^2 + |y|^2 - 2 x.y)) (the clamp guards the cancellation of
+    near-identical frames)."""
+    X = np.asarray(X, dtype=np.float32)
+    Y = np.asarray(Y, dtype=np.float32)
+    X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+    xx = (X64 * X64).sum(axis=1)
+    yy = (Y64 * Y64).sum(axis=1)
+    dot = bf16_round(X).astype(np.float64) @ bf16_round(Y).astype(np.float64).T
+    return np.sqrt(np.maximum(0.0, xx[:, None] + yy[None, :] - 2.0 * dot))
 
 
 def linmdtw(X, Y, m: int = 500):

@@ -98,6 +98,27 @@ static int plist_push(plist_t *l, int64_t i, int64_t j) {
 #undef SFX
 #undef COSTFN
 
+/* A frame cost given as an explicit M x N matrix (row-major FP64, held in p->X;
+ * p->Y and p->d unused): for a cost form evaluated outside the oracle, such as
+ * the tensor-core form's expanded Euclidean cost (Section 4.1 with the frames
+ * rounded to BF16).  Only the textbook DP and backtrace are used with it. */
+static double cost_given(const prob_t *p, int64_t i, int64_t j) {
+    return ((const double *)p->X)[i * p->N + j];
+}
+
+#pragma GCC diagnostic push
+#pragma GCC diagnostic ignored "-Wunused-function"
+#define ACC double
+#define ACC_INF (INFINITY)
+#define SFX _given
+#define COSTFN cost_given
+#include "oracle_impl.h"
+#undef ACC
+#undef ACC_INF
+#undef SFX
+#undef COSTFN
+#pragma GCC diagnostic pop
+
 static int check_args(const void *X, int64_t M, const void *Y, int64_t N, int32_t d, int32_t kind) {
     if (!X || !Y || M < 1 || N < 1 || d < 1) return OR_EINVAL;
     if (kind != OR_EUCLID_F32 && kind != OR_ABS_I32) return OR_EINVAL;
@@ -203,4 +224,22 @@ int oracle_path_cost(const void *X, int64_t M, const void *Y, int64_t N, int32_t
     if (cost_out) *cost_out = kind == OR_EUCLID_F32 ? s : (double)si;
     if (icost_out) *icost_out = si;
     return OR_OK;
+}
+
+/* Oracle 1 on a given FP64 cost matrix C (M x N, row-major): the textbook DP,
+ * backpointers (first strict minimum in the order DIAG, UP, LEFT) and backtrace
+ * of Section 2.1, unchanged; only C(i,j) is read from the matrix. */
+int oracle_dtw_given(const double *C, int64_t M, int64_t N, int32_t *path_out, int64_t *K_out, double *cost_out) {
+    if (!C || M < 1 || N < 1 || M > INT32_MAX || N > INT32_MAX) return OR_EINVAL;
+    prob_t p = {C, C, M, N, 1};
+    plist_t l = {0, 0, 0};
+    double c = 0;
+    int rc = textbook_given(&p, 0, 0, M, N, &l, &c);
+    if (rc == OR_OK) {
+        memcpy(path_out, l.v, (size_t)l.n * 2 * sizeof(int32_t));
+        *K_out = l.n;
+        *cost_out = c;
+    }
+    free(l.v);
+    return rc;
 }

@@ -132,10 +132,28 @@ def workload_batch_sizes(seed: int = 3, B: int = 256, lo: int = 1000, hi: int = 
     return M, N
 
 
+def batch_pair(k: int, seed: int = 3, B: int = 256, lo: int = 1000, hi: int = 20000):
+    """Pair k of the uneven chroma-like batch (as workload_batch builds it)."""
+    M, N = workload_batch_sizes(seed, B, lo, hi)
+    return chroma_pair(seed * 100003 + k, int(M[k]), int(N[k]))
+
+
 def workload_batch(seed: int = 3, B: int = 256, lo: int = 1000, hi: int = 20000):
     """The uneven batch of chroma-like pairs: list of (X, Y)."""
     M, N = workload_batch_sizes(seed, B, lo, hi)
     return [chroma_pair(seed * 100003 + k, int(M[k]), int(N[k])) for k in range(B)]
+
+
+def batch_int_pair(k: int, seed: int = 3, B: int = 256, lo: int = 1000, hi: int = 20000):
+    """Pair k of the uneven batch's integer counterpart: the same (M, N) with
+    int_pair data (values in [0, 255], noise in [-8, 8])."""
+    M, N = workload_batch_sizes(seed, B, lo, hi)
+    return int_pair(seed * 100003 + k, int(M[k]), int(N[k]))
+
+
+def workload_batch_int(seed: int = 3, B: int = 256, lo: int = 1000, hi: int = 20000):
+    """The uneven batch's shapes with 1-D int32 |x-y| data: list of (X, Y)."""
+    return [batch_int_pair(k, seed, B, lo, hi) for k in range(B)]
 
 
 @dataclasses.dataclass

@@ -72,8 +72,13 @@ def backward_moves(path):
 
 def solve(X, Y):
     """(optimal cost, canonical path, number of optimal paths, number of paths)."""
-    M, N = len(X), len(Y)
-    C = cost_table(X, Y)
+    return solve_table(cost_table(X, Y))
+
+
+def solve_table(C):
+    """solve() over a given cost table C (a list of rows, or a 2-D array)."""
+    M, N = len(C), len(C[0])
+    C = [[float(v) if not isinstance(v, int) else v for v in row] for row in C]
     best = None
     opt = []
     paths = all_paths(M, N)

@@ -317,3 +317,72 @@ def test_discrepancy_zero_and_symmetry():
     r, c = oracle.path_discrepancy(P1, P2)
     rt, ct = oracle.path_discrepancy(P1[:, ::-1], P2[:, ::-1])
     assert (rt == c).all() and (ct == r).all()
+
+
+# ------------------------------------------ oracle 1 on a given cost matrix
+
+@pytest.mark.parametrize("levels", [2, 3, 1000])
+def test_dtw_given_vs_brute_force(levels):
+    """Cost and canonical path over explicit matrices; few distinct values make
+    many optimal paths, so the tie order DIAG, UP, LEFT is exercised."""
+    rng = np.random.default_rng(300 + levels)
+    for _ in range(60):
+        M, N = (int(v) for v in rng.integers(1, 7, 2))
+        C = rng.integers(0, levels, (M, N)).astype(np.float64) * 0.25
+        best, canon, _, _ = brute.solve_table(C)
+        path, cost = oracle.dtw_given(C)
+        assert cost == best
+        assert [tuple(c) for c in path] == canon
+
+
+def test_dtw_given_equals_oracle_on_euclidean_costs():
+    """Handing oracle 1's own frame costs in as a matrix changes nothing."""
+    X, Y = np.random.default_rng(5).standard_normal((2, 40, 3)).astype(np.float32)
+    C = np.array(brute.cost_table(X, Y))
+    p1, c1 = oracle.dtw(X, Y)
+    p2, c2 = oracle.dtw_given(C)
+    assert c1 == c2 and np.array_equal(p1, p2)
+
+
+# ------------------------------------------ the BF16 tensor-core cost form
+
+def test_bf16_round_ties_to_even_and_matches_torch():
+    one = np.float32(1.0)
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7: ties go to the even 1
+    assert oracle.bf16_round(np.float32(1 + 2.0 ** -8)) == one
+    # 1 + 3 2^-8 lies halfway between 1 + 2^-7 and 1 + 2^-6: the even one is 1 + 2^-6
+    assert oracle.bf16_round(np.float32(1 + 3 * 2.0 ** -8)) == np.float32(1 + 2.0 ** -6)
+    assert oracle.bf16_round(np.float32(1 + 2.0 ** -8 + 2.0 ** -20)) == np.float32(1 + 2.0 ** -7)
+    assert oracle.bf16_round(np.float32(-1 - 2.0 ** -8)) == -one
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    a = np.concatenate([rng.standard_normal(20000).astype(np.float32) * 10.0 ** rng.integers(-6, 6, 20000),
+                        (rng.integers(-2 ** 15, 2 ** 15, 2000) * 2.0 ** -15).astype(np.float32) + np.float32(2.0 ** -24)])
+    ref = torch.from_numpy(a).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(oracle.bf16_round(a), ref)
+
+
+def test_bf16_form_costs_reduce_to_euclidean_on_bf16_frames():
+    """Frames that BF16 holds exactly: |x|^2 + |y|^2 - 2 x.y = |x - y|^2, so the
+    form's costs are the Euclidean costs of Section 4.1 (up to FP64 rounding)."""
+    rng = np.random.default_rng(12)
+    X = oracle.bf16_round(rng.standard_normal((9, 64)).astype(np.float32))
+    Y = oracle.bf16_round(rng.standard_normal((7, 64)).astype(np.float32))
+    Y[3] = X[2]  # an identical frame: the clamp at 0 holds the cost at exactly 0
+    C = oracle.bf16_form_costs(X, Y)
+    ref = np.array(brute.cost_table(X, Y))
+    assert np.allclose(C, ref, rtol=1e-12, atol=1e-6)
+    assert C[2, 3] == 0.0 or C[2, 3] < 1e-6
+
+
+def test_bf16_form_costs_handworked():
+    """d = 1, x = 1 + 2^-9, y = 1: the norms come from the FP32 frames,
+    (1 + 2^-9)^2 and 1; the dot product from the BF16 frames, 1 * 1 (1 + 2^-9
+    rounds to 1).  Cost = sqrt(2^-8 + 2^-18), not 2^-9 (an FP32 dot product)
+    nor 0 (norms of the rounded frames)."""
+    X = np.array([[1 + 2.0 ** -9]], np.float32)
+    Y = np.array([[1.0]], np.float32)
+    C = oracle.bf16_form_costs(X, Y)
+    assert C[0, 0] == pytest.approx(math.sqrt(2.0 ** -8 + 2.0 ** -18), rel=1e-12)
+    # swapped roles give the same cost
+    assert oracle.bf16_form_costs(Y, X)[0, 0] == C[0, 0]
