@@ -320,7 +320,9 @@ enum dtw_option {
                                  step, 1: 2 x 4, 2: 8 x 4, 3: 4 x 4 with each 8-step group as straight-line
                                  code (faster on long bands) (chosen by the autotuner in the Python package) */
     DTW_OPT_EDIT_SUB = 7,     /* DTW_EDIT_I32: cost of a substitution, 0 .. 2^20 (default 1) */
-    DTW_OPT_EDIT_GAP = 8      /* DTW_EDIT_I32: cost of an insertion or a deletion, 0 .. 2^20 (default 1) */
+    DTW_OPT_EDIT_GAP = 8,     /* DTW_EDIT_I32: cost of an insertion or a deletion, 0 .. 2^20 (default 1) */
+    DTW_OPT_NOALLOC_EPOCH = 9 /* test hook: the next dtw_cost_noalloc call starts its boundary-word epochs at
+                                 this value, 0 .. 2^32-1 (exercises the restart near the 32-bit limit) */
 };
 DTW_API int dtw_set_option(int32_t key, int64_t value);
 

@@ -951,6 +951,10 @@ int dtw_set_option(int32_t key, int64_t value) {
             if (value < 0 || value > (1 << 20)) return DTW_EINVAL;
             c.egap = (int32_t)value;
             return DTW_OK;
+        case DTW_OPT_NOALLOC_EPOCH:
+            if (value < 0 || value > 0xFFFFFFFFLL) return DTW_EINVAL;
+            noalloc_set_epoch(value);
+            return DTW_OK;
         default: return DTW_EINVAL;
     }
 }

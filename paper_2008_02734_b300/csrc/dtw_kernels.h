@@ -130,6 +130,8 @@ cudaError_t launch_level_cond(LevelCtl* ctl, cudaGraphConditionalHandle h, int m
 
 // Serving engine (serve.cu): device memory its groups may take from now on.
 void serve_set_budget(uint64_t bytes);
+// dtw_cost_noalloc (noalloc.cu), test hook: the next call's first boundary-word epoch.
+void noalloc_set_epoch(long long ep);
 
 // The paper's plain form (plain.cu)
 struct PlainProblem {

@@ -7,6 +7,8 @@
 // device array defined in this file.  The array is part of the library's
 // device image: every GPU that loads the library holds it until the process
 // exits, and every call on a device reuses the same bytes.
+#include <atomic>
+#include <cmath>
 #include <mutex>
 
 #include "dtw_b300.h"
@@ -30,9 +32,13 @@ constexpr size_t kOffSweep = kOffBox + up256(sizeof(Box));
 constexpr size_t kOffRes = kOffSweep + up256(sizeof(Sweep));
 constexpr size_t kOffCtl = kOffRes + up256(sizeof(SweepRes));
 constexpr size_t kOffMinMax = kOffCtl + up256(sizeof(LevelCtl));
+constexpr size_t kOffClear = kOffMinMax + 128;  // 1: this call clears the boundary row first
 constexpr long long kBufWords = 2 * (kShortMax + kPadCols);  // two epoch-stamped words per column
 constexpr size_t kOffBuf = kOffMinMax + 256;
 constexpr size_t kScratchBytes = kOffBuf + up256(8 * (size_t)kBufWords);
+// Epochs one call may take: the plan gives each band of the sweep its own (a
+// band has at least 32 rows), plus one.
+constexpr uint32_t kCallEpochs = (uint32_t)(kLongMax / 32 + 2);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -44,7 +50,10 @@ int g_sms[kMaxDevices] = {};
 // Writes the pair, the root box and a zeroed control block for this call (the
 // previous call's contents are still there).  The boundary-word epoch counter
 // is carried over, so that words left by earlier calls are never accepted.
-__global__ void noalloc_init_kernel(const void* X, int M, const void* Y, int N) {
+// When the counter could wrap within this call (or a test sets it, ep_set >= 0),
+// the epochs restart at 1 and the call first clears the boundary row: no word
+// written before the restart can then bear an epoch the call expects.
+__global__ void noalloc_init_kernel(const void* X, int M, const void* Y, int N, long long ep_set) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     PairDesc* pd = reinterpret_cast<PairDesc*>(g_noalloc_scratch + kOffPair);
     pd->X = X;
@@ -62,13 +71,29 @@ __global__ void noalloc_init_kernel(const void* X, int M, const void* Y, int N) 
     b->W = N;
     b->flags = BOX_ROOT;
     b->known_i = -1;
-    b->known_f = 0.0;
+    b->known_f = NAN;
     LevelCtl* c = reinterpret_cast<LevelCtl*>(g_noalloc_scratch + kOffCtl);
-    const uint32_t ep = c->epoch_base;
+    uint32_t ep = ep_set >= 0 ? (uint32_t)ep_set : c->epoch_base;
+    int* clear = reinterpret_cast<int*>(g_noalloc_scratch + kOffClear);
+    *clear = 0;
+    if (ep == 0 || ep > 0xFFFFFFFFu - kCallEpochs) {
+        ep = 1;
+        *clear = 1;
+    }
     *c = LevelCtl{};
-    c->epoch_base = ep == 0 ? 1u : ep;
+    c->epoch_base = ep;
     SweepRes* r = reinterpret_cast<SweepRes*>(g_noalloc_scratch + kOffRes);
     *r = SweepRes{};
+}
+
+// Zeroes the boundary row when the init kernel restarted the epochs (otherwise
+// every thread returns at once).
+__global__ void noalloc_clear_kernel() {
+    if (*reinterpret_cast<const int*>(g_noalloc_scratch + kOffClear) == 0) return;
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(g_noalloc_scratch + kOffBuf);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < kBufWords;
+         i += (long long)gridDim.x * blockDim.x)
+        w[i] = 0ull;
 }
 
 bool on_device(const void* p) {
@@ -101,8 +126,13 @@ int setup(int dev, char** base, int* sms) {
 }
 
 std::mutex g_call_mu;  // the scratch is shared: one call at a time from the host
+std::atomic<long long> g_ep_set{-1};  // test hook: the next call's first epoch
 
 }  // namespace
+
+namespace dtwb {
+void noalloc_set_epoch(long long ep) { g_ep_set.store(ep); }
+}  // namespace dtwb
 
 extern "C" int dtw_cost_noalloc(const void* X, int64_t M, const void* Y, int64_t N, int32_t d, int32_t cost_kind,
                                 double* cost_out, void* cuda_stream) {
@@ -131,8 +161,12 @@ extern "C" int dtw_cost_noalloc(const void* X, int64_t M, const void* Y, int64_t
     LevelCtl* ctl = reinterpret_cast<LevelCtl*>(base + kOffCtl);
     int32_t* minmax = reinterpret_cast<int32_t*>(base + kOffMinMax);
 
-    noalloc_init_kernel<<<1, 32, 0, st>>>(X, (int)M, Y, (int)N);
+    noalloc_init_kernel<<<1, 32, 0, st>>>(X, (int)M, Y, (int)N, g_ep_set.exchange(-1));
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        noalloc_clear_kernel<<<sms, 256, 0, st>>>();
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess && kind == KIND_ABS) e = launch_int_range_check(pairs, 1, (int)hi, minmax, ctl, st);
     // the plan resets the band ticket and assigns this call's epochs
     PlanArgs pa{box, 1, pairs, MODE_COST, kind, 0, sweep_block_cols(kind, d), sweep_band_rows(kind, d),
@@ -146,7 +180,13 @@ extern "C" int dtw_cost_noalloc(const void* X, int64_t M, const void* Y, int64_t
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hr, res, sizeof(hr), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return DTW_ECUDA;
+    if (e != cudaSuccess) {
+        // kernels enqueued before the failure may still run on the shared array:
+        // wait for them before another call may start
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        return DTW_ECUDA;
+    }
     switch (hc.err) {
         case ERR_NONE: break;
         case ERR_TIMEOUT: return DTW_ETIMEOUT;

@@ -42,6 +42,7 @@
 // cell copies the tag of its backpointer (first minimum in the order DIAG, UP,
 // LEFT).  The tag reaching the last cell names the column where the canonical
 // backtrace meets the split row, so that cell lies on the canonical path.
+#include <atomic>
 #include <climits>
 #include <type_traits>
 
@@ -1193,16 +1194,25 @@ static cudaError_t setup_one(int* nb_out) {
     constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
     constexpr size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>();
     static_assert(smem <= 227 * 1024, "the block's rings exceed the shared memory of an SM (see yslots)");
-    static int nb = 0;
-    if (nb == 0) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<KIND, R, U, DIM, TAGS, FULL>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // per device: the attribute is set in (and the occupancy read for) the
+    // context of the device that is current
+    constexpr int kDevs = 64;
+    static std::atomic<int> nb[kDevs];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kDevs) return cudaErrorInvalidDevice;
+    int v = nb[dev].load(std::memory_order_acquire);
+    if (v == 0) {
+        e = cudaFuncSetAttribute(sweep_kernel<KIND, R, U, DIM, TAGS, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
         if (e != cudaSuccess) return e;
         int n = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<KIND, R, U, DIM, TAGS, FULL>, threads_of<KIND>(), smem);
-        nb = n < 1 ? 1 : n;
+        v = n < 1 ? 1 : n;
+        nb[dev].store(v, std::memory_order_release);
     }
-    *nb_out = nb;
+    *nb_out = v;
     return cudaSuccess;
 }
 

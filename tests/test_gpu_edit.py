@@ -1,6 +1,9 @@
 """Edit distance (Section 5's generalisation) through the same recursion and the
 C ABI, against the edit-distance oracle: cost and node path bit for bit (the
 canonical DIAG > UP > LEFT path) on every case."""
+import hashlib
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -10,6 +13,8 @@ import paper_2008_02734_b300 as dtw
 from paper_2008_02734_b300 import synth
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN_EDIT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "edit_20000.txt")
 
 
 @pytest.fixture(autouse=True)
@@ -84,16 +89,20 @@ def test_larger_pair():
     check_edit(X, Y)
 
 
-def test_full_size_properties():
-    """The 20000-symbol workload: the path is a node path whose edge costs sum to
-    the returned cost, and the cost equals the one-sweep cost."""
+def test_full_size_against_stored_oracle():
+    """The 20000-symbol workload (unit costs): cost and canonical node path equal
+    the edit oracle's, stored by tests/golden/make_workload_goldens.py (the path
+    by its length and SHA-256); the one-sweep cost agrees."""
+    with open(GOLDEN_EDIT) as f:
+        row = [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")][-1].split("|")
+    M, N, c_ref, K_ref = (int(v) for v in row[:4])
     X, Y = synth.workload_edit_pair()
+    assert (len(X), len(Y)) == (M, N)
     path, cost = dtw.edit_align(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda())
     p = path.cpu().numpy()
-    M, N = len(X), len(Y)
-    assert p[0].tolist() == [0, 0] and p[-1].tolist() == [M, N]
-    steps = np.diff(p, axis=0)
-    assert np.all((steps == [1, 1]).all(1) | (steps == [1, 0]).all(1) | (steps == [0, 1]).all(1))
+    assert cost == c_ref
+    assert len(p) == K_ref
+    assert hashlib.sha256(np.ascontiguousarray(p, dtype="<i4").tobytes()).hexdigest() == row[4]
     assert oracle.edit_path_cost(X, Y, p) == cost
     assert dtw.edit_distance(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()) == cost
 

@@ -1,6 +1,9 @@
 """Local alignment (Smith-Waterman, named in Section 5) through the C ABI in
 linear memory, against the local-alignment oracle: score, start and end nodes
 and the node path, bit for bit."""
+import hashlib
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -10,6 +13,8 @@ import paper_2008_02734_b300 as dtw
 from paper_2008_02734_b300 import synth
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN_LOCAL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "local_20000x24000.txt")
 
 
 @pytest.fixture(autouse=True)
@@ -62,20 +67,24 @@ def test_degenerate():
     check_local(X, X.copy())                                                      # identical: the diagonal
 
 
-def test_full_size_properties():
-    """20000 vs 24000 symbols sharing a mutated 5000-symbol stretch: the path runs
-    from the start to the end node, its score is the local score, and the
-    global alignment score of the two substrings equals it."""
+def test_full_size_against_stored_oracle():
+    """20000 vs 24000 symbols sharing a mutated 5000-symbol stretch, scores
+    +2 / -3 / -3: score, start and end nodes and node path equal the oracle's,
+    stored by tests/golden/make_workload_goldens.py (the path by its length and
+    SHA-256); the path's own score is the local score."""
+    with open(GOLDEN_LOCAL) as f:
+        row = [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")][-1].split("|")
+    M, N, s_ref, a_s0, b_s0, a_e0, b_e0, K_ref = (int(v) for v in row[:8])
     X, Y = synth.workload_local_pair()
-    path, score, (a_s, b_s, a_e, b_e) = dtw.local_align(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda())
+    assert (len(X), len(Y)) == (M, N)
+    path, score, (a_s, b_s, a_e, b_e) = dtw.local_align(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(),
+                                                         match=2, mismatch=3, gap=3)
     p = path.cpu().numpy()
-    assert score > 0
-    assert p[0].tolist() == [a_s, b_s] and p[-1].tolist() == [a_e, b_e]
-    steps = np.diff(p, axis=0)
-    assert np.all((steps == [1, 1]).all(1) | (steps == [1, 0]).all(1) | (steps == [0, 1]).all(1))
+    assert score == s_ref
+    assert (a_s, b_s, a_e, b_e) == (a_s0, b_s0, a_e0, b_e0)
+    assert len(p) == K_ref
+    assert hashlib.sha256(np.ascontiguousarray(p, dtype="<i4").tobytes()).hexdigest() == row[8]
     sc = 0
     for (a0, b0), (a1, b1) in zip(p[:-1], p[1:]):
-        sc += (2 if X[a1 - 1] == Y[b1 - 1] else -1) if (a1 - a0 == 1 and b1 - b0 == 1) else -1
+        sc += (2 if X[a1 - 1] == Y[b1 - 1] else -3) if (a1 - a0 == 1 and b1 - b0 == 1) else -3
     assert sc == score
-    _, sub_cost = oracle.edit(X[a_s:a_e], Y[b_s:b_e], 1, 1)  # unit-cost distance of the pieces: a sanity bound
-    assert sub_cost <= (a_e - a_s) + (b_e - b_s)

@@ -305,56 +305,20 @@ def test_dp_f32_kahan_batch_and_serving():
     assert rc == dtw.OK and c == pytest.approx(oracle.dtw(X, Y)[1], rel=REL_TOL)
 
 
-def _bf16(a):
-    """Round-to-nearest-even FP32 -> BF16, returned as FP32 values."""
-    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
-    return u.astype(np.uint32).view(np.float32)
-
-
-def _bf16_form_costs(X, Y):
-    """The BF16 form's cost matrix, evaluated in FP64 from the same inputs:
-    sqrt(max(0, |x|^2 + |y|^2 - 2 bf16(x).bf16(y)))."""
-    X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
-    xx = (X64 ** 2).sum(1)
-    yy = (Y64 ** 2).sum(1)
-    dot = _bf16(X).astype(np.float64) @ _bf16(Y).astype(np.float64).T
-    return np.sqrt(np.maximum(0.0, xx[:, None] + yy[None, :] - 2.0 * dot))
-
-
-def _dtw_on_costs(C):
-    """Textbook DP over a given cost matrix, one anti-diagonal at a time."""
-    M, N = C.shape
-    D = np.full((M, N), np.inf)
-    for k in range(M + N - 1):
-        i = np.arange(max(0, k - N + 1), min(M, k + 1))
-        j = k - i
-        best = np.full(len(i), np.inf)
-        if k == 0:
-            best[:] = 0.0
-        m = (i > 0) & (j > 0)
-        best[m] = np.minimum(best[m], D[i[m] - 1, j[m] - 1])
-        m = i > 0
-        best[m] = np.minimum(best[m], D[i[m] - 1, j[m]])
-        m = j > 0
-        best[m] = np.minimum(best[m], D[i[m], j[m] - 1])
-        D[i, j] = C[i, j] + best
-    return D[-1, -1]
-
-
 @pytest.mark.parametrize("M,N,base_area", [(1, 5, 16384), (50, 70, 16384), (200, 300, 16384), (333, 129, 4),
                                            (700, 650, 64), (1100, 1300, 16384)])
 def test_cost_bf16_form(M, N, base_area):
     """Tensor-core BF16 cost tiles: the result is the optimum of the form's own
-    costs (checked against the same costs evaluated in FP64 on the CPU and a
-    textbook DP), and the path is a warping path carrying that cost."""
+    costs (the oracle's BF16-form cost matrix, evaluated in FP64, under oracle
+    1's DP), and the path is a warping path carrying that cost.  The GPU takes
+    the norms and the dot products in FP32, hence the 2e-4 relative bound."""
     dtw.set_option(dtw.OPT_BASE_AREA, base_area)
     X, Y = synth.mfcc_pair(M * 3 + N, M, N)
     path, cost = dtw.align(_cuda(X), _cuda(Y), cost_bf16=True)
     p = path.cpu().numpy()
     check_path_struct(p, M, N)
-    C = _bf16_form_costs(X, Y)
-    ref = _dtw_on_costs(C)
+    C = oracle.bf16_form_costs(X, Y)
+    ref = oracle.dtw_given(C)[1]
     assert cost == pytest.approx(ref, rel=2e-4, abs=1e-6)
     assert C[p[:, 0], p[:, 1]].sum() == pytest.approx(ref, rel=2e-4, abs=1e-6)
     assert dtw.cost(_cuda(X), _cuda(Y), cost_bf16=True) == pytest.approx(ref, rel=2e-4, abs=1e-6)

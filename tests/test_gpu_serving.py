@@ -28,42 +28,74 @@ def _dev(cuda_device):
     yield
 
 
-def _alone(X, Y):
-    path, cost = dtw.align(_cuda(X), _cuda(Y))
+# The BF16 form against its own cost model (the oracle's BF16-form costs under
+# oracle 1's DP; the GPU takes norms and dot products in FP32): 2e-4 relative.
+BF16_FORM_TOL = 2e-4
+# The BF16 form against the exact FP64 optimum, for these short d=64 pairs (1 to
+# 1500 frames): 5e-3 relative.  A cell's cost moves by up to
+# sqrt(2^-7 |x| |y|) where frames are near-identical, and a short path averages
+# few cells (one pair here measured 1.03e-3; the 60000 x 75000 pair, 4.9e-5
+# against its stated 1e-3).
+BF16_EXACT_TOL = 5e-3
+
+
+def _alone(X, Y, **form):
+    path, cost = dtw.align(_cuda(X), _cuda(Y), **form)
     return path.cpu().numpy(), cost
 
 
 def test_mixed_stream_matches_alone():
+    """Integer, chroma d=12 and MFCC-like d=64 requests (the d=64 ones in the
+    exact FP32-cost form and in the BF16 tensor-core form), on host and device
+    buffers, submitted in waves while earlier ones run: every result equals the
+    same pair aligned alone by dtw_align in the same form (integer: bit for bit;
+    float forms: 1e-6 relative); against the FP64 oracle the exact forms lie
+    within 1e-6 (cost, and the path re-scored in FP64); the BF16 form lies within
+    2e-4 of the oracle's optimum of the BF16-form costs (cost and re-scored path)
+    and within 5e-3 of the exact FP64 optimum."""
     rng = np.random.default_rng(7)
     jobs = []
-    for k in range(24):
+    for k in range(32):
         M = int(rng.integers(1, 3000))
         N = int(rng.integers(1, 3000))
-        if k % 3 == 2:
+        form = {}
+        if k % 4 == 2:
             X, Y = synth.chroma_pair(1000 + k, M, N)
+        elif k % 4 == 3:
+            X, Y = synth.mfcc_pair(1000 + k, M // 2 + 1, N // 2 + 1)
+            form = {"cost_bf16": True} if k % 8 == 7 else {}
         else:
             X, Y = synth.int_pair(1000 + k, M, N)
         on_dev = k % 2 == 0
-        jobs.append((X, Y, on_dev))
+        jobs.append((X, Y, on_dev, form))
     tickets = []
-    for i, (X, Y, on_dev) in enumerate(jobs):
+    for i, (X, Y, on_dev, form) in enumerate(jobs):
         xs, ys = (_cuda(X), _cuda(Y)) if on_dev else (X, Y)
         path_buf = None if on_dev else torch.empty((len(X) + len(Y) - 1, 2), dtype=torch.int32)
-        tickets.append(dtw.submit(xs, ys, path_out=path_buf))
+        tickets.append(dtw.submit(xs, ys, path_out=path_buf, **form))
         if i % 5 == 4:  # let earlier requests get under way before more arrive
             dtw.poll(tickets[0][0])
-    for (X, Y, on_dev), (t, path, keep) in zip(jobs, tickets):
+    for (X, Y, on_dev, form), (t, path, keep) in zip(jobs, tickets):
         rc, K, c = dtw.wait(t)
         assert rc == dtw.OK, dtw.DTWError(rc, "serve")
         p = path[:K].cpu().numpy()
-        p_ref, c_ref = _alone(X, Y)
+        p_ref, c_ref = _alone(X, Y, **form)
         if X.dtype == np.int32:
             assert c == c_ref
             assert np.array_equal(p, p_ref)
             assert c == oracle.dtw(X, Y)[1]
+        elif form.get("cost_bf16"):
+            assert c == pytest.approx(c_ref, rel=REL_TOL, abs=1e-9)
+            C = oracle.bf16_form_costs(X, Y)
+            c_form = oracle.dtw_given(C)[1]
+            assert c == pytest.approx(c_form, rel=BF16_FORM_TOL, abs=1e-6)
+            assert C[p[:, 0], p[:, 1]].sum() == pytest.approx(c_form, rel=BF16_FORM_TOL, abs=1e-6)
+            assert c == pytest.approx(oracle.dtw(X, Y)[1], rel=BF16_EXACT_TOL, abs=1e-6)
         else:
             assert c == pytest.approx(c_ref, rel=REL_TOL, abs=1e-9)
-            assert oracle.path_cost(X, Y, p) == pytest.approx(oracle.dtw(X, Y)[1], rel=REL_TOL, abs=1e-9)
+            c_opt = oracle.dtw(X, Y)[1]
+            assert c == pytest.approx(c_opt, rel=REL_TOL, abs=1e-9)
+            assert oracle.path_cost(X, Y, p) == pytest.approx(c_opt, rel=REL_TOL, abs=1e-9)
 
 
 def test_late_request_admitted_while_long_one_runs():
