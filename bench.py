@@ -325,15 +325,22 @@ def run_ours(args):
     e2e_total = max_over_ranks(sum(e2e_ms), dev)
     e2e_value = whole_job_gcups(M * N, ws, args.steps, e2e_total)
 
-    # the paper's plain FP64 GPU form on the same pair (one run; its own clock)
+    # the paper's plain FP64 GPU form on the same pair (one warm-up run, then the
+    # mean of two timed runs on the host clock around synchronised calls)
     plain = None
     if not args.no_plain:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
         pp, pc = dtw.align(Xd, Yd, plain=True)
-        torch.cuda.synchronize()
-        pt = time.perf_counter() - t0
-        plain = {"gcups": M * N / pt / 1e9, "ms": 1e3 * pt, "cost_equal": bool(pc == cost),
+        pts = []
+        for _ in range(2):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pp, pc = dtw.align(Xd, Yd, plain=True)
+            torch.cuda.synchronize()
+            pts.append(time.perf_counter() - t0)
+        pt = float(np.mean(pts))
+        plain = {"gcups": M * N / pt / 1e9, "ms": 1e3 * pt, "runs_ms": [1e3 * t for t in pts],
+                 "cost_equal": bool(pc == cost), "warmup": 1,
                  "form": "one launch per anti-diagonal, one thread per cell, FP64 cost and DP, host recursion, "
                          "textbook DTW below side 500"}
 
@@ -370,6 +377,13 @@ def run_ours(args):
         e = err.cpu().numpy().ravel()
         disc = {"of": "GPU path vs oracle 1 path", "max_frames": emax,
                 "within_frames": {str(f): float(np.mean(e <= f)) for f in (0, 1, 2)}}
+    # the other configurations, each with its own timing, roofline and error
+    # against the oracle (single-GPU default runs of the integer pair only)
+    extra = {}
+    if args.workload == "int_pair" and ws == 1 and not args.no_extra:
+        extra["c3_batch"] = measure_batch(steps=5, warmup=3, tune=True)
+        extra["c2_precision"] = measure_precision(steps=2, warmup=3, forms=("f32cost_f64dp", "bf16cost_f32kahan"))
+        extra["c4_serving"] = measure_serving(requests=2000, max_len=20000, budget_gb=64.0, rho=0.7)
     line = {
         "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total / args.steps, "higher_is_better": True,
@@ -378,7 +392,8 @@ def run_ours(args):
         "config": {"workload": WORKLOADS[args.workload][0], "M": M, "N": N, "pairs_per_rank": 1,
                    "parallelism": f"replicas{ws}", "l2": "flushed between steps (256 MiB write outside the events)",
                    "autotuned": None if tuned is None else {"sweep_variant": tuned["variant"],
-                                                           "base_area": tuned["base_area"]},
+                                                           "base_area": tuned["base_area"],
+                                                           "table": tuned["table"]},
                    "fixed": None if args.variant is None and args.base_area is None else
                    {"sweep_variant": args.variant, "base_area": args.base_area}},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -393,6 +408,7 @@ def run_ours(args):
         "path_discrepancy_vs_oracle": disc,
         "clocks": clk.summary(),
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -403,63 +419,123 @@ def _percentiles(ms):
     return {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))}
 
 
-def run_batch_workload(args):
-    """The uneven batch: 256 chroma-like d=12 pairs, M log-uniform in [1000, 20000],
-    N = clip(r M), r log-uniform in [0.8, 1.25]; all pairs through dtw_align_batch
-    (every pair's boxes of a level share the launches).  value = sum(M N) / time."""
+# Measured per-SM-and-clock issue rates of the instructions the rooflines count
+# (dtw_pipe_rates on a B300, profiles/pipe_rates.md): the FP64 add of the FP64 DP.
+FP64_ADD_PER_SM_CLK = 1.65
+# Algorithmic lane instructions per cell of the BF16 form: 2 adds, a maximum and a
+# square root of the expanded cost, a compensated add (4) and two minima.
+BF16_FORM_I_CELL = 10.0
+# The FP32-cost form at d = 64 with the compensated DP: 64 lane instructions for
+# the 64 differences and squares in packed FP32x2 arithmetic, a square root, and
+# the compensated add and minima (10).
+F32COST_D64_I_CELL = 75.0
+
+
+def _peak_rates(dev=None):
+    """(SM count, max SM clock in MHz, its source) of this GPU."""
+    import torch
+    peaks, src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev or 0).multi_processor_count
+    return sms, float(peaks.get("sm_max_mhz", 2032.0)), src
+
+
+def _golden_rows(name):
+    with open(os.path.join(ROOT, "tests", "golden", name)) as f:
+        return [ln.strip().split("|") for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def measure_batch(steps: int, warmup: int, tune: bool = True, check: bool = True):
+    """The uneven batch (256 chroma-like d=12 pairs) through dtw_align_batch:
+    time per batch (CUDA events, L2 flushed between steps), GCUPS, the end-to-end
+    figure from pinned host buffers, the roofline against the FP64-add pipe (the
+    FP64 DP's one add per cell) and the largest cost error against oracle 1's
+    stored costs (tests/golden/batch_chroma_256.txt)."""
     import torch
 
     import paper_2008_02734_b300 as dtw
 
-    pairs = synth.workload_batch(B=args.batch)
+    pairs = synth.workload_batch()
+    B = len(pairs)
     cells = float(sum(len(x) * len(y) for x, y in pairs))
     Xs = [torch.from_numpy(x).cuda() for x, _ in pairs]
     Ys = [torch.from_numpy(y).cuda() for _, y in pairs]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     tuned = None
-    if not args.no_tune:
+    if tune:
         # the library's autotuner picks the base-case cutoff on this batch
         from paper_2008_02734_b300 import autotune
         tuned = autotune.tune_batch(Xs, Ys)
-    for _ in range(max(args.warmup, 3)):
-        dtw.align_batch(Xs, Ys)
+    for _ in range(max(warmup, 3)):
+        res = dtw.align_batch(Xs, Ys)
     ms = []
-    for _ in range(args.steps):
+    launches = 0
+    for _ in range(steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        dtw.align_batch(Xs, Ys)
+        res = dtw.align_batch(Xs, Ys)
         b.record(stream)
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
+        launches += dtw.get_stats()["kernel_launches"]
     st = dtw.get_stats()
+    processed = float(st["sweep_cells"] + st["base_cells"])
+    err = None
+    if check:
+        ref = [float(r[3]) for r in _golden_rows("batch_chroma_256.txt")]
+        err = max(abs(c - r) / r for (_, c), r in zip(res, ref))
     # end to end from pinned host buffers (paths come back to host buffers too)
     Xh = [torch.from_numpy(x).pin_memory() for x, _ in pairs]
     Yh = [torch.from_numpy(y).pin_memory() for _, y in pairs]
     Ph = [torch.empty((len(x) + len(y) - 1, 2), dtype=torch.int32).pin_memory() for x, y in pairs]
     e2e = []
-    for _ in range(max(1, args.steps // 2)):
+    for _ in range(max(1, steps // 2)):
+        flush.zero_()
         torch.cuda.synchronize()
         t = time.perf_counter()
         dtw.align_batch(Xh, Yh, paths_out=Ph)
         e2e.append(1e3 * (time.perf_counter() - t))
-    h2d = int(sum(x.nbytes + y.nbytes for x, y in pairs))
-    d2h = int(sum(8 * (len(x) + len(y) - 1) for x, y in pairs))
-    line = {"metric": METRIC, "value": cells / (np.mean(ms) / 1e3) / 1e9, "unit": "GCUPS", "n_gpus": 1,
-            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": float(np.mean(ms)),
+    sms, mhz, src = _peak_rates()
+    mean_ms = float(np.mean(ms))
+    fp64_peak = sms * FP64_ADD_PER_SM_CLK * mhz * 1e6 / 1e9  # Gcells/s
+    achieved = processed / (mean_ms / 1e3) / 1e9
+    return {
+        "workload": f"uneven batch: {B} chroma-like d=12 FP32 pairs, M log-uniform [1000,20000], N = clip(r M), "
+                    "r log-uniform [0.8,1.25]; FP32 cost, FP64 DP",
+        "pairs": B, "problem_cells": cells, "processed_cells_per_step": processed, "steps": steps,
+        "ms_per_step": mean_ms, "gcups": cells / (mean_ms / 1e3) / 1e9, "latency_ms": _percentiles(ms),
+        "e2e": {"gcups": cells / (np.mean(e2e) / 1e3) / 1e9, "ms": float(np.mean(e2e)),
+                "h2d_bytes_per_step": int(sum(x.nbytes + y.nbytes for x, y in pairs)),
+                "d2h_bytes_per_step": int(sum(8 * (len(x) + len(y) - 1) for x, y in pairs))},
+        "gpu_launches": launches, "levels": st["levels"],
+        "roofline": {"bound": "fp64", "achieved": achieved, "peak": fp64_peak, "unit": "Gcells/s",
+                     "frac": achieved / fp64_peak,
+                     "peak_source": f"{sms} SMs x {FP64_ADD_PER_SM_CLK} FP64 adds per SM and clock (measured, "
+                                    f"profiles/pipe_rates.md) x {mhz:.0f} MHz ({src}); one FP64 add per processed cell"},
+        "max_rel_err_vs_oracle": err, "oracle_source": "tests/golden/batch_chroma_256.txt",
+        "l2": "flushed between steps",
+        "autotuned": None if tuned is None else {"base_area": tuned["base_area"]},
+    }
+
+
+def run_batch_workload(args):
+    """The uneven batch: 256 chroma-like d=12 pairs, M log-uniform in [1000, 20000],
+    N = clip(r M), r log-uniform in [0.8, 1.25]; all pairs through dtw_align_batch
+    (every pair's boxes of a level share the launches).  value = sum(M N) / time."""
+    r = measure_batch(args.steps, args.warmup, tune=not args.no_tune)
+    line = {"metric": METRIC, "value": r["gcups"], "unit": "GCUPS", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": r["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-cost/f64-dp",
             "data": "synthetic",
-            "config": {"workload": f"uneven batch: {args.batch} chroma-like d=12 FP32 pairs, M log-uniform "
-                                   "[1000,20000], N = clip(r M), r log-uniform [0.8,1.25]",
-                       "pairs": args.batch, "problem_cells": cells, "l2": "flushed between steps",
-                       "autotuned": None if tuned is None else {"base_area": tuned["base_area"],
-                                                                "table": tuned["table"]}},
-            "latency_ms": _percentiles(ms),
-            "e2e": {"value": cells / (np.mean(e2e) / 1e3) / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "gpu_launches": st["kernel_launches"], "levels": st["levels"],
-            "processed_cells_per_step": st["sweep_cells"] + st["base_cells"]}
+            "config": {"workload": r["workload"], "pairs": r["pairs"], "problem_cells": r["problem_cells"],
+                       "l2": r["l2"], "autotuned": r["autotuned"]},
+            "latency_ms": r["latency_ms"],
+            "e2e": {"value": r["e2e"]["gcups"], "unit": "GCUPS", "h2d_bytes_per_step": r["e2e"]["h2d_bytes_per_step"],
+                    "d2h_bytes_per_step": r["e2e"]["d2h_bytes_per_step"]},
+            "gpu_launches": r["gpu_launches"], "levels": r["levels"],
+            "processed_cells_per_step": r["processed_cells_per_step"], "roofline": r["roofline"],
+            "max_rel_err_vs_oracle": r["max_rel_err_vs_oracle"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -478,12 +554,21 @@ def golden_mfcc_cost():
         return None
 
 
-def run_precision_workload(args):
-    """The orchestral-length pair: 60000 x 64-d MFCC-like frames vs a 75000-frame
-    warp plus noise, in each precision form: FP32 frame cost with FP64
-    accumulation (exact form), FP32 cost with compensated FP32 accumulation, and
-    BF16 tensor-core cost tiles (FP32 accumulation) with compensated FP32 DP.
-    Each form's optimal cost is set against the FP64 oracle's."""
+PRECISION_FORMS = (
+    ("f32cost_f64dp", {}, "FP32 frame cost, FP64 DP"),
+    ("f32cost_f32kahan", {"dp_f32": True}, "FP32 frame cost, compensated FP32 DP"),
+    ("bf16cost_f32kahan", {"cost_bf16": True}, "BF16 tensor-core cost tiles (FP32 accumulation), compensated FP32 DP"),
+)
+
+
+def measure_precision(steps: int, warmup: int, forms=("f32cost_f64dp", "f32cost_f32kahan", "bf16cost_f32kahan"),
+                      discrepancy: bool = True):
+    """The orchestral-length pair (60000 x 64-d MFCC-like frames vs a 75000-frame
+    warp plus noise) in the given precision forms: time per alignment, GCUPS,
+    relative error against the FP64 oracle's stored optimum, and the roofline of
+    the form's binding bound (FP64 DP: the FP64-add pipe, one add per processed
+    cell; compensated FP32 forms: the ALU issue rate at the form's algorithmic
+    instructions per cell)."""
     import torch
 
     import paper_2008_02734_b300 as dtw
@@ -493,45 +578,66 @@ def run_precision_workload(args):
     Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
     stream = torch.cuda.current_stream()
     c_ref = golden_mfcc_cost()
-    forms, paths = {}, {}
-    for name, kw, desc in (("f32cost_f64dp", {}, "FP32 frame cost, FP64 DP"),
-                           ("f32cost_f32kahan", {"dp_f32": True}, "FP32 frame cost, compensated FP32 DP"),
-                           ("bf16cost_f32kahan", {"cost_bf16": True},
-                            "BF16 tensor-core cost tiles (FP32 accumulation), compensated FP32 DP")):
-        for _ in range(max(args.warmup, 3)):
+    sms, mhz, src = _peak_rates()
+    issue = sms * 4 * 32 * mhz * 1e6 / 1e9  # lane instructions per ns
+    out, paths = {}, {}
+    for name, kw, desc in PRECISION_FORMS:
+        if name not in forms:
+            continue
+        for _ in range(max(warmup, 3)):
             dtw.align(Xd, Yd, **kw)
         ms = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             path, cost = dtw.align(Xd, Yd, **kw)
             b.record(stream)
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
+        st = dtw.get_stats()
+        processed = float(st["sweep_cells"] + st["base_cells"])
+        mean_ms = float(np.mean(ms))
+        achieved = processed / (mean_ms / 1e3) / 1e9
+        if name == "f32cost_f64dp":
+            rl = {"bound": "fp64", "peak": sms * FP64_ADD_PER_SM_CLK * mhz * 1e6 / 1e9,
+                  "peak_source": f"{sms} SMs x {FP64_ADD_PER_SM_CLK} FP64 adds per SM and clock (measured) x "
+                                 f"{mhz:.0f} MHz ({src}); one FP64 add per processed cell"}
+        else:
+            icell = BF16_FORM_I_CELL if name.startswith("bf16") else F32COST_D64_I_CELL
+            rl = {"bound": "alu", "peak": issue / icell,
+                  "peak_source": f"{sms} SMs x 4 x 32 lanes x {mhz:.0f} MHz ({src}) / {icell:.0f} algorithmic lane "
+                                 "instructions per cell"}
+        rl.update({"achieved": achieved, "unit": "Gcells/s", "frac": achieved / rl["peak"]})
         paths[name] = path
-        forms[name] = {"form": desc, "ms": float(np.mean(ms)), "gcups": M * N / (np.mean(ms) / 1e3) / 1e9,
-                       "cost": cost, "rel_err_vs_oracle": None if c_ref is None else abs(cost - c_ref) / c_ref}
-    # Section 4.3's alignment discrepancy of the BF16 form's path against the
-    # exact form's, as the share of errors within 1, 2, 22 and 43 frames (23 ms,
-    # 47 ms, 0.51 s and 1 s at the features' ~43 frames per second)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    err, emax = dtw.path_discrepancy(paths["bf16cost_f32kahan"], paths["f32cost_f64dp"], M, N)
-    b.record(stream)
-    torch.cuda.synchronize()
-    e = err.cpu().numpy().ravel()
-    disc = {"of": "bf16cost_f32kahan path vs f32cost_f64dp path", "cells": int(err.shape[1]), "max_frames": emax,
-            "within_frames": {str(f): float(np.mean(e <= f)) for f in (0, 1, 2, 22, 43)},
-            "call_ms": a.elapsed_time(b)}
-    ex = forms["f32cost_f64dp"]
+        out[name] = {"form": desc, "ms": mean_ms, "gcups": M * N / (mean_ms / 1e3) / 1e9, "cost": cost,
+                     "rel_err_vs_oracle": None if c_ref is None else abs(cost - c_ref) / c_ref,
+                     "processed_cells": processed, "roofline": rl}
+    disc = None
+    if discrepancy and "bf16cost_f32kahan" in paths and "f32cost_f64dp" in paths:
+        # Section 4.3's alignment discrepancy of the BF16 form's path against the
+        # exact form's, as the share of errors within 1, 2, 22 and 43 frames (23 ms,
+        # 47 ms, 0.51 s and 1 s at the features' ~43 frames per second)
+        err, emax = dtw.path_discrepancy(paths["bf16cost_f32kahan"], paths["f32cost_f64dp"], M, N)
+        e = err.cpu().numpy().ravel()
+        disc = {"of": "bf16cost_f32kahan path vs f32cost_f64dp path", "cells": int(err.shape[1]), "max_frames": emax,
+                "within_frames": {str(f): float(np.mean(e <= f)) for f in (0, 1, 2, 22, 43)}}
+    return {"workload": "orchestral-length pair: 60000 x 64-d MFCC-like vs 75000-frame warp + N(0,0.1^2)",
+            "M": M, "N": N, "steps": steps, "oracle_cost": c_ref,
+            "oracle_source": "tests/golden/mfcc_pair_60000x75000.txt", "forms": out, "path_discrepancy": disc}
+
+
+def run_precision_workload(args):
+    """The orchestral-length pair in each precision form; value is the exact
+    (FP32 cost, FP64 DP) form's GCUPS."""
+    r = measure_precision(args.steps, args.warmup)
+    ex = r["forms"]["f32cost_f64dp"]
     line = {"metric": METRIC, "value": ex["gcups"], "unit": "GCUPS", "n_gpus": 1,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ex["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-cost/f64-dp",
             "data": "synthetic",
-            "config": {"workload": "orchestral-length pair: 60000 x 64-d MFCC-like vs 75000-frame warp + "
-                                   "N(0,0.1^2); value is the FP32-cost/FP64-DP form", "M": M, "N": N,
-                       "oracle_cost": c_ref, "oracle_source": "tests/golden/mfcc_pair_60000x75000.txt"},
-            "forms": forms, "path_discrepancy": disc}
+            "config": {"workload": r["workload"] + "; value is the FP32-cost/FP64-DP form", "M": r["M"], "N": r["N"],
+                       "oracle_cost": r["oracle_cost"], "oracle_source": r["oracle_source"]},
+            "forms": r["forms"], "path_discrepancy": r["path_discrepancy"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -655,35 +761,27 @@ def run_local_workload(args):
     return 0
 
 
-def run_serving_workload(args):
-    """The serving stream: Poisson arrivals, lengths log-uniform in [500, max_len],
-    d = 12 (FP32 frames) or 64 with equal probability, submitted at their arrival
-    times through dtw_submit and collected with dtw_poll.  Reports throughput over
-    the makespan and per-request latency (submit to result), beside the serial
-    plain FP64 GPU form's throughput measured on one pair of the stream."""
-    import torch
+def _plain_model(samples):
+    """Least-squares fit t = a L + b M N of the plain form's time per request,
+    L = (M + N) max(1, log2(M N / 250000)): one launch per anti-diagonal of every
+    box of the host recursion, plus the cells.  samples: (M, N, seconds)."""
+    A = np.array([[(m + n) * max(1.0, math.log2(m * n / 2.5e5)), m * n] for m, n, _ in samples], dtype=np.float64)
+    t = np.array([x[2] for x in samples], dtype=np.float64)
+    coef, *_ = np.linalg.lstsq(A, t, rcond=None)
+    return np.maximum(coef, 0.0)
 
-    import paper_2008_02734_b300 as dtw
 
-    dtw.set_budget(int(args.budget_gb * (1 << 30)))
-    reqs = synth.workload_serving(R=args.requests, rate_hz=args.rate, hi=args.max_len)
-    feats = [r.features() for r in reqs]
-    cells = float(sum(r.M * r.N for r in reqs))
-    bufs = [(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()) for x, y in feats]
-    torch.cuda.synchronize()
-    # d = 64 requests use the BF16 tensor-core cost tiles with the compensated FP32 DP
-    bf16 = [r.d == 64 and not args.exact for r in reqs]
-    # warm the engines of both groups
-    for k in range(min(4, len(reqs))):
-        t, _, keep = dtw.submit(*bufs[k], cost_bf16=bf16[k])
-        dtw.wait(t)
+def _run_stream(dtw, bufs, reqs, arrivals, bf16):
+    """Submits request k at arrivals[k] seconds (all at once if arrivals is
+    None), polls every request to completion; returns (makespan s, latencies ms)."""
     pend = {}
     lat = []
     t0 = time.perf_counter()
     nxt = 0
-    while nxt < len(reqs) or pend:
+    R = len(reqs)
+    while nxt < R or pend:
         now = time.perf_counter() - t0
-        while nxt < len(reqs) and reqs[nxt].arrival_s <= now:
+        while nxt < R and (arrivals is None or arrivals[nxt] <= now):
             t, path, keep = dtw.submit(*bufs[nxt], cost_bf16=bf16[nxt])
             pend[t] = (time.perf_counter(), path, keep, nxt)
             nxt += 1
@@ -694,25 +792,102 @@ def run_serving_workload(args):
                     raise RuntimeError(f"request {pend[t][3]} failed: {rc}")
                 lat.append(1e3 * (time.perf_counter() - pend[t][0]))
                 del pend[t]
-        time.sleep(1e-4)
-    makespan = time.perf_counter() - t0
-    # the serial plain form on a mid-size request of the stream
-    k = int(np.argsort([r.M * r.N for r in reqs])[len(reqs) // 2])
+        time.sleep(5e-5)
+    return time.perf_counter() - t0, lat
+
+
+def measure_serving(requests: int, max_len: int, budget_gb: float, rho: float = 0.7, exact: bool = False,
+                    plain_samples: int = 8, plain_budget_s: float = 8.0):
+    """The serving stream (Poisson arrivals, lengths log-uniform in [500, max_len],
+    d = 12 FP32-cost/FP64-DP or d = 64 BF16-cost/compensated-FP32-DP requests with
+    equal probability) through dtw_submit / dtw_poll.
+
+    1. Capacity: every request submitted at once; capacity = requests / makespan.
+    2. The stream at offered load rho of that capacity (the seeded arrival
+       process rescaled to rate rho x capacity): GCUPS over the makespan and the
+       p50 / p99 latency from submission to result.
+    3. The serial plain FP64 GPU form: timed on a seeded sample of the stream's
+       requests per feature dimension (the smaller ones, within a time budget),
+       fitted per dimension by t = a L + b M N, and run as a single FIFO server on
+       the same arrival times (its makespan and p50 / p99 latency)."""
+    import torch
+
+    import paper_2008_02734_b300 as dtw
+
+    dtw.set_budget(int(budget_gb * (1 << 30)))
+    reqs = synth.workload_serving(R=requests, rate_hz=1.0, hi=max_len)
+    feats = [r.features() for r in reqs]
+    cells = float(sum(r.M * r.N for r in reqs))
+    bufs = [(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()) for x, y in feats]
     torch.cuda.synchronize()
-    tp = time.perf_counter()
-    dtw.align(*bufs[k], plain=True)
-    torch.cuda.synchronize()
-    plain_gcups = reqs[k].M * reqs[k].N / (time.perf_counter() - tp) / 1e9
-    line = {"metric": METRIC, "value": cells / makespan / 1e9, "unit": "GCUPS", "n_gpus": 1,
+    bf16 = [r.d == 64 and not exact for r in reqs]
+    # warm the engines of both groups
+    for k in range(min(8, len(reqs))):
+        dtw.wait(dtw.submit(*bufs[k], cost_bf16=bf16[k])[0])
+    sat_s, sat_lat = _run_stream(dtw, bufs, reqs, None, bf16)
+    capacity = len(reqs) / sat_s
+    base = np.array([r.arrival_s for r in reqs])  # the arrival process at 1 request per second
+    rate = rho * capacity
+    arrivals = base / rate
+    mk, lat = _run_stream(dtw, bufs, reqs, arrivals, bf16)
+    # the serial plain form: a seeded sample per dimension, smallest requests first
+    rng = np.random.default_rng(17)
+    samples = {12: [], 64: []}
+    cap_cells = {12: 5e7, 64: 2e7}  # larger requests would take seconds each in the plain form
+    for dim in (12, 64):
+        idx = [k for k in range(len(reqs)) if reqs[k].d == dim and reqs[k].M * reqs[k].N <= cap_cells[dim]]
+        idx = sorted(rng.choice(idx, size=min(4 * plain_samples, len(idx)), replace=False),
+                     key=lambda k: reqs[k].M * reqs[k].N)
+        spent = 0.0
+        for k in idx[:: max(1, len(idx) // plain_samples)]:
+            if spent > plain_budget_s / 2:
+                break
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            dtw.align(*bufs[k], plain=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            spent += dt
+            samples[dim].append((reqs[k].M, reqs[k].N, dt))
+    coef = {dim: _plain_model(v) for dim, v in samples.items() if len(v) >= 2}
+
+    def t_plain(r):
+        a, b = coef[r.d]
+        return a * (r.M + r.N) * max(1.0, math.log2(r.M * r.N / 2.5e5)) + b * r.M * r.N
+
+    end = 0.0
+    plat = []
+    for r, at in zip(reqs, arrivals):
+        end = max(end, at) + t_plain(r)
+        plat.append(1e3 * (end - at))
+    plain_mk = end - arrivals[0]
+    return {
+        "workload": f"serving stream: {len(reqs)} Poisson arrivals, lengths log-uniform [500,{max_len}], "
+                    "d 12 (FP32 cost, FP64 DP) or 64 (" + ("exact form" if exact else
+                    "BF16 tensor-core cost, compensated FP32 DP") + f"), admission budget {budget_gb} GB",
+        "requests": len(reqs), "problem_cells": cells,
+        "capacity": {"requests_per_s": capacity, "makespan_s": sat_s, "gcups": cells / sat_s / 1e9,
+                     "how": "every request submitted at once"},
+        "offered_load": rho, "arrival_rate_hz": rate,
+        "gcups": cells / mk / 1e9, "makespan_s": mk, "latency_ms": _percentiles(lat),
+        "vs_plain_gpu": {"plain_makespan_s": plain_mk, "plain_latency_ms": _percentiles(plat),
+                         "makespan_speedup": plain_mk / mk,
+                         "p99_ratio": float(np.percentile(plat, 99) / np.percentile(lat, 99)),
+                         "how": "the plain form timed on a seeded sample per dimension, fitted by t = a (M+N) "
+                                "max(1, log2(MN/250000)) + b MN, run as one FIFO server on the same arrivals",
+                         "samples": {str(k): [[m, n, round(t, 4)] for m, n, t in v] for k, v in samples.items()}},
+    }
+
+
+def run_serving_workload(args):
+    """The serving stream at offered load --rho of the capacity measured in the
+    same run; value is its GCUPS."""
+    r = measure_serving(args.requests, args.max_len, args.budget_gb, args.rho, args.exact)
+    line = {"metric": METRIC, "value": r["gcups"], "unit": "GCUPS", "n_gpus": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
-            "config": {"workload": f"serving stream: {args.requests} Poisson arrivals at {args.rate} Hz, lengths "
-                                   f"log-uniform [500,{args.max_len}], d 12 (FP32 cost, FP64 DP) or 64 ("
-                                   + ("exact form" if args.exact else "BF16 tensor-core cost, compensated FP32 DP")
-                                   + f"), admission budget {args.budget_gb} GB", "problem_cells": cells},
-            "latency_ms": _percentiles(lat), "makespan_s": makespan,
-            "vs_plain_gpu": {"plain_gcups_one_request": plain_gcups,
-                             "serial_plain_makespan_s_est": cells / plain_gcups / 1e9,
-                             "speedup_est": (cells / makespan) / (plain_gcups * 1e9)}}
+            "config": {"workload": r["workload"], "problem_cells": r["problem_cells"], "offered_load": r["offered_load"]},
+            "latency_ms": r["latency_ms"], "makespan_s": r["makespan_s"], "capacity": r["capacity"],
+            "arrival_rate_hz": r["arrival_rate_hz"], "vs_plain_gpu": r["vs_plain_gpu"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -748,12 +923,14 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "precision", "serving", "edit", "local"],
                     default="int_pair")
     ap.add_argument("--batch", type=int, default=256, help="pairs of the batch workload")
-    ap.add_argument("--requests", type=int, default=200, help="requests of the serving workload")
-    ap.add_argument("--rate", type=float, default=100.0, help="arrival rate of the serving workload (Hz)")
+    ap.add_argument("--requests", type=int, default=2000, help="requests of the serving workload")
+    ap.add_argument("--rho", type=float, default=0.7, help="serving workload: offered load (share of capacity)")
     ap.add_argument("--max-len", type=int, default=20000, help="longest request of the serving workload")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="admission budget of the serving workload")
     ap.add_argument("--exact", action="store_true", help="serving workload: exact form for d = 64 too")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 GPU comparator")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default run: skip the batch, precision and serving configurations")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default lane block and cutoff)")

@@ -1,8 +1,14 @@
 // Request engine behind dtw_submit / dtw_poll: continuous batching of
 // alignments (the serving pattern built on Algorithm 2's level structure).
 //
-// A worker thread owns, per (cost kind, dimension) group, one fixed device arena
-// sized from the admission budget.  Each iteration of a group:
+// Each (cost kind, dimension) group has its own engine: a worker thread, a
+// CUDA stream and one fixed device arena.  The groups' threads run at the same
+// time, so levels of different groups (say d=12 and d=64 requests) overlap on
+// the device.  With an admission budget (dtw_set_budget) the arenas share it in
+// proportion to the footprint of the requests each group has received (at least
+// a quarter each); an idle engine whose share has drifted by more than a
+// quarter gives its arena back and takes the new share at its next request.
+// Each iteration of a group:
 //   1. admits queued requests while a pair slot, their rows of the per-row path
 //      arrays, their staging bytes and their share of the level scratch (linear
 //      in M+N, Section 4.3's memory argument) are free -- requests that arrive
@@ -98,6 +104,7 @@ struct Result {
 
 constexpr int kSlots = 4096;                 // pairs in flight per group
 constexpr size_t kDefaultArena = 2ull << 30;  // bytes per group when no budget is set
+constexpr size_t kMinArena = 96ull << 20;     // the smallest arena an engine starts with
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -127,6 +134,8 @@ struct Engine {
     int kind = 0, d = 1;
     cudaStream_t st = nullptr;
     char* ws = nullptr;
+    size_t arena = 0;  // bytes taken from the budget (0: none)
+    bool running = false;  // under the server's mutex: the engine's thread is iterating
     Layout L{};
     long long S_max = 0, S_active = 0, stage_cap = 0;
     RangeAlloc rows, bytes;
@@ -159,7 +168,7 @@ struct Engine {
             ws = nullptr;
             return DTW_ENOMEM;
         }
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return DTW_ECUDA;
+        if (!st && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return DTW_ECUDA;
         char* x = ws + L.total;
         d_roots = reinterpret_cast<Box*>(x);
         x += up256(sizeof(Box) * kSlots);
@@ -182,6 +191,15 @@ struct Engine {
         cur = reinterpret_cast<Box*>(ws + L.boxA);
         nxt = reinterpret_cast<Box*>(ws + L.boxB);
         return DTW_OK;
+    }
+
+    // Gives the arena back (the engine must be idle); the next request re-creates it.
+    void free_arena() {
+        if (!ws) return;
+        cudaStreamSynchronize(st);
+        cudaFree(ws);
+        ws = nullptr;
+        n_cur = 0;
     }
 
     bool idle() const { return active.empty() && queue.empty(); }
@@ -209,15 +227,17 @@ struct Server {
     std::mutex mu;
     std::condition_variable cv;
     std::map<std::pair<int, int>, std::unique_ptr<Engine>> engines;
+    std::map<Engine*, double> demand;  // footprint of the requests each group has received
     std::unordered_map<long long, Result> done;
     std::unordered_set<long long> inflight;
     long long next_ticket = 0;
-    bool running = false;
     int device = 0;
     uint64_t budget = 0;
+    size_t allocated = 0;  // arena bytes taken from the budget by all engines
     size_t max_queue = 1 << 20;
 
-    void worker();
+    size_t target_arena(Engine* en);  // under mu
+    void engine_loop(Engine* en);
 };
 
 Server& server() {
@@ -427,61 +447,104 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
     return DTW_OK;
 }
 
-void Server::worker() {
+// The engine's share of the budget: its groups' part of the footprint received
+// so far, at least a quarter (a second group always finds room).
+size_t Server::target_arena(Engine* en) {
+    if (!budget) return kDefaultArena;
+    double tot = 0;
+    for (auto& kv : demand) tot += kv.second;
+    double share = tot > 0 ? demand[en] / tot : 1.0;
+    if (engines.size() > 1) share = std::min(std::max(share, 0.25), 0.75);
+    return (size_t)(share * (double)budget);
+}
+
+void Server::engine_loop(Engine* en) {
     cudaSetDevice(device);
     for (;;) {
-        std::vector<Engine*> busy;
+        size_t arena = 0;
         {
             std::unique_lock<std::mutex> g(mu);
-            cv.wait(g, [&] {
-                for (auto& kv : engines)
-                    if (!kv.second->idle()) return true;
-                return false;
-            });
-            for (auto& kv : engines)
-                if (!kv.second->idle()) busy.push_back(kv.second.get());
-        }
-        for (Engine* en : busy) {
+            cv.wait(g, [&] { return !en->idle(); });
+            en->running = true;
             if (!en->ws) {
-                int sms = 0;
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-                const size_t arena = budget ? (size_t)(budget / 2) : kDefaultArena;
-                int rc = en->init(arena, sms);
-                if (rc != DTW_OK) {
-                    std::lock_guard<std::mutex> g(mu);
-                    for (const Pending& p : en->queue) {
-                        done[p.ticket] = Result{rc, 0, 0.0};
-                        inflight.erase(p.ticket);
+                // take the engine's share of what the budget has left; wait while
+                // another engine still holds more than its share
+                for (;;) {
+                    const size_t want = target_arena(en);
+                    size_t left = budget ? (budget > allocated ? budget - allocated : 0) : want;
+                    if (budget && left < want) {
+                        // idle engines holding more than their share give it back
+                        // (their threads wait for work and re-check their arena)
+                        for (auto& kv : engines) {
+                            Engine* o = kv.second.get();
+                            if (o != en && !o->running && o->ws && o->idle() && o->arena > target_arena(o)) {
+                                o->free_arena();
+                                allocated -= o->arena;
+                                o->arena = 0;
+                            }
+                        }
+                        left = budget > allocated ? budget - allocated : 0;
                     }
-                    en->queue.clear();
-                    continue;
+                    arena = std::min(want, left);
+                    if (!budget || arena >= std::min<size_t>(want, kMinArena)) break;
+                    cv.wait_for(g, std::chrono::milliseconds(1));
                 }
+                if (budget) allocated += arena;
             }
-            std::vector<std::pair<long long, Result>> out;
-            const int rc = en->iterate(mu, out);
-            if (rc != DTW_OK) {
-                // a device-side error or a failed CUDA call poisons the group's
-                // in-flight state: fail its active pairs and start it afresh
-                for (auto& kv : en->active) out.push_back({kv.second.ticket, Result{rc, 0, 0.0}});
-                std::vector<int> slots;
-                for (auto& kv : en->active) slots.push_back(kv.first);
-                for (int s : slots) en->release(s);
-                en->n_cur = 0;
-                cudaGetLastError();
-                LevelCtl c0{};
-                LevelCtl old{};
-                cudaMemcpyAsync(&old, en->ctl(), sizeof(old), cudaMemcpyDeviceToHost, en->st);
-                cudaStreamSynchronize(en->st);
-                c0.epoch_base = old.epoch_base + 1;
-                cudaMemcpyAsync(en->ctl(), &c0, sizeof(c0), cudaMemcpyHostToDevice, en->st);
-                cudaStreamSynchronize(en->st);
-            }
-            if (!out.empty()) {
+        }
+        if (!en->ws) {
+            int sms = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+            int rc = en->init(arena, sms);
+            if (rc == DTW_OK) {
+                en->arena = arena;
+            } else {
+                if (en->ws) cudaFree(en->ws);
+                en->ws = nullptr;
                 std::lock_guard<std::mutex> g(mu);
-                for (auto& r : out) {
-                    done[r.first] = r.second;
-                    inflight.erase(r.first);
+                if (budget) allocated -= arena;
+                for (const Pending& p : en->queue) {
+                    done[p.ticket] = Result{rc, 0, 0.0};
+                    inflight.erase(p.ticket);
                 }
+                en->queue.clear();
+                en->running = false;
+                continue;
+            }
+        }
+        std::vector<std::pair<long long, Result>> out;
+        const int rc = en->iterate(mu, out);
+        if (rc != DTW_OK) {
+            // a device-side error or a failed CUDA call poisons the group's
+            // in-flight state: fail its active pairs and start it afresh
+            for (auto& kv : en->active) out.push_back({kv.second.ticket, Result{rc, 0, 0.0}});
+            std::vector<int> slots;
+            for (auto& kv : en->active) slots.push_back(kv.first);
+            for (int sl : slots) en->release(sl);
+            en->n_cur = 0;
+            cudaGetLastError();
+            LevelCtl c0{};
+            LevelCtl old{};
+            cudaMemcpyAsync(&old, en->ctl(), sizeof(old), cudaMemcpyDeviceToHost, en->st);
+            cudaStreamSynchronize(en->st);
+            c0.epoch_base = old.epoch_base + 1;
+            cudaMemcpyAsync(en->ctl(), &c0, sizeof(c0), cudaMemcpyHostToDevice, en->st);
+            cudaStreamSynchronize(en->st);
+        }
+        std::lock_guard<std::mutex> g(mu);
+        for (auto& r : out) {
+            done[r.first] = r.second;
+            inflight.erase(r.first);
+        }
+        en->running = false;
+        if (budget && en->ws && en->idle()) {
+            // an idle engine whose share has drifted gives its arena back
+            const double want = (double)target_arena(en), have = (double)en->arena;
+            if (want > 1.25 * have || want < 0.75 * have) {
+                en->free_arena();
+                allocated -= en->arena;
+                en->arena = 0;
+                cv.notify_all();
             }
         }
     }
@@ -510,18 +573,18 @@ int64_t dtw_submit(const dtw_request* r) {
     Server& s = server();
     std::lock_guard<std::mutex> g(s.mu);
     if (s.inflight.size() >= s.max_queue) return DTW_EBUSY;
-    if (!s.running) {
-        if (cudaGetDevice(&s.device) != cudaSuccess) return DTW_ECUDA;
-        s.running = true;
-        std::thread(&Server::worker, &s).detach();
-    }
+    if (s.engines.empty() && cudaGetDevice(&s.device) != cudaSuccess) return DTW_ECUDA;
     auto key = std::make_pair(kind, kind == KIND_ABS ? 1 : (int)r->d);
     auto& en = s.engines[key];
     if (!en) {
         en.reset(new Engine());
         en->kind = kind;
         en->d = key.second;
+        s.demand[en.get()] = 0.0;
+        std::thread(&Server::engine_loop, &s, en.get()).detach();
     }
+    // the group's demand: level scratch and features, linear in M + N
+    s.demand[en.get()] += (double)(r->M + r->N) * (1800.0 + 4.0 * (double)r->d);
     const long long t = s.next_ticket++;
     en->queue.push_back(Pending{t, *r});
     s.inflight.insert(t);

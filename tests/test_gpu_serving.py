@@ -99,19 +99,67 @@ def test_mixed_stream_matches_alone():
 
 
 def test_late_request_admitted_while_long_one_runs():
-    Xb, Yb = synth.workload_int_pair()
+    """A short request submitted right after a long one of the same group joins
+    its levels instead of queueing behind it: it finishes while the long one
+    (a 50000 x 60000 integer pair, some ten levels) is still in flight.  Both
+    results: the short one equals the oracle's bit for bit, the long one equals
+    the pair aligned alone (the full-size oracle would take too long here)."""
+    import time
+    Xb, Yb = synth.int_pair(1, 50000, 60000)
     Xs, Ys = synth.int_pair(77, 600, 700)
-    tb, pb, kb = dtw.submit(_cuda(Xb), _cuda(Yb))
-    ts, ps, ks = dtw.submit(_cuda(Xs), _cuda(Ys))
-    rc, K, c = dtw.wait(ts)
+    Xbd, Ybd, Xsd, Ysd = _cuda(Xb), _cuda(Yb), _cuda(Xs), _cuda(Ys)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tb, pb, kb = dtw.submit(Xbd, Ybd)
+    ts, ps, ks = dtw.submit(Xsd, Ysd)
+    rc, K, c = dtw.wait(ts, interval_s=2e-5)
+    t_short = time.perf_counter() - t0
     assert rc == dtw.OK
     # the short request finished while the long one was still being aligned
-    assert dtw.poll(tb)[0] == dtw.PENDING
+    st_long = dtw.poll(tb)[0]
+    rcb, Kb, cb = dtw.wait(tb, interval_s=2e-5)
+    t_long = time.perf_counter() - t0
+    print(f"short request {1e3 * t_short:.2f} ms, long request {1e3 * t_long:.2f} ms")
+    assert st_long == dtw.PENDING
     p_ref, c_ref = oracle.dtw(Xs, Ys)
     assert c == c_ref and np.array_equal(ps[:K].cpu().numpy(), p_ref)
-    rc, K, c = dtw.wait(tb)
+    assert rcb == dtw.OK
+    p_alone, c_alone = _alone(Xb, Yb)
+    assert cb == c_alone and np.array_equal(pb[:Kb].cpu().numpy(), p_alone)
+
+
+def test_groups_overlap_short_d64_during_long_d12():
+    """The d=12 and d=64 groups have their own engines (threads and streams):
+    a short d=64 request submitted right after a long d=12 one is not served
+    level by level in turn with it.  It finishes while the long one is still in
+    flight, within half the long one's latency (alternating the groups' levels,
+    it would wait for a level of the long pair before each of its own), and both
+    results equal the pairs aligned alone."""
+    import time
+    Xl, Yl = synth.chroma_pair(501, 20000, 24000)
+    Xs, Ys = synth.mfcc_pair(502, 700, 800)
+    dl, ds = (_cuda(Xl), _cuda(Yl)), (_cuda(Xs), _cuda(Ys))
+    # warm both engines up (arena creation is not part of the measurement)
+    for X, Y in (dl, ds):
+        assert dtw.wait(dtw.submit(X, Y)[0])[0] == dtw.OK
+    t0 = time.perf_counter()
+    tl, pl, kl = dtw.submit(*dl)
+    ts, ps, ks = dtw.submit(*ds)
+    rc, Ks, cs = dtw.wait(ts, interval_s=2e-5)
+    t_short = time.perf_counter() - t0
     assert rc == dtw.OK
-    assert c == oracle.dtw(Xb, Yb)[1]
+    long_pending = dtw.poll(tl)[0] == dtw.PENDING
+    rc, Kl, cl = dtw.wait(tl, interval_s=2e-5)
+    t_long = time.perf_counter() - t0
+    assert rc == dtw.OK
+    print(f"short d=64 request {1e3 * t_short:.2f} ms, long d=12 request {1e3 * t_long:.2f} ms")
+    assert long_pending
+    assert t_short < 0.5 * t_long
+    ref_s = _alone(Xs, Ys)
+    assert cs == pytest.approx(ref_s[1], rel=REL_TOL)
+    assert oracle.path_cost(Xs, Ys, ps[:Ks].cpu().numpy()) == pytest.approx(ref_s[1], rel=REL_TOL)
+    ref_l = _alone(Xl, Yl)
+    assert cl == pytest.approx(ref_l[1], rel=REL_TOL)
 
 
 def test_overflowing_request_fails_alone():
