@@ -21,9 +21,12 @@
 //   4. finishes the pairs that own no box any more: path assembly, results
 //      copied out, resources returned.
 // Different requests are therefore at different recursion levels inside the
-// same launches.  Each box is computed exactly as in dtw_align, so a result does
+// same launches.  With DTW_SERVE_TRACE set in the environment each engine logs
+// its iterations (admissions, level ends, finished tickets) to stderr.  Each box is computed exactly as in dtw_align, so a result does
 // not depend on which other requests share its launches.
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -245,8 +248,14 @@ Server& server() {
     return *s;
 }
 
+static bool g_trace = getenv("DTW_SERVE_TRACE") != nullptr;
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& out) {
     const size_t esize = 4;
+    if (g_trace) fprintf(stderr, "[serve] %.3f kind %d d %d iterate: active %zu queue %zu n_cur %d\n", now_ms(), kind, d, active.size(), queue.size(), n_cur);
     // ---- 1. admission
     std::vector<Box> roots;
     std::vector<int> admitted;
@@ -410,6 +419,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
     n_cur = hc.n_cur;
     if (hc.err != ERR_NONE) return status_of(hc.err);
 
+    if (g_trace) fprintf(stderr, "[serve] %.3f kind %d level done: n_cur %d n_base %d\n", now_ms(), kind, hc.n_cur, hc.n_base);
     // ---- 3. pairs that own no box any more are complete
     std::vector<int> fin;
     int max_M = 1;
@@ -440,6 +450,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
     if (e != cudaSuccess) return DTW_ECUDA;
     for (size_t k = 0; k < fin.size(); ++k) {
         const Active& a = active[fin[k]];
+        if (g_trace) fprintf(stderr, "[serve] %.3f kind %d finished ticket %lld\n", now_ms(), kind, a.ticket);
         const double cost = kind == KIND_ABS ? (double)pr[k].cost_i : pr[k].cost_f;
         out.push_back({a.ticket, Result{DTW_OK, pr[k].K, cost}});
         release(fin[k]);

@@ -80,7 +80,10 @@ namespace {
 template <int KIND>
 __host__ __device__ constexpr int group_of() { return int_kind(KIND) ? DTW_SWEEP_G_INT : DTW_SWEEP_G_EUC; }
 template <int KIND>
-__host__ __device__ constexpr int threads_of() { return 32 * (group_of<KIND>() + 1); }  // + the loader warp
+__host__ __device__ constexpr int threads_of() {
+    // + the loader warp; the BF16 tensor-core form adds its tile warp
+    return 32 * (group_of<KIND>() + 1 + (KIND == KIND_EUCB ? 1 : 0));
+}
 constexpr int kGMax = 8;  // the frame ring partition covers up to 8 warps
 constexpr int URS = 64;                  // slots (column blocks) of a row ring
 #ifndef DTW_SWEEP_KC
@@ -288,29 +291,121 @@ struct FrameWords {
     static constexpr int v = int_kind(KIND) ? 1 : (KIND == KIND_EUCB ? 0 : DIM);
 };
 
-// Per-warp shared memory of the BF16 tensor-core form: the band's 32 row frames
-// and a tile's 32 column frames as BF16 (rows padded to 36 words: conflict-free
-// fragment loads), their FP32 squared norms, and a ring of three 32 x 32 cost
-// tiles (rows padded to 33 floats: conflict-free reads along the skewed lanes).
-struct TcWarp {
-    uint32_t xb[32][36];
-    uint32_t yb[32][36];
-    float xx[32], yy[32];
-    float tile[3][32][33];
+// ---- BF16 tensor-core cost tiles (tcgen05, TMEM accumulators)
+//
+// A block of the BF16 form holds four bands of 32 rows of one sweep: 128 frame
+// rows, the M = 128 of one tcgen05.mma.  The band warps write their rows' frames
+// (BF16) into operand A once per ticket.  The bands run about 40 steps apart
+// (the band below waits for the lanes of the band above), so each band has its
+// own stream of 32-column tiles: for band g's tile t, a tile warp converts the
+// 32 column frames into the band's operand B, takes their FP32 squared norms,
+// and one of its threads issues four MMAs (K = 16 each, d = 64) into the band's
+// TMEM slot and commits them to the slot's mbarrier.  TMEM lane i holds frame
+// row i of the block, so band warp g (warp g % 4 reads lanes 32g..32g+31) loads
+// its own rows' dot products with one tcgen05.ld (the other lanes of its slot go
+// unused), forms the expanded cost and writes its ring of three 32 x 32 cost
+// tiles in shared memory, which its skewed lanes read.  Each band has two slots
+// (TMEM columns, operand B and norms): the tile warp fills one while the band
+// works from the other.
+constexpr int kTcBands = 4;
+constexpr int kTcSlots = 2;                // per band
+constexpr int kTcRows = 128;               // M: four bands of 32 frame rows
+constexpr int kTcCols = 32;                // N: column frames per tile
+constexpr int kTcK = 64;                   // K: the feature dimension
+constexpr uint32_t kTcTmemCols = kTcBands * kTcSlots * kTcCols;  // 256 (a power of two >= 32)
+// Operands in the no-swizzle K-major layout: 8-row x 16-byte core matrices;
+// element (r, k) at (k / 8) * LBO + (r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2.
+constexpr uint32_t kTcSBO = 128;                      // next 8 rows
+constexpr uint32_t kTcLboA = (kTcRows / 8) * 128;     // next 8 k of A (2048 B)
+constexpr uint32_t kTcLboB = (kTcCols / 8) * 128;     // next 8 k of B (512 B)
+constexpr int kTcBytesA = kTcRows * kTcK * 2;
+constexpr int kTcBytesB = kTcCols * kTcK * 2;
+
+struct TcShared {
+    __align__(128) unsigned char a[kTcBytesA];
+    __align__(128) unsigned char b[kTcBands][kTcSlots][kTcBytesB];
+    float yy[kTcBands][kTcSlots][kTcCols];        // squared norms of the tile's column frames
+    float tile[kTcBands][3][32][33];               // per band: three cost tiles (rows padded: conflict-free skewed reads)
+    unsigned long long mbar[kTcBands][kTcSlots];   // MMA completion per slot
+    int produced[kTcBands];                        // per band: tiles whose MMAs are issued (running count)
+    int consumed[kTcBands];                        // per band: tiles loaded from TMEM (running count)
+    int tbase[kTcBands];                           // per band: running count at this ticket's start
+    int a_ready[kTcBands];                         // ticket + 1 once the band warp's rows of operand A are written
+    uint32_t tmem;                                 // TMEM base address of the block's slots
 };
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     const __nv_bfloat162 t = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&t);
 }
+__device__ __forceinline__ uint32_t tc_off(int r, int k, uint32_t lbo) {
+    return (uint32_t)(k >> 3) * lbo + (uint32_t)(r >> 3) * kTcSBO + (uint32_t)(r & 7) * 16 + (uint32_t)(k & 7) * 2;
+}
+// Writes the 64 features of frame row r of an operand (BF16, 16 bytes at a time).
+__device__ __forceinline__ void tc_store_row(unsigned char* base, int r, uint32_t lbo, const float* v) {
+#pragma unroll
+    for (int k8 = 0; k8 < kTcK / 8; ++k8) {
+        const uint4 q = make_uint4(pack_bf16x2(v[8 * k8], v[8 * k8 + 1]), pack_bf16x2(v[8 * k8 + 2], v[8 * k8 + 3]),
+                                   pack_bf16x2(v[8 * k8 + 4], v[8 * k8 + 5]), pack_bf16x2(v[8 * k8 + 6], v[8 * k8 + 7]));
+        *reinterpret_cast<uint4*>(base + tc_off(r, 8 * k8, lbo)) = q;
+    }
+}
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+// Instruction descriptor of kind::f16: FP32 accumulators, BF16 A and B, both
+// K-major, N = 32, M = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcCols >> 3) << 17) |
+                              ((uint32_t)(kTcRows >> 4) << 24);
 
-// D += A(16x16, row) B(16x8, col), BF16 inputs, FP32 accumulators.
-__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(unsigned long long* m) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(m)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* m, uint32_t parity) {
+    uint32_t done;
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(m)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// D[tmem] (+)= A(desc) B(desc)^T, one thread.
+__device__ __forceinline__ void tc_mma(uint32_t dt, uint64_t ad, uint64_t bd, bool acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(kTcIdesc), "r"((int)acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned long long* m) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(m))
+                 : "memory");
+}
+// 32 consecutive TMEM columns of the warp's 32 lanes: lane l gets row l's values.
+__device__ __forceinline__ void tc_ld32(uint32_t ta, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // Shared memory of a block.  Row ring g carries the last row of the band above
@@ -361,6 +456,7 @@ struct StripSmem {
     int sweep_of[G], band_of[G], ystream[G];
     long long ticket;
     int stop;
+    int ntiles;  // BF16 tensor-core form: tiles of this ticket's sweep
 };
 
 // Column frame held by a lane: in registers, or (large fixed dimensions) a
@@ -395,7 +491,7 @@ struct ColFrame<KIND_EUCF, 64> {
 template <int KIND, int R, int U, int DIM, int NWMAX, int NW, int TAGM, bool VF, bool SPECIAL, bool FULL>
 __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_idx, int band, bool to_ring,
                                       bool to_global, const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>& sm,
-                                      int g, TcWarp* tc) {
+                                      int g, TcShared* tc) {
     using Acc = typename AccOf<KIND>::T;
     using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>;
     constexpr int YW = FrameWords<KIND, DIM>::v;
@@ -463,81 +559,50 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     }
 
     // ---- tensor-core cost tiles (BF16 form)
-    // A fragments of the band's rows (m16 x k16 tiles, 2 x 4 of them) stay in
-    // registers for the whole band; each tile of 16 column blocks (32 columns)
-    // is built by the whole warp when lane 0 reaches it: the column frames,
-    // loaded one tile ahead from global memory, become BF16 B fragments, 32
-    // MMAs give the dot products and the expanded form gives the costs.
-    uint32_t afr[TC ? 2 : 1][TC ? 4 : 1][4];
-    float yv[TC ? 64 : 1];
-    const float* colf = static_cast<const float*>(sp->colseq);
-    const long long cbase0 = sp->cbase;
-    const int cstep0 = sp->cstep;
-    auto load_ycol = [&](int t) {  // lane c: column frame 32t + c (clamped)
-        if constexpr (TC) {
-            const int q = min(32 * t + lane, Q - 1);
-            const float4* src = reinterpret_cast<const float4*>(colf + (cbase0 + (long long)cstep0 * q) * 64);
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const float4 v = __ldg(src + e);
-                yv[4 * e] = v.x;
-                yv[4 * e + 1] = v.y;
-                yv[4 * e + 2] = v.z;
-                yv[4 * e + 3] = v.w;
-            }
-        }
-    };
+    // The lane's row frame goes into operand A (row 32g + lane) and its FP32
+    // squared norm stays in a register.  Tile t (columns 32t .. 32t+31) is needed
+    // when lane 0 reaches it; the band warp then waits for the tile warp's MMA of
+    // it, loads its 32 lanes' dot products from TMEM and writes the costs of the
+    // expanded form into its ring of three tiles (lane l reads only row l).
+    float xxr = 0.f;
     if constexpr (TC) {
         Frame<KIND_EUC, 64> xf;
         xf.load(rowseq, (long long)rbase + (long long)rstep * min(p0, rows - 1), 64);
-        tc->xx[lane] = sqnorm<64>(xf.v);
-#pragma unroll
-        for (int e = 0; e < 32; ++e) tc->xb[lane][e] = pack_bf16x2(xf.v[2 * e], xf.v[2 * e + 1]);
+        xxr = sqnorm<64>(xf.v);
+        tc_store_row(tc->a, 32 * g + lane, kTcLboA, xf.v);
+        fence_proxy_async();  // the MMAs read operand A through the async proxy
         __syncwarp();
-        const int gr = lane >> 2, qd = lane & 3;
-#pragma unroll
-        for (int m = 0; m < 2; ++m)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                afr[m][k][0] = tc->xb[m * 16 + gr][k * 8 + qd];
-                afr[m][k][1] = tc->xb[m * 16 + gr + 8][k * 8 + qd];
-                afr[m][k][2] = tc->xb[m * 16 + gr][k * 8 + 4 + qd];
-                afr[m][k][3] = tc->xb[m * 16 + gr + 8][k * 8 + 4 + qd];
-            }
-        load_ycol(0);
+        if (lane == 0) st_release_cta(&tc->a_ready[g], (int)sm.ticket + 1);
     }
     auto build_tile = [&](int t) {
         if constexpr (TC) {
-            tc->yy[lane] = sqnorm<64>(yv);
-#pragma unroll
-            for (int e = 0; e < 32; ++e) tc->yb[lane][e] = pack_bf16x2(yv[2 * e], yv[2 * e + 1]);
-            load_ycol(t + 1);  // the next tile's frames, consumed at its build
-            __syncwarp();
-            const int gr = lane >> 2, qd = lane & 3;
-            float (*tile)[33] = tc->tile[t % 3];
-#pragma unroll
-            for (int n = 0; n < 4; ++n) {
-                float acc[2][4] = {};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t b0 = tc->yb[n * 8 + gr][k * 8 + qd];
-                    const uint32_t b1 = tc->yb[n * 8 + gr][k * 8 + 4 + qd];
-                    mma_bf16(acc[0], afr[0][k], b0, b1);
-                    mma_bf16(acc[1], afr[1][k], b0, b1);
+            const int gt = tc->tbase[g] + t;  // the band's running tile count
+            const int slot = gt % kTcSlots;
+            // the tile warp has issued the tile's MMAs ...
+            bool gave = false;
+            for (int it = 0; ld_acquire_cta(&tc->produced[g]) <= gt; ++it) {
+                if (it >= A.spin_limit || ((it & 255) == 255 && ld_relaxed(&A.ctl->err) != ERR_NONE)) {
+                    set_error(A.ctl, ERR_TIMEOUT, band);
+                    gave = true;
+                    break;
                 }
-#pragma unroll
-                for (int m = 0; m < 2; ++m)
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int r = m * 16 + gr + 8 * h;
-#pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            const int c = n * 8 + 2 * qd + j;
-                            tile[r][c] = expanded_cost(tc->xx[r], tc->yy[c], acc[m][2 * h + j]);
-                        }
-                    }
             }
+            // ... and they have completed (the slot's phase of this use)
+            for (int it = 0; !gave && !mbar_test(&tc->mbar[g][slot], (uint32_t)(gt / kTcSlots) & 1u); ++it) {
+                if (it >= A.spin_limit || ((it & 255) == 255 && ld_relaxed(&A.ctl->err) != ERR_NONE)) {
+                    set_error(A.ctl, ERR_TIMEOUT, band);
+                    break;
+                }
+            }
+            tc_fence_after();
+            float dot[32];
+            tc_ld32(tc->tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)((g * kTcSlots + slot) * kTcCols), dot);
+            tc_fence_before();
+            float (*tile)[33] = tc->tile[g][t % 3];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) tile[lane][j] = expanded_cost(xxr, tc->yy[g][slot][j], dot[j]);
             __syncwarp();
+            if (lane == 0) st_release_cta(&tc->consumed[g], gt + 1);
         }
     };
 
@@ -704,7 +769,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                     double c;
                     if constexpr (TC) {
                         const int t = cb >> 4;  // cb >= 0 here
-                        c = (double)tc->tile[t % 3][lane][(2 * cb + u) & 31];
+                        c = (double)tc->tile[g][t % 3][lane][(2 * cb + u) & 31];
                     } else {
                         c = 0.0;
                     }
@@ -1024,20 +1089,124 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
     }
 }
 
+// The tile warp of the BF16 form (see TcShared).  Once every band warp of the
+// ticket has written its rows of operand A, it serves the bands in turn: band
+// g's next tile as soon as one of the band's two slots is free -- the column
+// frames' FP32 squared norms and BF16 operand B (lane c: column 32t + c), then
+// one thread issues the four K = 16 MMAs into the slot's TMEM columns and
+// commits them to the slot's mbarrier.  It never waits on one band while
+// another could go on; an idle round sleeps briefly and a bounded number of
+// them ends in ERR_TIMEOUT.
+template <int KIND, int U, int NWMAX>
+__device__ __noinline__ void run_tiles(const SweepArgs& A, StripSmem<U, NWMAX, 0, group_of<KIND>()>& sm,
+                                       TcShared* tc) {
+    constexpr int kG = group_of<KIND>();
+    const int lane = threadIdx.x & 31;
+    int si = -1;
+    unsigned active = 0;
+    for (int g = 0; g < kG; ++g) {
+        if (sm.sweep_of[g] >= 0) {
+            si = sm.sweep_of[g];
+            active |= 1u << g;
+        }
+    }
+    if (si < 0) return;
+    const Sweep* sp = A.sweeps + si;
+    const int Q = sp->Q, ntiles = (Q + kTcCols - 1) / kTcCols;
+    const float* colf = static_cast<const float*>(sp->colseq);
+    const long long cbase = sp->cbase;
+    const int cstep = sp->cstep;
+    const int want_a = (int)sm.ticket + 1;
+    bool gave_up = false;
+    for (int g = 0; g < kG; ++g) {
+        if (!((active >> g) & 1u)) continue;
+        for (int it = 0; !gave_up && ld_acquire_cta(&tc->a_ready[g]) != want_a; ++it) {
+            if (it >= A.spin_limit || ((it & 255) == 255 && ld_relaxed(&A.ctl->err) != ERR_NONE)) {
+                set_error(A.ctl, ERR_TIMEOUT, -2);
+                gave_up = true;
+            }
+        }
+    }
+    const uint32_t a0 = smem_addr(tc->a);
+    int next[kTcBands], tb[kTcBands];  // per band: the ticket's next tile, its running-count base
+#pragma unroll
+    for (int g = 0; g < kTcBands; ++g) {
+        tb[g] = tc->tbase[g];
+        next[g] = ((active >> g) & 1u) ? 0 : ntiles;
+    }
+    for (int idle = 0;;) {
+        bool left = false, progress = false;
+#pragma unroll
+        for (int g = 0; g < kTcBands; ++g) {
+            if (next[g] >= ntiles) continue;
+            left = true;
+            const int gt = tb[g] + next[g];
+            // the slot's previous tile has been loaded by the band (or the band gave up)
+            if (!gave_up && ld_acquire_cta(&tc->consumed[g]) < gt - kTcSlots + 1) continue;
+            const int slot = gt % kTcSlots;
+            const int q = min(kTcCols * next[g] + lane, Q - 1);
+            Frame<KIND_EUC, 64> yf;
+            yf.load(colf, cbase + (long long)cstep * q, 64);
+            tc->yy[g][slot][lane] = sqnorm<64>(yf.v);
+            tc_store_row(tc->b[g][slot], lane, kTcLboB, yf.v);
+            fence_proxy_async();  // operand B is read through the async proxy
+            __syncwarp();
+            if (lane == 0) {
+                tc_fence_after();
+                const uint32_t b0 = smem_addr(tc->b[g][slot]);
+                const uint32_t dt = tc->tmem + (uint32_t)((g * kTcSlots + slot) * kTcCols);
+#pragma unroll
+                for (int kk = 0; kk < kTcK / 16; ++kk)
+                    tc_mma(dt, tc_desc(a0 + (uint32_t)kk * 2 * kTcLboA, kTcLboA, kTcSBO),
+                           tc_desc(b0 + (uint32_t)kk * 2 * kTcLboB, kTcLboB, kTcSBO), kk > 0);
+                tc_commit(&tc->mbar[g][slot]);
+                st_release_cta(&tc->produced[g], gt + 1);
+            }
+            __syncwarp();
+            ++next[g];
+            progress = true;
+        }
+        if (!left) break;
+        if (progress) {
+            idle = 0;
+        } else {
+            if (++idle >= A.spin_limit || ((idle & 63) == 0 && ld_relaxed(&A.ctl->err) != ERR_NONE)) {
+                if (!gave_up) set_error(A.ctl, ERR_TIMEOUT, -2);
+                gave_up = true;  // go on without waiting, on garbage
+            }
+            __nanosleep(32);
+        }
+    }
+    // the ticket's MMAs have completed before their slots or operand A are
+    // reused (the band warps waited for each; this covers a band that gave up)
+#pragma unroll
+    for (int g = 0; g < kTcBands; ++g) {
+        if (!((active >> g) & 1u) || ntiles == 0) continue;
+        const int gl = tb[g] + ntiles - 1;
+        for (int it = 0; !mbar_test(&tc->mbar[g][gl % kTcSlots], (uint32_t)(gl / kTcSlots) & 1u); ++it) {
+            if (it >= A.spin_limit) {
+                set_error(A.ctl, ERR_TIMEOUT, -2);
+                break;
+            }
+        }
+    }
+}
+
 template <int KIND, int R, int U, int DIM, int NWMAX, int NW, int TAGM, bool VF, bool FULL>
 __device__ __forceinline__ void run_band_s(bool special, const Sweep* sp, int si, int band, bool to_ring,
                                            bool to_global, const SweepArgs& A,
-                                           StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>& sm, int g, TcWarp* tc) {
+                                           StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>& sm, int g, TcShared* tc) {
     if (special) run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, true, FULL>(sp, si, band, to_ring, to_global, A, sm, g, tc);
     else run_band<KIND, R, U, DIM, NWMAX, NW, TAGM, VF, false, FULL>(sp, si, band, to_ring, to_global, A, sm, g, tc);
 }
 
 // Dynamic shared memory of a block: the strip state, then (tensor-core form)
-// one TcWarp per band warp.
+// the operands, norms, cost tiles and synchronisation of TcShared.
+static_assert(DTW_SWEEP_G_EUC == kTcBands && kTcBands * 32 == kTcRows, "the BF16 form's block holds the M = 128 rows of one MMA");
 template <int KIND, int U, int NWMAX, int DIM>
 constexpr size_t strip_smem_bytes() {
     constexpr size_t base = (sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>) + 127) & ~(size_t)127;
-    return base + (KIND == KIND_EUCB ? group_of<KIND>() * sizeof(TcWarp) : 0);
+    return base + (KIND == KIND_EUCB ? sizeof(TcShared) + 128 : 0);
 }
 
 // Index of the sweep holding level band gb: the last sweep whose band_begin is
@@ -1062,10 +1231,13 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
     using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM& sm = *reinterpret_cast<SM*>(smem_raw);
-    constexpr size_t tc_off = (sizeof(SM) + 127) & ~(size_t)127;
-    TcWarp* tcw = KIND == KIND_EUCB && (threadIdx.x >> 5) < kG
-                      ? reinterpret_cast<TcWarp*>(smem_raw + tc_off) + (threadIdx.x >> 5)
-                      : nullptr;
+    constexpr bool TCK = KIND == KIND_EUCB;
+    // the tensor-core state: 128-byte aligned in the shared window (operands)
+    TcShared* tcw = nullptr;
+    if constexpr (TCK) {
+        const unsigned a0 = smem_addr(smem_raw + sizeof(SM));
+        tcw = reinterpret_cast<TcShared*>(smem_raw + sizeof(SM) + (((a0 + 127u) & ~127u) - a0));
+    }
     int* sweep_of = sm.sweep_of;
     int* band_of = sm.band_of;
     const int warp = threadIdx.x >> 5;
@@ -1076,10 +1248,41 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
     // with fewer tickets than blocks only the first n_tickets blocks work: a grid
     // fixed in advance then still puts a level's few strips on separate SMs
     if ((long long)blockIdx.x >= n_tickets) return;
+    if constexpr (TCK) {
+        // the block's TMEM slots (its tile warp allocates and frees them), the
+        // slots' mbarriers (one arrival: the MMAs' commit) and the counters
+        if (warp == kG + 1) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tcw->tmem)),
+                         "r"(kTcTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        if (threadIdx.x == 0) {
+            for (int g = 0; g < kTcBands; ++g) {
+                for (int k = 0; k < kTcSlots; ++k) mbar_init(&tcw->mbar[g][k]);
+                tcw->a_ready[g] = 0;
+                tcw->produced[g] = 0;
+                tcw->consumed[g] = 0;
+                tcw->tbase[g] = 0;
+                sm.sweep_of[g] = -1;
+            }
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            sm.ntiles = 0;
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
     for (;;) {
         if (threadIdx.x == 0) {
             sm.ticket = (long long)atomicAdd(&A.ctl->ticket, 1ULL);
             sm.stop = ld_relaxed(&A.ctl->err) != ERR_NONE;
+            if constexpr (TCK) {
+                // the bands of the previous ticket have consumed all its tiles
+                for (int g = 0; g < kTcBands; ++g)
+                    if (sm.sweep_of[g] >= 0) tcw->tbase[g] += sm.ntiles;
+                sm.ntiles = 0;
+            }
         }
         if (threadIdx.x < kG) {
             sm.uprog[threadIdx.x] = 0;
@@ -1106,6 +1309,8 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
                 if (gb < n_bands) {
                     si = find_sweep(A.sweeps, n_sweeps, gb);
                     band = (int)(gb - A.sweeps[si].band_begin);
+                    // the BF16 form's plan pads each sweep's bands to whole groups
+                    if (band >= A.sweeps[si].nbands) si = -1;
                 }
             }
             if ((threadIdx.x & 31) == 0) {
@@ -1128,6 +1333,14 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
                 sm.yrs[j] = yslots(kG, w);
                 sm.ychb[j] = ychunk(w);
                 if (readers[j] > 0) base += yslots(kG, w);
+            }
+            if constexpr (TCK) {
+                // tiles of this ticket: the sweep's columns in 32s (every active
+                // band warp of a BF16-form ticket belongs to one sweep)
+                int si = -1;
+                for (int g = 0; g < kG; ++g)
+                    if (sweep_of[g] >= 0) si = sweep_of[g];
+                sm.ntiles = si >= 0 ? (A.sweeps[si].Q + kTcCols - 1) / kTcCols : 0;
             }
         }
         __syncthreads();
@@ -1173,14 +1386,26 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
                     }
                 }
             }
-        } else {
+        } else if (warp == kG) {
             const int si0 = sweep_of[0];
             if (!int_kind(KIND) || (TAGS && si0 >= 0 && A.sweeps[si0].tag_row >= 0))
                 run_loader<KIND, U, DIM, NWMAX, 2>(A, sm);
             else
                 run_loader<KIND, U, DIM, NWMAX, 1>(A, sm);
+        } else if constexpr (TCK) {
+            run_tiles<KIND, U, NWMAX>(A, sm, tcw);
         }
         __syncthreads();
+    }
+    if constexpr (TCK) {
+        // every TMEM load and MMA of the block is complete: free the slots
+        tc_fence_before();
+        __syncthreads();
+        if (warp == kG + 1) {
+            tc_fence_after();
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tcw->tmem), "r"(kTcTmemCols)
+                         : "memory");
+        }
     }
 }
 

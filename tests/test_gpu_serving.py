@@ -101,11 +101,11 @@ def test_mixed_stream_matches_alone():
 def test_late_request_admitted_while_long_one_runs():
     """A short request submitted right after a long one of the same group joins
     its levels instead of queueing behind it: it finishes while the long one
-    (a 50000 x 60000 integer pair, some ten levels) is still in flight.  Both
+    (a 100000 x 120000 integer pair, some ten levels) is still in flight.  Both
     results: the short one equals the oracle's bit for bit, the long one equals
     the pair aligned alone (the full-size oracle would take too long here)."""
     import time
-    Xb, Yb = synth.int_pair(1, 50000, 60000)
+    Xb, Yb = synth.int_pair(1, 100000, 120000)
     Xs, Ys = synth.int_pair(77, 600, 700)
     Xbd, Ybd, Xsd, Ysd = _cuda(Xb), _cuda(Yb), _cuda(Xs), _cuda(Ys)
     torch.cuda.synchronize()
