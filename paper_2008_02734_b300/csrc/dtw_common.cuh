@@ -205,8 +205,12 @@ __device__ __forceinline__ DF df_add(DF a, float c) {
 }
 __device__ __forceinline__ DF operator+(DF a, double c) { return df_add(a, (float)c); }  // c: a widened FP32 cost
 __device__ __forceinline__ bool operator==(DF a, DF b) { return a.hi == b.hi && a.lo == b.lo; }
-__device__ __forceinline__ bool operator<(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
-__device__ __forceinline__ DF df_min(DF a, DF b) { return b < a ? b : a; }
+// lexicographic order of normalised pairs; bitwise logic: no short-circuit branches
+__device__ __forceinline__ bool operator<(DF a, DF b) { return (a.hi < b.hi) | ((a.hi == b.hi) & (a.lo < b.lo)); }
+__device__ __forceinline__ DF df_min(DF a, DF b) {
+    const bool lt = b < a;
+    return DF{lt ? b.hi : a.hi, lt ? b.lo : a.lo};
+}
 __device__ __forceinline__ DF min3(DF a, DF b, DF c) { return df_min(df_min(a, b), c); }
 __device__ __forceinline__ DF acc_min(DF a, DF b) { return df_min(a, b); }
 __device__ __forceinline__ double acc_min(double a, double b) { return fmin(a, b); }

@@ -325,7 +325,9 @@ struct TcShared {
     __align__(128) unsigned char a[kTcBytesA];
     __align__(128) unsigned char b[kTcBands][kTcSlots][kTcBytesB];
     float yy[kTcBands][kTcSlots][kTcCols];        // squared norms of the tile's column frames
-    float tile[kTcBands][3][32][33];               // per band: three cost tiles (rows padded: conflict-free skewed reads)
+    // per band: three cost tiles, rows padded to 36 floats (16-byte rows; a step's
+    // 8-byte read of two columns by the skewed lanes is conflict-free per half warp)
+    __align__(16) float tile[kTcBands][3][32][36];
     unsigned long long mbar[kTcBands][kTcSlots];   // MMA completion per slot
     int produced[kTcBands];                        // per band: tiles whose MMAs are issued (running count)
     int consumed[kTcBands];                        // per band: tiles loaded from TMEM (running count)
@@ -363,6 +365,24 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
 // K-major, N = 32, M = 128.
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcCols >> 3) << 17) |
                               ((uint32_t)(kTcRows >> 4) << 24);
+
+// The BF16 form's cost from the TMEM dot product: sqrt(max(0, |x|^2 + |y|^2 -
+// 2 x.y)) in FP32 (the square root rounded to nearest, or, with
+// DTW_TC_SQRT_APPROX, the hardware approximation within 2 ulp: the form's error
+// is set by the BF16 frames, some 2^-8 relative; default: the approximation).
+#ifndef DTW_TC_SQRT_APPROX
+#define DTW_TC_SQRT_APPROX 1
+#endif
+__device__ __forceinline__ float tc_cost(float xx, float yy, float dot) {
+#if DTW_TC_SQRT_APPROX
+    const float t = fmaxf(__fmaf_rn(-2.f, dot, __fadd_rn(xx, yy)), 0.f);
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(t));
+    return r;
+#else
+    return expanded_cost(xx, yy, dot);
+#endif
+}
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -598,9 +618,15 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
             float dot[32];
             tc_ld32(tc->tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)((g * kTcSlots + slot) * kTcCols), dot);
             tc_fence_before();
-            float (*tile)[33] = tc->tile[g][t % 3];
+            float* row = tc->tile[g][t % 3][lane];
+            const float* yy = tc->yy[g][slot];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) tile[lane][j] = expanded_cost(xxr, tc->yy[g][slot][j], dot[j]);
+            for (int j = 0; j < 32; j += 4) {
+                const float4 y4 = *reinterpret_cast<const float4*>(yy + j);
+                *reinterpret_cast<float4*>(row + j) =
+                    make_float4(tc_cost(xxr, y4.x, dot[j]), tc_cost(xxr, y4.y, dot[j + 1]),
+                                tc_cost(xxr, y4.z, dot[j + 2]), tc_cost(xxr, y4.w, dot[j + 3]));
+            }
             __syncwarp();
             if (lane == 0) st_release_cta(&tc->consumed[g], gt + 1);
         }
@@ -756,6 +782,9 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         // and branches instead.
         const bool act = !CHECK || (unsigned)cb < (unsigned)nblk;
         if (!CHECK || !TC || act) {
+            // tensor-core form: the block's two costs from the lane's row of its tile
+            float2 tcc = make_float2(0.f, 0.f);
+            if constexpr (TC) tcc = *reinterpret_cast<const float2*>(&tc->tile[g][(cb >> 4) % 3][lane][(2 * cb) & 31]);
             Acc rowv[SPECIAL ? R : 1][U];  // the block's cells, for out rows and the last cell
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -766,13 +795,8 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                 int t_dg = (u == 0) ? dprevt : upt[u - 1];
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
-                    double c;
-                    if constexpr (TC) {
-                        const int t = cb >> 4;  // cb >= 0 here
-                        c = (double)tc->tile[g][t % 3][lane][(2 * cb + u) & 31];
-                    } else {
-                        c = 0.0;
-                    }
+                    double c = 0.0;
+                    if constexpr (TC) c = (double)(u == 0 ? tcc.x : tcc.y);  // cb >= 0 here
                     // edit distance: the diagonal move carries delta, every move the gap
                     const auto cc = [&]() {
                         if constexpr (TC) return c;
@@ -1134,6 +1158,7 @@ __device__ __noinline__ void run_tiles(const SweepArgs& A, StripSmem<U, NWMAX, 0
         tb[g] = tc->tbase[g];
         next[g] = ((active >> g) & 1u) ? 0 : ntiles;
     }
+    unsigned nap = 32;
     for (int idle = 0;;) {
         bool left = false, progress = false;
 #pragma unroll
@@ -1169,12 +1194,16 @@ __device__ __noinline__ void run_tiles(const SweepArgs& A, StripSmem<U, NWMAX, 0
         if (!left) break;
         if (progress) {
             idle = 0;
+            nap = 32;
         } else {
             if (++idle >= A.spin_limit || ((idle & 63) == 0 && ld_relaxed(&A.ctl->err) != ERR_NONE)) {
                 if (!gave_up) set_error(A.ctl, ERR_TIMEOUT, -2);
                 gave_up = true;  // go on without waiting, on garbage
             }
-            __nanosleep(32);
+            // a band needs a tile every 16 steps: back off while none is due, so
+            // that polling takes few issue slots from the band warp on this SMSP
+            __nanosleep(nap);
+            nap = min(2 * nap, 1024u);
         }
     }
     // the ticket's MMAs have completed before their slots or operand A are
