@@ -32,6 +32,7 @@ struct Ctx {
     int timing = 0;
     long long base_area = 16384;
     int spin_limit = 1 << 22;
+    int fused_split = 1;  // the split in the sweep kernel: 0 never, 1 float kinds, 2 every kind but BF16
     long long skip_publish = -1;
     uint32_t epoch = 1;  // next boundary-word epoch; increases across calls
     int num_sms = 0;
@@ -142,7 +143,7 @@ int level_graph(Ctx& c, const std::vector<long long>& key, const SweepArgs& sa, 
         e = cudaStreamBeginCaptureToGraph(lg.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaError_t e1 = launch_sweep(kind, d, int_kind(kind), sa, c.num_sms, 0, lg.cap, c.variant);
-            if (e1 == cudaSuccess) e1 = launch_split(sp, lg.cap);
+            if (e1 == cudaSuccess && sa.prog == nullptr) e1 = launch_split(sp, lg.cap);
             if (e1 == cudaSuccess) e1 = launch_plan(pn, lg.cap);
             if (e1 == cudaSuccess) e1 = launch_level_cond(ctl, h, max_levels, lg.cap);
             cudaGraph_t got = nullptr;
@@ -407,10 +408,15 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     // first sweep); an error the plan records stops the loop on the device and is
     // returned from the counters read after the base case.
     const bool graph = c.use_graph && !c.timing && mode == MODE_ALIGN && !roots.empty();
+    // fused split: the sweep kernel runs the level's split items once its tickets are gone
+    const bool fuse = mode == MODE_ALIGN && kind != KIND_EUCB &&
+                      (c.fused_split == 2 || (c.fused_split == 1 && !int_kind(kind)));
+    int* d_prog = fuse ? reinterpret_cast<int*>(ws + L.prog) : nullptr;
     if (!roots.empty()) {
         PlanArgs pa{cur, (int)roots.size(), d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
                     L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
         pa.tmap = d_tmap;
+        pa.prog = d_prog;
         pa.cap_tickets = L.cap_tickets;
         pa.map_min = c.num_sms;
         e = launch_plan(pa, st);
@@ -436,10 +442,13 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         pn.tmap = d_tmap;
         pn.cap_tickets = L.cap_tickets;
         pn.map_min = c.num_sms;
+        pn.prog = d_prog;
+        sa.prog = d_prog;
+        sa.split = sp;
         const std::vector<long long> key{(long long)(uintptr_t)ws, (long long)L.total, L.cap_box, L.cap_base,
                                          L.cap_sweeps, L.cap_buf, L.cap_out, L.cap_items, kind, d, base_area,
                                          c.spin_limit, c.skip_publish, c.num_sms, max_levels, (long long)L.ctl,
-                                         c.variant};
+                                         c.variant, d_prog != nullptr};
         cudaGraphExec_t ex = nullptr;
         int grc = level_graph(c, key, sa, sp, pn, d_ctl, kind, d, max_levels, &ex);
         if (grc != DTW_OK) return grc;
@@ -453,6 +462,14 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         SweepArgs sa{d_sweeps, d_ctl,        reinterpret_cast<unsigned long long*>(ws + L.bufpool),
                      ws + L.outpool, d_sres, d, c.spin_limit, c.skip_publish};
         sa.tmap = d_tmap;
+        SplitArgs sp{cur,    n_cur,          d_pairs, d_pres, kind,      d,
+                     halo,   d_sweeps,       d_sres,  ws + L.outpool, nxt, d_base,
+                     d_ctl,  base_area,      (int)L.cap_box, (int)L.cap_base,
+                     d_boxdone, ws + L.partials, hc.n_items, c.num_sms};
+        if (d_prog != nullptr) {
+            sa.prog = d_prog;
+            sa.split = sp;
+        }
         cudaEvent_t s0 = nullptr, s1 = nullptr;
         if (c.timing) s0 = T.mark();
         // integer levels may mix tagged and untagged boxes
@@ -461,16 +478,15 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         if (c.timing) s1 = T.mark();
         ++sweeps;
         if (e == cudaSuccess && mode != MODE_COST) {
-            SplitArgs sp{cur,    n_cur,          d_pairs, d_pres, kind,      d,
-                         halo,   d_sweeps,       d_sres,  ws + L.outpool, nxt, d_base,
-                         d_ctl,  base_area,      (int)L.cap_box, (int)L.cap_base,
-                         d_boxdone, ws + L.partials, hc.n_items, c.num_sms};
-            e = launch_split(sp, st);
-            ++launches;
+            if (d_prog == nullptr) {
+                e = launch_split(sp, st);
+                ++launches;
+            }
             // plan the next level from the boxes the split appended (count read on the device)
             PlanArgs pa{nxt, -1, d_pairs, mode, kind, halo, U, BR, G, d_sweeps, d_ctl,
                         L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
             pa.tmap = d_tmap;
+            pa.prog = d_prog;
             pa.cap_tickets = L.cap_tickets;
             pa.map_min = c.num_sms;
             if (e == cudaSuccess) e = launch_plan(pa, st);
@@ -950,6 +966,10 @@ int dtw_set_option(int32_t key, int64_t value) {
         case DTW_OPT_EDIT_GAP:
             if (value < 0 || value > (1 << 20)) return DTW_EINVAL;
             c.egap = (int32_t)value;
+            return DTW_OK;
+        case DTW_OPT_FUSED_SPLIT:
+            if (value < 0 || value > 2) return DTW_EINVAL;
+            c.fused_split = (int)value;
             return DTW_OK;
         case DTW_OPT_NOALLOC_EPOCH:
             if (value < 0 || value > 0xFFFFFFFFLL) return DTW_EINVAL;

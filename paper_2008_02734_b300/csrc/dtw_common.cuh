@@ -151,6 +151,8 @@ struct LevelCtl {
     unsigned long long polls;    // failed polls of boundary words
     int32_t levels;              // levels planned on the device (graph-driven level loop)
     int32_t tmap_on;             // the current level's tickets follow the ticket map (group-major order)
+    int32_t split_ticket;        // next split work item of the sweep kernel's split phase
+    int32_t pad_;
 };
 
 // ---------------------------------------------------------------- memory order

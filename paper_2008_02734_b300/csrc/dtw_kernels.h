@@ -9,6 +9,26 @@
 
 namespace dtwb {
 
+struct SplitArgs {
+    const Box* boxes;
+    int n_boxes;
+    const PairDesc* pairs;
+    PairRes* pres;
+    int kind, d;
+    int halo;
+    const Sweep* sweeps;
+    const SweepRes* res;
+    const void* outpool;
+    Box* next;
+    Box* base;
+    LevelCtl* ctl;
+    long long base_area;
+    int cap_next, cap_base;
+    int* box_done;    // per-box count of finished work items
+    void* partials;   // per work item: kSplitRowsMax partial row minima (16 B each)
+    int n_items;      // work items of the level (as planned); < 0: read ctl->n_items on the device
+    int num_sms;
+};
 struct SweepArgs {
     const Sweep* sweeps;
     LevelCtl* ctl;
@@ -20,6 +40,11 @@ struct SweepArgs {
     long long skip_ticket;  // test hook: this level band never publishes (-1: none)
     int32_t* best = nullptr;  // KIND_LOCAL: 4 int32 per level band (value, frame row, column, written)
     const int2* tmap = nullptr;  // ticket -> (sweep, band group), when the plan wrote it (ctl->tmap_on)
+    // Fused split (prog non-null): bands holding split rows publish their
+    // progress in prog (kProgWords per sweep), and blocks that find the ticket
+    // queue empty run the level's split work items (split) while the sweeps end.
+    int* prog = nullptr;
+    SplitArgs split{};
 };
 
 // Sweep variants
@@ -61,29 +86,10 @@ struct PlanArgs {
     long long cap_tickets = 0; // its capacity; a level that needs more uses the plain order
     long long map_min = 0;     // levels with at most this many plain tickets skip the map (all
                                // their tickets run at once, so their order does not matter)
+    int* prog = nullptr;       // non-null: reset the sweeps' split-row progress words (fused split)
 };
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st);
 
-struct SplitArgs {
-    const Box* boxes;
-    int n_boxes;
-    const PairDesc* pairs;
-    PairRes* pres;
-    int kind, d;
-    int halo;
-    const Sweep* sweeps;
-    const SweepRes* res;
-    const void* outpool;
-    Box* next;
-    Box* base;
-    LevelCtl* ctl;
-    long long base_area;
-    int cap_next, cap_base;
-    int* box_done;    // per-box count of finished work items
-    void* partials;   // per work item: kSplitRowsMax partial row minima (16 B each)
-    int n_items;      // work items of the level (as planned); < 0: read ctl->n_items on the device
-    int num_sms;
-};
 cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
 
 struct BaseArgs {

@@ -48,6 +48,7 @@
 
 #include "dtw_common.cuh"
 #include "dtw_kernels.h"
+#include "split.cuh"
 
 // Lane block of the integer sweep (rows x columns per lane and step).
 #ifndef DTW_INT_R
@@ -95,6 +96,16 @@ constexpr int URS = 64;                  // slots (column blocks) of a row ring
 #ifndef DTW_SWEEP_UNROLL_EUC
 #define DTW_SWEEP_UNROLL_EUC 1
 #endif
+// Steps between a split-row band's progress publications (fused split): a power
+// of two, or 0 (default) for only at the band's end.  Publishing along the way
+// lets split items start while the window bands still run, but each publication
+// is a gpu-scope fence in the level's last band, and the check alone slowed that
+// band's steps: end-only was measured fastest (integer pair 2.34 ms against 2.46
+// with a publication every 64 steps).
+#ifndef DTW_PROG_EVERY
+#define DTW_PROG_EVERY 0
+#endif
+
 #ifndef DTW_EUC_YPREFETCH
 #define DTW_EUC_YPREFETCH 0
 #endif
@@ -886,10 +897,30 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         }
     };
 
+    // fused split: a band holding split rows publishes, every DTW_PROG_EVERY steps
+    // (0: only) and at its end, how many column blocks of them are stored (all its lanes up to the last
+    // one holding such a row have passed them); every lane fences its own stores
+    // before the warp barrier, lane 0 then writes the word (gpu scope)
+    int* pword = nullptr;
+    int l_last = 0;
+    if constexpr (SPECIAL) {
+        const int b_lo = band * 32 * R;
+        if (A.prog != nullptr && nout > 0 && out_row0 < b_lo + 32 * R && out_row0 + nout > b_lo) {
+            pword = A.prog + (size_t)sweep_idx * kProgWords + (band == out_row0 / (32 * R) ? 0 : 1);
+            l_last = min(31, (out_row0 + nout - 1 - b_lo) / R);
+        }
+    }
+    auto publish = [&](int* w, int v) {
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(w), "r"(v) : "memory");
+    };
     sync_group(0);
     fetch(0);
     for (int s0 = 0; s0 < nsteps; s0 += KC) {
         if (s0 > 0) sync_group(s0);
+        if (SPECIAL && DTW_PROG_EVERY > 0 && pword != nullptr && (s0 & (DTW_PROG_EVERY - 1)) == 0 && s0 > l_last)
+            publish(pword, min(nblk, s0 - l_last));
         if (TC && (s0 & 15) == 0 && s0 < nblk) build_tile(s0 >> 4);
         if (s0 >= 31 && s0 + KC < nblk) {
             if constexpr (FULL) {
@@ -953,6 +984,10 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
             else r->end_f = to_double(end_v);
             r->end_tag = end_t;
         }
+        if (pword != nullptr) publish(pword, nblk);
+        // the band holding the sweep's last row: its last cell is recorded
+        if (A.prog != nullptr && (rows - 1) / (32 * R) == band)
+            publish(A.prog + (size_t)sweep_idx * kProgWords + 2, 1);
     }
     if (lane == 0 && ws.waits) {
         atomicAdd(&A.ctl->resyncs, ws.waits);
@@ -997,6 +1032,7 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
     int unext = 0;
     bool gave_up = false, inflight = false;
     WaitStats ws;
+    unsigned nap = 64;
     for (int idle = 0;;) {
         bool work_left = inflight, progress = false;
         int issued[kG];
@@ -1090,6 +1126,7 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
         if (!work_left) break;
         if (progress) {
             idle = 0;
+            nap = 64;
         } else if (!inflight) {
             if (idle == 0) ++ws.waits;
             if (++idle >= A.spin_limit || ((idle & 63) == 0 && ld_relaxed(&A.ctl->err) != ERR_NONE)) {
@@ -1104,7 +1141,15 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
                 }
                 break;
             }
-            __nanosleep(64);
+            // integer kinds: short steps, the hand-off latency is on the critical
+            // path; float kinds: long steps, and the loader shares its scheduler
+            // with a band warp, so it backs off (up to 512 ns) while idle
+            if constexpr (int_kind(KIND)) {
+                __nanosleep(64);
+            } else {
+                __nanosleep(nap);
+                nap = min(2 * nap, 512u);
+            }
         }
     }
     if (lane == 0 && ws.waits) {
@@ -1248,6 +1293,29 @@ __device__ __forceinline__ int find_sweep(const Sweep* sweeps, int n_sweeps, lon
         else hi = mid - 1;
     }
     return lo;
+}
+
+// The fused split phase: a block that found the ticket queue empty (every band
+// of the level is running or done) takes the level's split work items in turn;
+// each waits for its columns' split rows (split_item) while the window bands
+// finish.
+template <int KIND, int DIM, int U, typename SM>
+__device__ __noinline__ void split_phase(const SweepArgs& A, SM& sm) {
+    const SplitArgs& a = A.split;
+    const int n_items = a.n_items >= 0 ? a.n_items : A.ctl->n_items;
+    __syncthreads();  // every thread has left the ticket loop (it read sm.ticket)
+    for (;;) {
+        if (threadIdx.x == 0) {
+            sm.ticket = atomicAdd(&A.ctl->split_ticket, 1);
+            sm.stop = ld_relaxed(&A.ctl->err) != ERR_NONE;  // outputs of a failed level are not valid
+        }
+        __syncthreads();
+        const int it = (int)sm.ticket;
+        const bool stop = sm.stop != 0;
+        __syncthreads();
+        if (stop || it >= n_items) break;
+        split_item<KIND, DIM, true>(a, it, U, A.prog, A.spin_limit);
+    }
 }
 
 // TAGS: the launch may contain tagged sweeps (integer kind), whose rows carry
@@ -1435,6 +1503,11 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tcw->tmem), "r"(kTcTmemCols)
                          : "memory");
         }
+    }
+    // (the BF16 form keeps the separate split launch: its split recomputes
+    // 64-dimensional BF16 costs, which would raise the whole kernel's registers)
+    if constexpr (KIND != KIND_LOCAL && KIND != KIND_EUCB) {
+        if (A.prog != nullptr) split_phase<KIND, DIM, U>(A, sm);
     }
 }
 

@@ -14,7 +14,7 @@ inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
     size_t feat, pairs, pres, boxA, boxB, base, sweeps, sres, bufpool, outpool, boxdone, partials, minmax, jlo, jhi,
-        off, path, ctl, tmap, total;
+        off, path, ctl, tmap, prog, total;
     long long cap_box, cap_base, cap_sweeps, cap_buf, cap_out, cap_items, cap_tickets;
 };
 
@@ -58,6 +58,7 @@ inline Layout make_layout(int B, long long sumM, long long sumN, long long feat_
     L.path = take(8 * (size_t)path_pairs);
     L.ctl = take(sizeof(LevelCtl));
     L.tmap = take(8 * (size_t)L.cap_tickets);
+    L.prog = take(4 * 4 * (size_t)L.cap_sweeps);  // split-row progress, four words per sweep (fused split)
     L.total = o;
     return L;
 }

@@ -389,3 +389,28 @@ def test_precision_forms_orchestral_pair():
         check_path_struct(p, M, N)
         assert cost == pytest.approx(c_ref, rel=tol), kw
         assert oracle.path_cost(X, Y, p) == pytest.approx(c_ref, rel=tol), kw
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+@pytest.mark.parametrize("fused", [2, 0])
+def test_split_in_sweep_kernel_and_separate(fused, graph):
+    """The level's split as the sweep kernel's split phase (blocks past the
+    ticket queue take split items while the window bands finish) and as a
+    separate launch, with the level loop as a graph and from the host: the same
+    canonical integer paths and optimal float costs."""
+    dtw.set_option(dtw.OPT_FUSED_SPLIT, fused)
+    dtw.set_option(dtw.OPT_GRAPH, graph)
+    try:
+        check_int(*synth.int_pair(321, 3000, 3500))
+        rng = np.random.default_rng(17)
+        check_int(rng.integers(0, 3, 2500).astype(np.int32), rng.integers(0, 3, 2100).astype(np.int32))
+        check_int(np.full(700, 4, np.int32), np.full(900, 9, np.int32))  # every split row ties: tag sweeps
+        check_float(*synth.chroma_pair(322, 900, 1100))
+        pairs = [synth.int_pair(330 + k, m, n) for k, (m, n) in enumerate([(1200, 900), (40, 3000), (2500, 2600)])]
+        res = dtw.align_batch([_cuda(x) for x, _ in pairs], [_cuda(y) for _, y in pairs])
+        for (X, Y), (path, cost) in zip(pairs, res):
+            p_ref, c_ref = oracle.dtw(X, Y)
+            assert cost == c_ref and np.array_equal(path.cpu().numpy(), p_ref)
+    finally:
+        dtw.set_option(dtw.OPT_FUSED_SPLIT, 1)
+        dtw.set_option(dtw.OPT_GRAPH, 1)
