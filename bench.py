@@ -629,8 +629,9 @@ def measure_precision(steps: int, warmup: int, forms=("f32cost_f64dp", "f32cost_
 def run_precision_workload(args):
     """The orchestral-length pair in each precision form; value is the exact
     (FP32 cost, FP64 DP) form's GCUPS."""
-    r = measure_precision(args.steps, args.warmup)
-    ex = r["forms"]["f32cost_f64dp"]
+    forms = tuple(args.forms.split(",")) if args.forms else ("f32cost_f64dp", "f32cost_f32kahan", "bf16cost_f32kahan")
+    r = measure_precision(args.steps, args.warmup, forms=forms)
+    ex = r["forms"].get("f32cost_f64dp") or next(iter(r["forms"].values()))
     line = {"metric": METRIC, "value": ex["gcups"], "unit": "GCUPS", "n_gpus": 1,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ex["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-cost/f64-dp",
@@ -928,6 +929,8 @@ def main():
     ap.add_argument("--max-len", type=int, default=20000, help="longest request of the serving workload")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="admission budget of the serving workload")
     ap.add_argument("--exact", action="store_true", help="serving workload: exact form for d = 64 too")
+    ap.add_argument("--forms", default=None,
+                    help="precision workload: comma-separated forms (f32cost_f64dp, f32cost_f32kahan, bf16cost_f32kahan)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 GPU comparator")
     ap.add_argument("--no-extra", action="store_true",
                     help="default run: skip the batch, precision and serving configurations")
@@ -947,6 +950,12 @@ def main():
         return run_pipes()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "int_pair" and (args.no_graph or args.base_area is not None):
+        import paper_2008_02734_b300 as dtw
+        if args.no_graph:
+            dtw.set_option(dtw.OPT_GRAPH, 0)
+        if args.base_area is not None:
+            dtw.set_option(dtw.OPT_BASE_AREA, args.base_area)
     if args.workload == "batch":
         return run_batch_workload(args)
     if args.workload == "precision":
