@@ -96,6 +96,12 @@ constexpr int URS = 64;                  // slots (column blocks) of a row ring
 #ifndef DTW_SWEEP_UNROLL_EUC
 #define DTW_SWEEP_UNROLL_EUC 1
 #endif
+// The block's last band warp hands its last row to the loader warp through one
+// more shared-memory ring, and the loader writes it to the global boundary row
+// (1), instead of storing the epoch-stamped words itself every step (0).
+#ifndef DTW_LOADER_DRAIN
+#define DTW_LOADER_DRAIN 1
+#endif
 // Steps between a split-row band's progress publications (fused split): a power
 // of two, or 0 (default) for only at the band's end.  Publishing along the way
 // lets split items start while the window bands still run, but each publication
@@ -110,6 +116,12 @@ constexpr int URS = 64;                  // slots (column blocks) of a row ring
 #define DTW_EUC_YPREFETCH 0
 #endif
 constexpr int KC = DTW_SWEEP_KC;         // steps per group: rings are synchronised once per group
+// Drained by the loader: every kind but the integer kind's fully unrolled
+// variant, whose steady 8-step groups publish one row ring per group and whose
+// cross-block hand-off then lags by up to a group (integer pair 2.35 ms with
+// the band's own stores against 2.52 with the drain; the others gain 2-6%).
+template <int KIND, bool FULL>
+__host__ __device__ constexpr bool drain_of() { return DTW_LOADER_DRAIN != 0 && !(int_kind(KIND) && FULL); }
 constexpr int kGroupUnroll = DTW_SWEEP_UNROLL;        // integer kind
 constexpr int kGroupUnrollEuc = DTW_SWEEP_UNROLL_EUC;  // Euclidean kind (longer steps, larger code)
 
@@ -480,9 +492,9 @@ template <int U, int NWMAX, int YW, int G>
 struct StripSmem {
     static_assert(G >= 1 && G <= kGMax, "compute warps per block");
     static constexpr int YSW = FrameSlot<U, YW>::W;  // words per frame ring slot
-    __align__(16) uint32_t uring[G][URS * U * NWMAX];
+    __align__(16) uint32_t uring[G + 1][URS * U * NWMAX];  // ring G: the last warp's row, for the loader
     __align__(16) uint32_t yring[YW > 0 ? kYSlotsOf(G) * YSW : 4];
-    int uprog[G], ucons[G], yprog[G], ycons[G];
+    int uprog[G + 1], ucons[G + 1], yprog[G], ycons[G];
     int ybase[G], yrs[G], ychb[G];  // per stream: first slot, slots, blocks per loader round
     int sweep_of[G], band_of[G], ystream[G];
     long long ticket;
@@ -528,6 +540,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     constexpr int YW = FrameWords<KIND, DIM>::v;
     // BF16 tensor-core form: one row per lane, 16 column blocks of 2 per tile
     constexpr bool TC = KIND == KIND_EUCB;
+    constexpr bool kDr = drain_of<KIND, FULL>();
     static_assert(!TC || (DIM == 64 && R == 1 && U == 2), "the tensor-core form is built for d = 64, R = 1, U = 2");
     constexpr bool TAG = TAGM != 0;
     constexpr int SLOT = U * NWMAX;  // row ring slot stride (words)
@@ -564,7 +577,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
 
     uint32_t* rin = sm.uring[g];
     constexpr int kG = group_of<KIND>();
-    uint32_t* rout = sm.uring[g + 1 < kG ? g + 1 : g];
+    uint32_t* rout = sm.uring[kDr || g + 1 < kG ? g + 1 : g];
     const int ys = sm.ystream[g];
     constexpr int YSW = SM::YSW;
     const uint32_t* yr = sm.yring + (size_t)sm.ybase[ys] * YSW;
@@ -716,7 +729,10 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     int uroom = URS;  // this warp may write blocks < uroom into rout
     const int nsteps = nblk + 31;
 
-    const bool w31_ring = to_ring && lane == 31, w31_global = to_global && lane == 31;
+    // the band's last row goes to a ring (the next warp's, or the loader's for the
+    // block's last warp) or, without the loader's drain, to global memory
+    const bool out_ring = to_ring || (kDr && to_global);
+    const bool w31_ring = out_ring && lane == 31, w31_global = !kDr && to_global && lane == 31;
     // warp-uniform: release what the previous groups read and wrote, wait for
     // the blocks this group reads, and for room for the blocks it writes
     int uavail = 0, yavail = 0;  // blocks known to be in the row ring / the frame ring
@@ -733,7 +749,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
             asm volatile("fence.acq_rel.cta;" ::: "memory");
             st_relaxed_cta_if(lane == 0 && has_above, &sm.ucons[g], min(s0 + 1, nblk));
             if constexpr (YW > 0) st_relaxed_cta_if(lane == 0 && yrel, &sm.ycons[g], min(s0 - 30, nblk));
-            st_relaxed_cta_if(w31_ring && s0 > 31, &sm.uprog[g + 1 < kG ? g + 1 : g], min(s0 - 31, nblk));
+            st_relaxed_cta_if(w31_ring && s0 > 31, &sm.uprog[kDr || g + 1 < kG ? g + 1 : g], min(s0 - 31, nblk));
         }
         if (s0 < nblk) {  // lane 0 reads blocks up to s0 + KC (the last one ahead of time)
             const int need = min(s0 + KC + 1, nblk);
@@ -743,7 +759,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
                 if (need > yavail) yavail = wait_counter(&sm.yprog[ys], need, A.ctl, A.spin_limit, band, gave_up, ws);
             }
         }
-        if (to_ring) {  // this group writes blocks up to s0 + KC - 32
+        if (out_ring) {  // this group writes blocks up to s0 + KC - 32
             const int last = s0 + KC - 32;
             if (last >= uroom)
                 uroom = wait_counter(&sm.ucons[g + 1], last + 1 - URS, A.ctl, A.spin_limit, band, gave_up, ws) + URS;
@@ -890,10 +906,12 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
 #pragma unroll
             for (int u = 0; u < U; ++u) pack<KIND, NW>(bot[u], bott[u], w + u * NW);
             st_shared_words_if<BW>(w31_ring && obok, rout + (ob & (URS - 1)) * SLOT, w);
-            unsigned long long* dst = buf + (long long)ob * BW;
+            if constexpr (!kDr) {
+                unsigned long long* dst = buf + (long long)ob * BW;
 #pragma unroll
-            for (int i = 0; i < BW / 2; ++i)
-                st_words2_if(w31_global && obok, dst + 2 * i, mkword(w[2 * i], ep_out), mkword(w[2 * i + 1], ep_out));
+                for (int i = 0; i < BW / 2; ++i)
+                    st_words2_if(w31_global && obok, dst + 2 * i, mkword(w[2 * i], ep_out), mkword(w[2 * i + 1], ep_out));
+            }
         }
     };
 
@@ -946,7 +964,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
             }
         }
     }
-    if (to_ring && lane == 31) st_release_cta(&sm.uprog[g + 1], nblk);
+    if (out_ring && lane == 31) st_release_cta(&sm.uprog[g + 1], nblk);
     if constexpr (KIND == KIND_LOCAL) {
         // the band's best node: lowest value, then lowest frame row, then column
         Acc v = INF;
@@ -1005,7 +1023,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
 // round in flight).  Nothing blocks on another
 // warp: a round that can do nothing sleeps briefly, and a bounded number of
 // idle rounds ends in ERR_TIMEOUT.
-template <int KIND, int U, int DIM, int NWMAX, int NW>
+template <int KIND, int U, int DIM, int NWMAX, int NW, bool DRAIN>
 __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>& sm) {
     using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>;
     constexpr int YW = FrameWords<KIND, DIM>::v;
@@ -1030,11 +1048,43 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
     const unsigned long long* ubuf = s0 ? A.bufpool + s0->buf_off : nullptr;
     const uint32_t uep = s0 ? s0->epoch0 + (uint32_t)uband : 0u;  // epoch of the band above
     int unext = 0;
+    // the block's last band warp's row, drained into the global boundary row
+    // (when its band has a band below): epoch-stamped words, like the band would
+    // write them; two payload words per column for float kinds and tag sweeps
+    const int sil = sm.sweep_of[kG - 1];
+    const Sweep* sl = sil >= 0 ? A.sweeps + sil : nullptr;
+    const int dband = sl ? sm.band_of[kG - 1] : 0;
+    const bool drain = DRAIN && sl && dband + 1 < sl->nbands && sl->band_begin + dband != A.skip_ticket;
+    const int dnblk = drain ? sl->nblk : 0;
+    const int dnw = (int_kind(KIND) && (sl == nullptr || sl->tag_row < 0)) ? 1 : 2;
+    unsigned long long* dbuf = drain ? A.bufpool + sl->buf_off : nullptr;
+    const uint32_t dep = drain ? sl->epoch0 + (uint32_t)dband + 1u : 0u;
+    int dnext = 0;  // blocks written to global memory
     bool gave_up = false, inflight = false;
     WaitStats ws;
     unsigned nap = 64;
     for (int idle = 0;;) {
         bool work_left = inflight, progress = false;
+        if (dnext < dnblk) {
+            work_left = true;
+            const int avail = ld_acquire_cta(&sm.uprog[kG]);
+            if (avail > dnext) {
+                const int b1 = min(avail, dnext + 32 / U);
+                const int col = dnext * U + lane;
+                if (col < b1 * U) {
+                    const uint32_t* src = sm.uring[kG] + ((col / U) & (URS - 1)) * SLOT + (col % U) * dnw;
+                    unsigned long long* dst = dbuf + (size_t)col * dnw;
+                    for (int i = 0; i < dnw; ++i)
+                        asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(dst + i), "l"(mkword(src[i], dep))
+                                     : "memory");
+                }
+                // the warp barrier orders every lane's ring reads before lane 0 frees the slots
+                __syncwarp();
+                if (lane == 0) st_release_cta(&sm.ucons[kG], b1);
+                dnext = b1;
+                progress = true;
+            }
+        }
         int issued[kG];
         if constexpr (YW > 0) {
 #pragma unroll
@@ -1138,6 +1188,7 @@ __device__ __noinline__ void run_loader(const SweepArgs& A, StripSmem<U, NWMAX, 
 #pragma unroll
                     for (int j = 0; j < kG; ++j) st_release_cta(&sm.yprog[j], 1 << 30);
                     st_release_cta(&sm.uprog[0], 1 << 30);
+                    st_release_cta(&sm.ucons[kG], 1 << 30);
                 }
                 break;
             }
@@ -1382,10 +1433,12 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
             }
         }
         if (threadIdx.x < kG) {
-            sm.uprog[threadIdx.x] = 0;
-            sm.ucons[threadIdx.x] = 0;
             sm.yprog[threadIdx.x] = 0;
             sm.ycons[threadIdx.x] = 0;
+        }
+        if (threadIdx.x <= kG) {
+            sm.uprog[threadIdx.x] = 0;
+            sm.ucons[threadIdx.x] = 0;
         }
         __syncthreads();
         const long long t = sm.ticket;
@@ -1486,9 +1539,9 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
         } else if (warp == kG) {
             const int si0 = sweep_of[0];
             if (!int_kind(KIND) || (TAGS && si0 >= 0 && A.sweeps[si0].tag_row >= 0))
-                run_loader<KIND, U, DIM, NWMAX, 2>(A, sm);
+                run_loader<KIND, U, DIM, NWMAX, 2, drain_of<KIND, FULL>()>(A, sm);
             else
-                run_loader<KIND, U, DIM, NWMAX, 1>(A, sm);
+                run_loader<KIND, U, DIM, NWMAX, 1, drain_of<KIND, FULL>()>(A, sm);
         } else if constexpr (TCK) {
             run_tiles<KIND, U, NWMAX>(A, sm, tcw);
         }
