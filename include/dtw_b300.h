@@ -324,11 +324,12 @@ enum dtw_option {
     DTW_OPT_NOALLOC_EPOCH = 9, /* test hook: the next dtw_cost_noalloc call starts its boundary-word epochs at
                                   this value, 0 .. 2^32-1 (exercises the restart near the 32-bit limit) */
     DTW_OPT_FUSED_SPLIT = 10  /* where dtw_align / dtw_align_batch run each level's split (the argmin of
-                                 F + B - C, Lemma 2): 1 (default) float kinds in the sweep kernel, whose
-                                 blocks take split items once the sweep tickets are gone, integer kinds in a
-                                 separate launch (measured faster for them); 2 every kind in the sweep kernel;
-                                 0 every kind in a separate launch.  The BF16 cost form always uses the
-                                 separate launch.  Results are the same in every case. */
+                                 F + B - C, Lemma 2): 1 (default) in the sweep kernel, whose blocks take split
+                                 items once the sweep tickets are gone, for float kinds and for batches of
+                                 two or more pairs, and in a separate launch for a single integer or edit
+                                 pair (measured faster for it); 2 always in the sweep kernel; 0 always in a
+                                 separate launch.  The BF16 cost form always uses the separate launch.
+                                 Results are the same in every case. */
 };
 DTW_API int dtw_set_option(int32_t key, int64_t value);
 

@@ -35,7 +35,7 @@ OK, PENDING, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBUSY, EINTERNAL = 0, 1
 OPT_TIMING, OPT_BASE_AREA, OPT_SPIN_LIMIT, OPT_SKIP_PUBLISH, OPT_GRAPH, OPT_SWEEP_VARIANT = 1, 2, 3, 4, 5, 6
 OPT_EDIT_SUB, OPT_EDIT_GAP = 7, 8
 OPT_NOALLOC_EPOCH = 9  # test hook: the next dtw_cost_noalloc call's first boundary-word epoch
-OPT_FUSED_SPLIT = 10  # 0 separate split launch, 1 (default) float kinds in the sweep kernel, 2 every kind
+OPT_FUSED_SPLIT = 10  # 0 separate split launch, 1 (default) float kinds and batches in the sweep kernel, 2 always
 EDIT_I32 = 2  # weighted edit distance of int32 symbol sequences (cost kind)
 
 
