@@ -352,7 +352,7 @@ __device__ __forceinline__ float sqnorm(const float* v) {
 }
 
 // Frame cost C (Section 2.1): |x-y|, or the Euclidean distance (Section 4.1)
-// evaluated in FP32 (sum of squares with FMA, correctly rounded sqrt) and widened.
+// evaluated in FP32 (sum of squares with FMA, square root by cost_sqrt) and widened.
 __device__ __forceinline__ int32_t frame_cost(const Frame<KIND_ABS, 1>& a, const Frame<KIND_ABS, 1>& b) {
     return abs(a.v - b.v);
 }
@@ -362,6 +362,26 @@ __device__ __forceinline__ int32_t frame_cost(const Frame<KIND_EDIT, 1>&, const 
 __device__ __forceinline__ int32_t frame_cost(const Frame<KIND_LOCAL, 1>&, const Frame<KIND_LOCAL, 1>&) { return 0; }
 __device__ __forceinline__ int32_t edit_delta(int32_t x, int32_t y, int32_t match, int32_t sub, int32_t gap) {
     return (x == y ? match : sub) - gap;
+}
+
+// Square root of a frame cost's sum of squares: the hardware approximation
+// (sqrt.approx.f32, one instruction, within 2 ulp; exact at +0 and +infinity),
+// or with DTW_EUC_SQRT_APPROX=0 the correctly rounded square root, several
+// instructions with a slow-path branch.  The approximation adds at most about
+// 2.4e-7 relative to a cost, the size of the FP32 sum of squares' own rounding,
+// far inside the 1e-6 tolerance; every kernel evaluates costs through here, so
+// the sweeps, the split and the base case see the same cost of a cell.
+#ifndef DTW_EUC_SQRT_APPROX
+#define DTW_EUC_SQRT_APPROX 1
+#endif
+__device__ __forceinline__ float cost_sqrt(float s) {
+#if DTW_EUC_SQRT_APPROX
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(s));
+    return r;
+#else
+    return __fsqrt_rn(s);
+#endif
 }
 
 // Exact FP32 -> FP64 widening of a frame cost with integer operations (the
@@ -401,7 +421,7 @@ __device__ __forceinline__ float sumsq8(const float* a, const float* b) {
 template <int DIM>
 __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, DIM>& a, const Frame<KIND_EUC, DIM>& b) {
     if constexpr (DIM % 8 == 0) {
-        return widen_cost(__fsqrt_rn(sumsq8<DIM>(a.v, b.v)));
+        return widen_cost(cost_sqrt(sumsq8<DIM>(a.v, b.v)));
     } else if constexpr (DIM % 2 == 0) {
         float2 s = make_float2(0.f, 0.f);
         const float2 m1 = make_float2(-1.f, -1.f);
@@ -410,7 +430,7 @@ __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, DIM>& a, cons
             const float2 t = __ffma2_rn(make_float2(b.v[e], b.v[e + 1]), m1, make_float2(a.v[e], a.v[e + 1]));
             s = __ffma2_rn(t, t, s);
         }
-        return widen_cost(__fsqrt_rn(s.x + s.y));
+        return widen_cost(cost_sqrt(s.x + s.y));
     } else {
         float s = 0.f;
 #pragma unroll
@@ -418,7 +438,7 @@ __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, DIM>& a, cons
             float t = a.v[e] - b.v[e];
             s = fmaf(t, t, s);
         }
-        return widen_cost(__fsqrt_rn(s));
+        return widen_cost(cost_sqrt(s));
     }
 }
 
@@ -428,7 +448,7 @@ __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, 0>& a, const 
         float t = __ldg(a.p + e) - __ldg(b.p + e);
         s = fmaf(t, t, s);
     }
-    return widen_cost(__fsqrt_rn(s));
+    return widen_cost(cost_sqrt(s));
 }
 
 template <int DIM>
@@ -458,7 +478,7 @@ __device__ __forceinline__ double frame_cost(const Frame<KIND_EUC, DIM>& a, cons
         y[e + 2] = t.z;
         y[e + 3] = t.w;
     }
-    return widen_cost(__fsqrt_rn(sumsq8<DIM>(a.v, y)));
+    return widen_cost(cost_sqrt(sumsq8<DIM>(a.v, y)));
 }
 
 // Out rows of a sweep (its window of split rows), nout rows of Q columns:
