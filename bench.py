@@ -392,6 +392,7 @@ def run_ours(args):
         "config": {"workload": WORKLOADS[args.workload][0], "M": M, "N": N, "pairs_per_rank": 1,
                    "parallelism": f"replicas{ws}", "l2": "flushed between steps (256 MiB write outside the events)",
                    "autotuned": None if tuned is None else {"sweep_variant": tuned["variant"],
+                                                           "split_windows": tuned["windows"],
                                                            "base_area": tuned["base_area"],
                                                            "table": tuned["table"]},
                    "fixed": None if args.variant is None and args.base_area is None else
@@ -515,7 +516,7 @@ def measure_batch(steps: int, warmup: int, tune: bool = True, check: bool = True
                                     f"profiles/pipe_rates.md) x {mhz:.0f} MHz ({src}); one FP64 add per processed cell"},
         "max_rel_err_vs_oracle": err, "oracle_source": "tests/golden/batch_chroma_256.txt",
         "l2": "flushed between steps",
-        "autotuned": None if tuned is None else {"base_area": tuned["base_area"]},
+        "autotuned": None if tuned is None else {"base_area": tuned["base_area"], "split_windows": tuned["windows"]},
     }
 
 
@@ -941,6 +942,8 @@ def main():
                     help="integer sweep variant (lane block) to use instead of the autotuner's choice")
     ap.add_argument("--base-area", type=int, default=None,
                     help="base-case cutoff (cells) to use instead of the autotuner's choice")
+    ap.add_argument("--split-windows", type=int, default=None,
+                    help="windows of split rows per box and level, at most (library default 7; 1: one split row)")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the level loop from the host (the same kernels; profilers list every launch)")
     ap.add_argument("--pipes", action="store_true",
@@ -950,6 +953,9 @@ def main():
         return run_pipes()
     if args.impl == "reference":
         return run_reference(args)
+    if args.split_windows is not None:
+        import paper_2008_02734_b300 as dtw
+        dtw.set_option(dtw.OPT_SPLIT_WINDOWS, args.split_windows)
     if args.workload != "int_pair" and (args.no_graph or args.base_area is not None):
         import paper_2008_02734_b300 as dtw
         if args.no_graph:

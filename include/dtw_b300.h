@@ -323,13 +323,24 @@ enum dtw_option {
     DTW_OPT_EDIT_GAP = 8,     /* DTW_EDIT_I32: cost of an insertion or a deletion, 0 .. 2^20 (default 1) */
     DTW_OPT_NOALLOC_EPOCH = 9, /* test hook: the next dtw_cost_noalloc call starts its boundary-word epochs at
                                   this value, 0 .. 2^32-1 (exercises the restart near the 32-bit limit) */
-    DTW_OPT_FUSED_SPLIT = 10  /* where dtw_align / dtw_align_batch run each level's split (the argmin of
+    DTW_OPT_FUSED_SPLIT = 10, /* where dtw_align / dtw_align_batch run each level's split (the argmin of
                                  F + B - C, Lemma 2): 1 (default) in the sweep kernel, whose blocks take split
                                  items once the sweep tickets are gone, for float kinds and for batches of
                                  two or more pairs, and in a separate launch for a single integer or edit
                                  pair (measured faster for it); 2 always in the sweep kernel; 0 always in a
                                  separate launch.  The BF16 cost form always uses the separate launch.
                                  Results are the same in every case. */
+    DTW_OPT_SPLIT_WINDOWS = 11 /* windows of split rows per box and recursion level, at most: 1 .. 15
+                                 (default 7).  Lemma 1 holds for any row that every warping path crosses,
+                                 so each box's forward and backward sweeps may end on several equally
+                                 spaced split rows (windows of 9 rows for the integer and edit kinds, one
+                                 row for the others) and each window fixes one cell of the optimal path
+                                 (Lemma 2): the box splits into up to that many + 1 pieces.  1 is the
+                                 paper's single middle split.  Fewer levels and a shorter dependency
+                                 chain per alignment for about the same work (2MN cells); the window
+                                 count shrinks on boxes too small for it.  Integer and edit paths are
+                                 the same for every value; float costs agree within rounding.  Takes
+                                 effect for serving engines started afterwards. */
 };
 DTW_API int dtw_set_option(int32_t key, int64_t value);
 

@@ -36,6 +36,7 @@ OPT_TIMING, OPT_BASE_AREA, OPT_SPIN_LIMIT, OPT_SKIP_PUBLISH, OPT_GRAPH, OPT_SWEE
 OPT_EDIT_SUB, OPT_EDIT_GAP = 7, 8
 OPT_NOALLOC_EPOCH = 9  # test hook: the next dtw_cost_noalloc call's first boundary-word epoch
 OPT_FUSED_SPLIT = 10  # 0 separate split launch, 1 (default) float kinds and batches in the sweep kernel, 2 always
+OPT_SPLIT_WINDOWS = 11  # windows of split rows per box and level, at most (1: the paper's single split; default 7)
 EDIT_I32 = 2  # weighted edit distance of int32 symbol sequences (cost kind)
 
 

@@ -1,30 +1,37 @@
-"""Autotuner of the sweep's lane block and of the base-case cutoff.
+"""Autotuner of the sweep's lane block, the split windows and the base-case cutoff.
 
-The integer sweep is compiled in three lane blocks (4, 2 or 8 rows per lane, 4
-columns per step: DTW_OPT_SWEEP_VARIANT 0, 1, 2) and the recursion hands boxes to
-the full-table base case below a cutoff area (DTW_OPT_BASE_AREA).  Neither
-changes a result -- the integer path is the canonical one at any cutoff, and the
-lane block only reorders the same cell updates -- but both change the time: a
-thinner band means more bands (more warps at the top levels, a longer pipeline
-ramp), a larger cutoff means fewer, cheaper levels at the bottom.  ``tune`` times
-dtw_align on a seeded synthetic pair of the caller's size for every candidate
-and applies the fastest.
+The integer sweep is compiled in four lane blocks (4, 2 or 8 rows per lane, 4
+columns per step, and 4 rows with fully unrolled step groups:
+DTW_OPT_SWEEP_VARIANT 0..3), each box of a level may be split on up to 1, 7 or
+15 windows of split rows (DTW_OPT_SPLIT_WINDOWS), and the recursion hands boxes
+to the full-table base case below a cutoff area (DTW_OPT_BASE_AREA).  None of
+them changes a result -- the integer path is the canonical one at any cutoff
+and split, and the lane block only reorders the same cell updates -- but all
+change the time: a thinner band means more bands (more warps at the top levels,
+a longer pipeline ramp), more windows fewer levels with longer sweeps, a larger
+cutoff fewer, cheaper levels at the bottom.  ``tune`` times dtw_align on a
+seeded synthetic pair of the caller's size for every candidate and applies the
+fastest.
 """
 from __future__ import annotations
 
 import itertools
 
-from . import OPT_BASE_AREA, OPT_SWEEP_VARIANT, align, set_option
+from . import OPT_BASE_AREA, OPT_SPLIT_WINDOWS, OPT_SWEEP_VARIANT, align, set_option
 from . import synth
 
 VARIANTS = (0, 1, 2, 3)
+WINDOWS = (1, 7, 15)
 BASE_AREAS = (4096, 16384, 32768)
+DEFAULT_WINDOWS = 7
 
 
-def tune(M: int, N: int, *, variants=VARIANTS, base_areas=BASE_AREAS, reps: int = 3, apply: bool = True) -> dict:
-    """Times every (variant, base area) on an integer pair of M x N frames with
-    CUDA events (median of ``reps`` after one warm-up) and returns
-    {"variant", "base_area", "ms", "table"}; with ``apply`` the fastest is set."""
+def tune(M: int, N: int, *, variants=VARIANTS, windows=WINDOWS, base_areas=BASE_AREAS, reps: int = 3,
+         apply: bool = True) -> dict:
+    """Times every (variant, windows, base area) on an integer pair of M x N
+    frames with CUDA events (median of ``reps`` after one warm-up) and returns
+    {"variant", "windows", "base_area", "ms", "table"}; with ``apply`` the
+    fastest is set."""
     import torch
 
     X, Y = synth.int_pair(12345, M, N)
@@ -32,8 +39,9 @@ def tune(M: int, N: int, *, variants=VARIANTS, base_areas=BASE_AREAS, reps: int 
     path = torch.empty((M + N - 1, 2), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     table = []
-    for v, a in itertools.product(variants, base_areas):
+    for v, w, a in itertools.product(variants, windows, base_areas):
         set_option(OPT_SWEEP_VARIANT, v)
+        set_option(OPT_SPLIT_WINDOWS, w)
         set_option(OPT_BASE_AREA, a)
         align(Xd, Yd, path_out=path)
         ms = []
@@ -45,26 +53,31 @@ def tune(M: int, N: int, *, variants=VARIANTS, base_areas=BASE_AREAS, reps: int 
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         ms.sort()
-        table.append({"variant": v, "base_area": a, "ms": ms[len(ms) // 2]})
+        table.append({"variant": v, "windows": w, "base_area": a, "ms": ms[len(ms) // 2]})
     best = min(table, key=lambda r: r["ms"])
     set_option(OPT_SWEEP_VARIANT, best["variant"] if apply else 0)
+    set_option(OPT_SPLIT_WINDOWS, best["windows"] if apply else DEFAULT_WINDOWS)
     set_option(OPT_BASE_AREA, best["base_area"] if apply else 16384)
-    return {"variant": best["variant"], "base_area": best["base_area"], "ms": best["ms"], "table": table}
+    return {"variant": best["variant"], "windows": best["windows"], "base_area": best["base_area"], "ms": best["ms"],
+            "table": table}
 
 
-def tune_batch(Xs, Ys, *, base_areas=BASE_AREAS, reps: int = 2, apply: bool = True, **align_kw) -> dict:
-    """The base-case cutoff for a batch: times align_batch on the caller's own
-    pairs (device tensors) for every candidate area (median of ``reps`` after
-    one warm-up) and returns {"base_area", "ms", "table"}; with ``apply`` the
-    fastest is set.  Results do not depend on the cutoff (integer paths are
-    canonical; float paths are optimal within the float tolerance)."""
+def tune_batch(Xs, Ys, *, base_areas=BASE_AREAS, windows=(1, 3, 7), reps: int = 2, apply: bool = True,
+               **align_kw) -> dict:
+    """The base-case cutoff and split windows for a batch: times align_batch on
+    the caller's own pairs (device tensors) for every candidate (median of
+    ``reps`` after one warm-up) and returns {"base_area", "windows", "ms",
+    "table"}; with ``apply`` the fastest is set.  Results do not depend on
+    either (integer paths are canonical; float paths are optimal within the
+    float tolerance)."""
     import torch
 
     from . import align_batch
 
     stream = torch.cuda.current_stream()
     table = []
-    for a in base_areas:
+    for w, a in itertools.product(windows, base_areas):
+        set_option(OPT_SPLIT_WINDOWS, w)
         set_option(OPT_BASE_AREA, a)
         align_batch(Xs, Ys, **align_kw)
         ms = []
@@ -76,7 +89,8 @@ def tune_batch(Xs, Ys, *, base_areas=BASE_AREAS, reps: int = 2, apply: bool = Tr
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         ms.sort()
-        table.append({"base_area": a, "ms": ms[len(ms) // 2]})
+        table.append({"windows": w, "base_area": a, "ms": ms[len(ms) // 2]})
     best = min(table, key=lambda r: r["ms"])
+    set_option(OPT_SPLIT_WINDOWS, best["windows"] if apply else DEFAULT_WINDOWS)
     set_option(OPT_BASE_AREA, best["base_area"] if apply else 16384)
-    return {"base_area": best["base_area"], "ms": best["ms"], "table": table}
+    return {"base_area": best["base_area"], "windows": best["windows"], "ms": best["ms"], "table": table}

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -33,6 +34,7 @@ struct Ctx {
     long long base_area = 16384;
     int spin_limit = 1 << 22;
     int fused_split = 1;  // the split in the sweep kernel: 0 never, 1 float kinds and batches, 2 always (not BF16)
+    int split_windows = kSplitWindowsDefault;  // windows of split rows per box at most
     long long skip_publish = -1;
     uint32_t epoch = 1;  // next boundary-word epoch; increases across calls
     int num_sms = 0;
@@ -262,7 +264,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
             if (!pdev[b]) path_pairs += M[b] + N[b] - 1;
         }
     }
-    const Layout L = make_layout(B, sumM, sumN, feat_bytes, path_pairs);
+    const Layout L = make_layout(B, sumM, sumN, feat_bytes, path_pairs, c.split_windows, split_win_rows(kind));
     void* wsv = nullptr;
     int rc = workspace(c, L.total, &wsv);
     if (rc) return rc;
@@ -419,6 +421,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
                     L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
         pa.tmap = d_tmap;
         pa.prog = d_prog;
+        pa.nwin = c.split_windows;
         pa.cap_tickets = L.cap_tickets;
         pa.map_min = c.num_sms;
         e = launch_plan(pa, st);
@@ -445,12 +448,13 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         pn.cap_tickets = L.cap_tickets;
         pn.map_min = c.num_sms;
         pn.prog = d_prog;
+        pn.nwin = c.split_windows;
         sa.prog = d_prog;
         sa.split = sp;
         const std::vector<long long> key{(long long)(uintptr_t)ws, (long long)L.total, L.cap_box, L.cap_base,
                                          L.cap_sweeps, L.cap_buf, L.cap_out, L.cap_items, kind, d, base_area,
                                          c.spin_limit, c.skip_publish, c.num_sms, max_levels, (long long)L.ctl,
-                                         c.variant, d_prog != nullptr};
+                                         c.variant, d_prog != nullptr, c.split_windows};
         cudaGraphExec_t ex = nullptr;
         int grc = level_graph(c, key, sa, sp, pn, d_ctl, kind, d, max_levels, &ex);
         if (grc != DTW_OK) return grc;
@@ -489,6 +493,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
                         L.cap_sweeps, L.cap_buf, L.cap_out, d_boxdone, L.cap_items, false, nullptr};
             pa.tmap = d_tmap;
             pa.prog = d_prog;
+            pa.nwin = c.split_windows;
             pa.cap_tickets = L.cap_tickets;
             pa.map_min = c.num_sms;
             if (e == cudaSuccess) e = launch_plan(pa, st);
@@ -768,6 +773,14 @@ int run_plain(Ctx& c, const void* X, int64_t M, const void* Y, int64_t N, int d,
 
 }  // namespace
 
+namespace dtwb {
+namespace {
+std::atomic<int> g_split_windows{kSplitWindowsDefault};
+}
+int split_windows_option() { return g_split_windows.load(std::memory_order_relaxed); }
+void set_split_windows_option(int windows) { g_split_windows.store(windows, std::memory_order_relaxed); }
+}  // namespace dtwb
+
 // ================================================================= C ABI
 
 extern "C" {
@@ -852,6 +865,7 @@ int dtw_set_arena(void* device_ptr, uint64_t bytes) {
 
 size_t dtw_footprint(int64_t M, int64_t N, int32_t d, int32_t cost_kind) {
     if (M < 1 || N < 1 || d < 1) return 0;
+    const int windows = split_windows_option();
     if (cost_kind & DTW_PLAIN_F64) {
         return align_up((size_t)(M + N) * d * 4) + 3 * 256 + align_up(8 * (size_t)(M + N)) +
                plain_workspace_bytes(M, N);
@@ -859,11 +873,12 @@ size_t dtw_footprint(int64_t M, int64_t N, int32_t d, int32_t cost_kind) {
     if ((cost_kind & 0xff) == DTW_EDIT_I32) {  // the node grid over the padded sequences
         const Layout L = make_layout(1, M + 1, N + 1,
                                      (long long)align_up((size_t)(M + 2) * 4) + (long long)align_up((size_t)(N + 2) * 4),
-                                     M + N + 1);
+                                     M + N + 1, windows, split_win_rows(KIND_EDIT));
         return L.total;
     }
+    const int kind = (cost_kind & 0xff) == DTW_ABS_I32 ? KIND_ABS : KIND_EUC;
     const Layout L = make_layout(1, M, N, (long long)align_up((size_t)M * d * 4) + (long long)align_up((size_t)N * d * 4),
-                                 M + N - 1);
+                                 M + N - 1, windows, split_win_rows(kind));
     return L.total;
 }
 
@@ -972,6 +987,11 @@ int dtw_set_option(int32_t key, int64_t value) {
         case DTW_OPT_FUSED_SPLIT:
             if (value < 0 || value > 2) return DTW_EINVAL;
             c.fused_split = (int)value;
+            return DTW_OK;
+        case DTW_OPT_SPLIT_WINDOWS:
+            if (value < 1 || value > kSplitWinMax) return DTW_EINVAL;
+            c.split_windows = (int)value;
+            set_split_windows_option((int)value);
             return DTW_OK;
         case DTW_OPT_NOALLOC_EPOCH:
             if (value < 0 || value > 0xFFFFFFFFLL) return DTW_EINVAL;

@@ -89,11 +89,24 @@ struct Box {
 #define DTW_SPLIT_CHUNK 256
 #endif
 constexpr int kSplitChunk = DTW_SPLIT_CHUNK;
+// Columns of one split work item of a box with nw windows of split rows: the
+// item covers one window, nw chunks wide, so that a box has about as many items
+// as with a single window.
+__host__ __device__ __forceinline__ int split_item_cols(int nw) { return kSplitChunk * (nw > 1 ? nw : 1); }
 
-// Half-width of the window of split rows written by forward/backward sweeps of
-// integer boxes: rows r-kSplitHalo .. r+kSplitHalo around the middle row r.
+// Half-width of a window of split rows written by forward/backward sweeps of
+// integer boxes: rows r-kSplitHalo .. r+kSplitHalo around a split row r.
 constexpr int kSplitHalo = 4;
 constexpr int kSplitRowsMax = 2 * kSplitHalo + 1;
+
+// Several split rows per box (Lemma 1 holds for each of them): a box's two sweeps
+// may end on up to kSplitWinMax equally spaced windows of split rows, at most
+// kOutRowsMax rows in all, each window kWinGap rows or more from the next (more
+// than the rows a lane of any sweep variant owns, so that a lane's rows meet one
+// window at most).
+constexpr int kSplitWinMax = 15;
+constexpr int kOutRowsMax = 64;
+constexpr int kWinGap = 8;
 
 // One wavefront sweep over frame rows [0, rows) x frame columns [0, Q).
 struct Sweep {
@@ -106,8 +119,11 @@ struct Sweep {
     int32_t rows;        // frame rows swept (0: empty slot)
     int32_t Q;           // frame columns
     int32_t nblk;        // column blocks of the sweep's kernel variant
-    int32_t out_row0;    // first frame row copied to the out pool
-    int32_t nout;        // rows copied (0: none)
+    int32_t out_row0;    // first frame row copied to the out pool (first row of the first window)
+    int32_t nout;        // rows copied (0: none): onw windows of owin rows
+    int32_t onw;         // windows of split rows
+    int32_t owin;        // rows per window
+    int32_t ospace;      // frame rows from one window's first row to the next one's
     int32_t tag_row;     // frame row where split tags start (-1: untagged sweep)
     int32_t nbands;
     uint32_t epoch0;     // band b stamps its boundary words with epoch0 + b + 1
@@ -494,6 +510,31 @@ template <typename Acc>
 __host__ __device__ __forceinline__ long long out_index(int m, int q, int nout) {
     constexpr int C = out_chunk<Acc>();
     return ((long long)(q / C) * nout + m) * C + q % C;
+}
+
+// Out-row number of frame row p of a sweep (window t, row e of it: t*owin + e),
+// or -1 where p holds no split row.
+__host__ __device__ __forceinline__ int out_row_of(const Sweep& s, int p) {
+    if (s.nout <= 0) return -1;
+    const int d = p - s.out_row0;
+    if (d < 0) return -1;
+    const int t = d / s.ospace, e = d - t * s.ospace;
+    return (t < s.onw && e < s.owin) ? t * s.owin + e : -1;
+}
+// Frame row of out row m of a sweep.
+__host__ __device__ __forceinline__ int out_frame_row(const Sweep& s, int m) {
+    const int t = m / s.owin;
+    return s.out_row0 + t * s.ospace + (m - t * s.owin);
+}
+// Whether frame rows [lo, hi) hold a split row of the sweep.
+__host__ __device__ __forceinline__ bool out_rows_meet(const Sweep& s, int lo, int hi) {
+    if (s.nout <= 0) return false;
+    const int a = max(lo - s.out_row0, 0);
+    const int t = a / s.ospace;
+    if (t >= s.onw) return false;
+    // the first window that ends after a: window t if a lies in it, else t + 1
+    const int w = (a - t * s.ospace < s.owin) ? t : t + 1;
+    return w < s.onw && s.out_row0 + w * s.ospace < hi;
 }
 
 // Cost of global cell (i, j) of a pair, for the split and checks.

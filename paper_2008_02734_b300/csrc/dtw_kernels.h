@@ -25,7 +25,7 @@ struct SplitArgs {
     long long base_area;
     int cap_next, cap_base;
     int* box_done;    // per-box count of finished work items
-    void* partials;   // per work item: kSplitRowsMax partial row minima (16 B each)
+    void* partials;   // per work item: kSplitRowsMax partial row minima (16 B each) of its window
     int n_items;      // work items of the level (as planned); < 0: read ctl->n_items on the device
     int num_sms;
 };
@@ -87,6 +87,7 @@ struct PlanArgs {
     long long map_min = 0;     // levels with at most this many plain tickets skip the map (all
                                // their tickets run at once, so their order does not matter)
     int* prog = nullptr;       // non-null: reset the sweeps' split-row progress words (fused split)
+    int nwin = 1;              // windows of split rows per box at most (odd; 1: one split row per box)
 };
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st);
 
@@ -133,6 +134,12 @@ cudaError_t launch_mark_pairs(const Box* boxes, const LevelCtl* ctl, int32_t* fl
 // Graph-driven level loop: sets the loop's condition to "another level": boxes
 // planned, no device error and fewer than max_levels levels so far.
 cudaError_t launch_level_cond(LevelCtl* ctl, cudaGraphConditionalHandle h, int max_levels, cudaStream_t st);
+
+// Windows of split rows per box at most (DTW_OPT_SPLIT_WINDOWS), as read by the
+// serving engines and dtw_footprint (api.cu keeps it).
+constexpr int kSplitWindowsDefault = 7;
+int split_windows_option();
+void set_split_windows_option(int windows);
 
 // Serving engine (serve.cu): device memory its groups may take from now on.
 void serve_set_budget(uint64_t bytes);

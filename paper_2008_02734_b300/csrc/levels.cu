@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         const bool valid = s < nsw;
         Sweep sw = {};
         long long nb = 0, nbuf = 0, nout = 0, nit = 0;
+        int wbands = 0;  // bands holding split rows (the fused split waits for them)
         if (valid) {
             const int bi = s / nslot, dir = s % nslot;
             const Box b = a.boxes[bi];
@@ -139,20 +140,54 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             sw.tag_row = -1;
             sw.nout = 0;
             sw.out_row0 = 0;
+            sw.onw = 0;
+            sw.owin = 1;
+            sw.ospace = 1;
             if (a.mode == MODE_COST) {
                 sw.rows = g.P;
             } else if (b.flags & BOX_TAG) {
                 sw.rows = dir == 0 ? g.P : 0;
                 sw.out_row0 = g.r;
                 sw.nout = dir == 0 ? 1 : 0;
+                sw.onw = sw.nout;
                 sw.tag_row = g.r;
+                wbands = sw.nout;
             } else {
-                // the window stays inside rows 1..P-2, so both children are
-                // strictly shorter than the box along the cut side
+                // the windows stay inside rows 1..P-2, so every child is strictly
+                // shorter than the box along the cut side
                 const int h = max(0, min(a.halo, min(g.r - 1, g.P - 2 - g.r)));
-                sw.rows = dir == 0 ? g.r + h + 1 : g.P - g.r + h;
-                sw.nout = 2 * h + 1;  // both halves end on rows r-h..r+h
-                sw.out_row0 = sw.rows - sw.nout;
+                const int ow = 2 * h + 1;
+                // nw windows of split rows centred on r + (t - c) S, t = 0..nw-1,
+                // c = (nw-1)/2, S = P/(nw+1): the middle one on row r, the
+                // children nw+1 pieces of about P/(nw+1) rows.  The forward sweep
+                // runs to the last window, the backward one to the first.
+                int nw = 1, S = ow, r0 = g.r, rl = g.r;
+                for (int cand = (min(a.nwin, kSplitWinMax) - 1) | 1; cand > 1; cand -= 2) {
+                    const int cs = g.P / (cand + 1), cc = (cand - 1) / 2;
+                    const int c0 = g.r - cc * cs, cl = g.r + (cand - 1 - cc) * cs;
+                    if (cand * ow <= kOutRowsMax && cs - ow >= kWinGap && c0 - h >= 1 && cl + h <= g.P - 2) {
+                        nw = cand;
+                        S = cs;
+                        r0 = c0;
+                        rl = cl;
+                        break;
+                    }
+                }
+                sw.rows = dir == 0 ? rl + h + 1 : g.P - r0 + h;
+                sw.onw = nw;
+                sw.owin = ow;
+                sw.ospace = S;
+                sw.nout = nw * ow;
+                // both sweeps end on their last window (rows r_t-h..r_t+h of every
+                // window, in each sweep's own frame order)
+                sw.out_row0 = dir == 0 ? r0 - h : g.P - 1 - (rl + h);
+                for (int t = 0, last = -1; t < nw; ++t) {
+                    const int w0 = sw.out_row0 + t * S;
+                    for (int bb = max(w0 / a.BR, last + 1); bb <= (w0 + ow - 1) / a.BR; ++bb) {
+                        ++wbands;
+                        last = bb;
+                    }
+                }
             }
             sw.nblk = sw.rows > 0 ? (g.Q + a.U - 1) / a.U : 0;
             sw.ostride = sw.nblk * a.U;
@@ -189,7 +224,8 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             nout = (long long)sw.nout * sw.ostride;
             // split work: the forward slot of an aligned box owns the box's column chunks
             if (a.mode != MODE_COST && dir == 0) {
-                nit = (b.flags & BOX_TAG) ? 1 : (g.Q + kSplitChunk - 1) / kSplitChunk;
+                const int ic = split_item_cols(sw.onw);
+                nit = (b.flags & BOX_TAG) ? 1 : (long long)sw.onw * ((g.Q + ic - 1) / ic);
                 if (a.box_done) a.box_done[bi] = 0;
             }
             sw.nitems = (int)nit;
@@ -208,11 +244,10 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             if (s < a.cap_sweeps) {
                 a.sweeps[s] = sw;
                 if (a.prog) {
-                    // split-row progress: a second word only when two bands hold the rows
+                    // split-row progress: bands holding split rows that have ended, of wbands
                     int* pw = a.prog + (size_t)s * kProgWords;
-                    const bool two = sw.nout > 0 && sw.out_row0 / a.BR != (sw.out_row0 + sw.nout - 1) / a.BR;
                     pw[0] = 0;
-                    pw[1] = two ? 0 : INT_MAX;
+                    pw[1] = wbands;
                     pw[2] = 0;
                 }
             }
@@ -312,12 +347,13 @@ cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st) {
 // Work items of a level: every column chunk of every box's split rows (one
 // item for a tagged box).  Each item writes its partial minima; the item that
 // finishes a box last (per-box counter) merges them and emits the children.
+// Two blocks per SM for the integer kinds (their item work fits in 128 registers).
 template <int KIND, int DIM>
-__global__ void __launch_bounds__(256) split_kernel(SplitArgs a) {
+__global__ void __launch_bounds__(256, int_kind(KIND) ? 2 : 1) split_kernel(SplitArgs a) {
     // after a planning or sweep error the sweep outputs are not valid
     if (ld_relaxed(&a.ctl->err) != ERR_NONE) return;
     const int n_items = a.n_items >= 0 ? a.n_items : a.ctl->n_items;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) split_item<KIND, DIM>(a, it, 0, nullptr);
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) split_item<KIND, DIM>(a, it, nullptr);
 }
 
 cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {

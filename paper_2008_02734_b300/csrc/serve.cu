@@ -153,15 +153,18 @@ struct Engine {
     long long base_area = 16384;
     int spin_limit = 1 << 22;
 
+    int windows = kSplitWindowsDefault;  // windows of split rows per box at most (fixed at init)
+
     int init(size_t arena, int sms) {
         num_sms = sms;
+        windows = split_windows_option();
         // arena: level scratch (about 1.75 KB per unit of M+N) + staging bytes + fixed parts
         const size_t fixed = (size_t)kSlots * (sizeof(PairDesc) + sizeof(PairRes) + sizeof(Box) + 3 * 4 + 16) + (1 << 20);
         if (arena < fixed + (64 << 20)) arena = fixed + (64 << 20);
         const size_t stage = (arena - fixed) * 2 / 5;
         S_max = (long long)((arena - fixed - stage) / 1800);
         for (;;) {
-            L = make_layout(kSlots, S_max, 0, (long long)stage, 0);
+            L = make_layout(kSlots, S_max, 0, (long long)stage, 0, windows, split_win_rows(kind));
             if (L.total + fixed <= arena || S_max < 1024) break;
             S_max = S_max * 15 / 16;
         }
@@ -390,6 +393,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
         pa.tmap = reinterpret_cast<int2*>(ws + L.tmap);
         pa.cap_tickets = L.cap_tickets;
         pa.map_min = num_sms;
+        pa.nwin = windows;
         e = launch_plan(pa, st);
         SweepArgs sa{d_sweeps, ctl(), reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres,
                      d, spin_limit, -1};
@@ -406,6 +410,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
     pn.tmap = reinterpret_cast<int2*>(ws + L.tmap);
     pn.cap_tickets = L.cap_tickets;
     pn.map_min = num_sms;
+    pn.nwin = windows;
     if (e == cudaSuccess) e = launch_plan(pn, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_flags, 0, 4 * kSlots, st);
     if (e == cudaSuccess) e = launch_mark_pairs(nxt, ctl(), d_flags, st);

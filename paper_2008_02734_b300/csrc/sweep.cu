@@ -102,16 +102,6 @@ constexpr int URS = 64;                  // slots (column blocks) of a row ring
 #ifndef DTW_LOADER_DRAIN
 #define DTW_LOADER_DRAIN 1
 #endif
-// Steps between a split-row band's progress publications (fused split): a power
-// of two, or 0 (default) for only at the band's end.  Publishing along the way
-// lets split items start while the window bands still run, but each publication
-// is a gpu-scope fence in the level's last band, and the check alone slowed that
-// band's steps: end-only was measured fastest (integer pair 2.34 ms against 2.46
-// with a publication every 64 steps).
-#ifndef DTW_PROG_EVERY
-#define DTW_PROG_EVERY 0
-#endif
-
 #ifndef DTW_EUC_YPREFETCH
 #define DTW_EUC_YPREFETCH 0
 #endif
@@ -552,7 +542,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     const int rows = sp->rows, Q = sp->Q, nblk = sp->nblk;
     const int rbase = sp->rbase, rstep = sp->rstep;
     const void* rowseq = sp->rowseq;
-    const int out_row0 = sp->out_row0, nout = sp->nout, tag_row = sp->tag_row;
+    const int nout = sp->nout, tag_row = sp->tag_row;
     const int32_t esub = sp->esub, egap = sp->egap, ematch = sp->ematch;  // edit kinds
     const bool lfloor = sp->floor != 0;                                      // KIND_LOCAL
     const uint32_t ep_out = sp->epoch0 + (uint32_t)band + 1u;
@@ -565,15 +555,21 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     // the half sweeps of an aligned box hand their last row over as out rows
     const bool need_end = nout == 0 || tag_row >= 0;
     const bool has_above = band > 0;
-    // out rows of this lane: row k is out row mo0 + k where that lies in
-    // [0, nout); in the out-row layout (out_index) the lane's rows of column
-    // block cb start at element mo0 * OC + cb * U * nout, row k OC further each
+    // out rows of this lane: its rows meet one window of split rows at most
+    // (windows are more than R rows apart), so valid row k is out row mo0 + k; in
+    // the out-row layout (out_index) the lane's rows of column block cb start at
+    // element mo0 * OC + cb * U * nout, row k OC further each
     constexpr int OC = out_chunk<Acc>();
     static_assert(U % OC == 0, "a lane's column block covers whole out-row chunks");
-    const int mo0 = p0 - out_row0;
+    static_assert(R <= kWinGap, "a lane's rows must not reach two windows of split rows");
+    int mo0 = 0;
     bool ovalid[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) ovalid[k] = SPECIAL && (unsigned)(mo0 + k) < (unsigned)nout;
+    for (int k = R - 1; k >= 0; --k) {
+        const int m = SPECIAL ? out_row_of(*sp, p0 + k) : -1;
+        ovalid[k] = m >= 0;
+        if (m >= 0) mo0 = m - k;
+    }
 
     uint32_t* rin = sm.uring[g];
     constexpr int kG = group_of<KIND>();
@@ -915,30 +911,13 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
         }
     };
 
-    // fused split: a band holding split rows publishes, every DTW_PROG_EVERY steps
-    // (0: only) and at its end, how many column blocks of them are stored (all its lanes up to the last
-    // one holding such a row have passed them); every lane fences its own stores
-    // before the warp barrier, lane 0 then writes the word (gpu scope)
-    int* pword = nullptr;
-    int l_last = 0;
-    if constexpr (SPECIAL) {
-        const int b_lo = band * 32 * R;
-        if (A.prog != nullptr && nout > 0 && out_row0 < b_lo + 32 * R && out_row0 + nout > b_lo) {
-            pword = A.prog + (size_t)sweep_idx * kProgWords + (band == out_row0 / (32 * R) ? 0 : 1);
-            l_last = min(31, (out_row0 + nout - 1 - b_lo) / R);
-        }
-    }
-    auto publish = [&](int* w, int v) {
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(w), "r"(v) : "memory");
-    };
+    // fused split: a band holding split rows counts itself in the sweep's
+    // progress word at its end (every lane fences its own stores before the warp
+    // barrier, lane 0 then adds, gpu scope)
     sync_group(0);
     fetch(0);
     for (int s0 = 0; s0 < nsteps; s0 += KC) {
         if (s0 > 0) sync_group(s0);
-        if (SPECIAL && DTW_PROG_EVERY > 0 && pword != nullptr && (s0 & (DTW_PROG_EVERY - 1)) == 0 && s0 > l_last)
-            publish(pword, min(nblk, s0 - l_last));
         if (TC && (s0 & 15) == 0 && s0 < nblk) build_tile(s0 >> 4);
         if (s0 >= 31 && s0 + KC < nblk) {
             if constexpr (FULL) {
@@ -1002,10 +981,18 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
             else r->end_f = to_double(end_v);
             r->end_tag = end_t;
         }
-        if (pword != nullptr) publish(pword, nblk);
-        // the band holding the sweep's last row: its last cell is recorded
-        if (A.prog != nullptr && (rows - 1) / (32 * R) == band)
-            publish(A.prog + (size_t)sweep_idx * kProgWords + 2, 1);
+        if (A.prog != nullptr) {
+            int* pw = A.prog + (size_t)sweep_idx * kProgWords;
+            const bool holds = out_rows_meet(*sp, band * 32 * R, (band + 1) * 32 * R);
+            // the band holding the sweep's last row: its last cell is recorded
+            const bool last = (rows - 1) / (32 * R) == band;
+            if (holds || last) {
+                __threadfence();
+                __syncwarp();
+                if (lane == 0 && holds) asm volatile("red.relaxed.gpu.global.add.s32 [%0], 1;" ::"l"(pw) : "memory");
+                if (lane == 0 && last) asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(pw + 2), "r"(1) : "memory");
+            }
+        }
     }
     if (lane == 0 && ws.waits) {
         atomicAdd(&A.ctl->resyncs, ws.waits);
@@ -1365,7 +1352,7 @@ __device__ __noinline__ void split_phase(const SweepArgs& A, SM& sm) {
         const bool stop = sm.stop != 0;
         __syncthreads();
         if (stop || it >= n_items) break;
-        split_item<KIND, DIM, true>(a, it, U, A.prog, A.spin_limit);
+        split_item<KIND, DIM, true>(a, it, A.prog, A.spin_limit);
     }
 }
 
@@ -1506,8 +1493,7 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
                 const bool to_global = below && warp + 1 == kG;
                 const int BR = 32 * R;
                 const int b_lo = band * BR, b_hi = b_lo + BR;  // band rows [b_lo, b_hi)
-                const bool special =
-                    (sp->nout > 0 && sp->out_row0 < b_hi && sp->out_row0 + sp->nout > b_lo) || (rows - 1 < b_hi);
+                const bool special = out_rows_meet(*sp, b_lo, b_hi) || (rows - 1 < b_hi);
                 if constexpr (!int_kind(KIND)) {
                     run_band_s<KIND, R, U, DIM, NWMAX, 2, 0, true, FULL>(special, sp, si, band, to_ring, to_global, A, sm,
                                                                    warp, tcw);

@@ -53,6 +53,9 @@ def test_strerror_and_options(lib):
     assert lib.lib.dtw_set_option(999, 1) == lib.EINVAL
     assert lib.lib.dtw_set_option(lib.OPT_BASE_AREA, 2) == lib.EINVAL
     assert lib.lib.dtw_set_option(lib.OPT_BASE_AREA, 1 << 20) == lib.EINVAL
+    for bad in (0, 16, -1):
+        assert lib.lib.dtw_set_option(lib.OPT_SPLIT_WINDOWS, bad) == lib.EINVAL
+    assert lib.lib.dtw_set_option(lib.OPT_SPLIT_WINDOWS, 7) == 0
 
 
 def test_pipe_rates_checks_arguments_on_host(lib):
@@ -82,5 +85,7 @@ def test_footprint_is_linear(lib):
     f2 = lib.footprint(20000, 24000)
     f4 = lib.footprint(40000, 48000)
     assert 1.8 < f2 / f1 < 2.2 and 1.8 < f4 / f2 < 2.2
-    assert f2 < 64 << 20  # well under the M*N*4 bytes = 1.9 GB of a full table
+    # well under the M*N*4 bytes = 1.9 GB of a full table (the split rows of up to
+    # seven windows per box are the largest part)
+    assert f2 < 128 << 20
     assert lib.footprint(0, 5) == 0

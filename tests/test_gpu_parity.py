@@ -61,6 +61,7 @@ def _defaults(cuda_device):
     dtw.set_option(dtw.OPT_SPIN_LIMIT, 1 << 22)
     dtw.set_option(dtw.OPT_SKIP_PUBLISH, -1)
     dtw.set_option(dtw.OPT_SWEEP_VARIANT, 0)
+    dtw.set_option(dtw.OPT_SPLIT_WINDOWS, 7)
 
 
 SHAPES = [(1, 1), (1, 9), (9, 1), (2, 2), (3, 7), (7, 13), (33, 65), (64, 64), (65, 63), (100, 37),
@@ -346,9 +347,9 @@ def test_int_sweep_variants_bit_exact(variant, M, N):
 
 def test_autotuner_applies_a_candidate():
     from paper_2008_02734_b300 import autotune
-    r = autotune.tune(1500, 1700, base_areas=(4096, 16384), reps=2)
-    assert r["variant"] in (0, 1, 2, 3) and r["base_area"] in (4096, 16384)
-    assert len(r["table"]) == 8 and all(t["ms"] > 0 for t in r["table"])
+    r = autotune.tune(1500, 1700, windows=(1, 7), base_areas=(4096, 16384), reps=2)
+    assert r["variant"] in (0, 1, 2, 3) and r["base_area"] in (4096, 16384) and r["windows"] in (1, 7)
+    assert len(r["table"]) == 16 and all(t["ms"] > 0 for t in r["table"])
     X, Y = synth.int_pair(4, 2500, 2100)
     check_int(X, Y)
 
@@ -359,7 +360,7 @@ def test_batch_autotuner_applies_a_candidate():
     pairs = [synth.chroma_pair(60 + k, 300 + 40 * k, 280 + 50 * k) for k in range(5)]
     Xs, Ys = [_cuda(x) for x, _ in pairs], [_cuda(y) for _, y in pairs]
     r = autotune.tune_batch(Xs, Ys, base_areas=(4096, 16384))
-    assert r["base_area"] in (4096, 16384) and len(r["table"]) == 2
+    assert r["base_area"] in (4096, 16384) and r["windows"] in (1, 3, 7) and len(r["table"]) == 6
     for (x, y), (p, c) in zip(pairs, dtw.align_batch(Xs, Ys)):
         c_ref = oracle.dtw(x, y)[1]
         assert c == pytest.approx(c_ref, rel=REL_TOL, abs=1e-9)
