@@ -78,8 +78,13 @@ namespace {
 #ifndef DTW_SWEEP_G_EUC
 #define DTW_SWEEP_G_EUC 4
 #endif
+// The BF16 tensor-core form's block always holds four bands: the M = 128 rows of
+// one MMA.
+constexpr int kGEucB = 4;
 template <int KIND>
-__host__ __device__ constexpr int group_of() { return int_kind(KIND) ? DTW_SWEEP_G_INT : DTW_SWEEP_G_EUC; }
+__host__ __device__ constexpr int group_of() {
+    return int_kind(KIND) ? DTW_SWEEP_G_INT : (KIND == KIND_EUCB ? kGEucB : DTW_SWEEP_G_EUC);
+}
 template <int KIND>
 __host__ __device__ constexpr int threads_of() {
     // + the loader warp; the BF16 tensor-core form adds its tile warp
@@ -462,10 +467,13 @@ __device__ __forceinline__ void tc_ld32(uint32_t ta, float* v) {
 // cannot deadlock; a lower band that runs late (its waits on the band above
 // make it lag by some 50 steps rather than 40) then holds back the first
 // reader.  With two warps per block (the integer kind, 16-byte slots) the
-// region is 512 slots and a stream gets 512 (two readers) or 256 (one).
-__host__ __device__ constexpr int kYSlotsOf(int G) { return G > 4 ? 1024 : (G > 2 ? 320 : 512); }
-__host__ __device__ constexpr int yslots(int G, int w) {
-    return G <= 2 ? (w >= 2 ? 512 : 256) : (w >= 5 ? 512 : (w >= 3 ? 256 : (w == 2 ? 128 : 64)));
+// region is 512 slots and a stream gets 512 (two readers) or 256 (one); with two
+// warps or fewer and large slots (more than 256 bytes) the least room applies.
+__host__ __device__ constexpr int kYSlotsOf(int G, bool big = false) {
+    return G > 4 ? 1024 : (G > 2 || big ? 320 : 512);
+}
+__host__ __device__ constexpr int yslots(int G, int w, bool big = false) {
+    return (G <= 2 && !big) ? (w >= 2 ? 512 : 256) : (w >= 5 ? 512 : (w >= 3 ? 256 : (w == 2 ? 128 : 64)));
 }
 __host__ __device__ constexpr int ychunk(int w) { return w >= 2 ? 32 : 16; }
 
@@ -483,7 +491,8 @@ struct StripSmem {
     static_assert(G >= 1 && G <= kGMax, "compute warps per block");
     static constexpr int YSW = FrameSlot<U, YW>::W;  // words per frame ring slot
     __align__(16) uint32_t uring[G + 1][URS * U * NWMAX];  // ring G: the last warp's row, for the loader
-    __align__(16) uint32_t yring[YW > 0 ? kYSlotsOf(G) * YSW : 4];
+    static constexpr bool kBigSlot = YSW > 64;
+    __align__(16) uint32_t yring[YW > 0 ? kYSlotsOf(G, kBigSlot) * YSW : 4];
     int uprog[G + 1], ucons[G + 1], yprog[G], ycons[G];
     int ybase[G], yrs[G], ychb[G];  // per stream: first slot, slots, blocks per loader round
     int sweep_of[G], band_of[G], ystream[G];
@@ -1314,7 +1323,7 @@ __device__ __forceinline__ void run_band_s(bool special, const Sweep* sp, int si
 
 // Dynamic shared memory of a block: the strip state, then (tensor-core form)
 // the operands, norms, cost tiles and synchronisation of TcShared.
-static_assert(DTW_SWEEP_G_EUC == kTcBands && kTcBands * 32 == kTcRows, "the BF16 form's block holds the M = 128 rows of one MMA");
+static_assert(kGEucB == kTcBands && kTcBands * 32 == kTcRows, "the BF16 form's block holds the M = 128 rows of one MMA");
 template <int KIND, int U, int NWMAX, int DIM>
 constexpr size_t strip_smem_bytes() {
     constexpr size_t base = (sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>) + 127) & ~(size_t)127;
@@ -1467,9 +1476,9 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
             for (int j = 0; j < kG; ++j) {
                 const int w = readers[j] > 0 ? readers[j] : 1;
                 sm.ybase[j] = base;
-                sm.yrs[j] = yslots(kG, w);
+                sm.yrs[j] = yslots(kG, w, SM::kBigSlot);
                 sm.ychb[j] = ychunk(w);
-                if (readers[j] > 0) base += yslots(kG, w);
+                if (readers[j] > 0) base += yslots(kG, w, SM::kBigSlot);
             }
             if constexpr (TCK) {
                 // tiles of this ticket: the sweep's columns in 32s (every active
@@ -1612,7 +1621,9 @@ int sweep_band_rows(int kind, int d, int variant) {
     if (edit_kind(kind)) return 32 * kIntR;
     return d == 12 ? 32 * kEucR : (d == 64 ? 32 : 64);
 }
-int sweep_group_bands(int kind) { return int_kind(kind) ? group_of<KIND_ABS>() : group_of<KIND_EUC>(); }
+int sweep_group_bands(int kind) {
+    return int_kind(kind) ? group_of<KIND_ABS>() : (kind == KIND_EUCB ? group_of<KIND_EUCB>() : group_of<KIND_EUC>());
+}
 
 cudaError_t sweep_prepare(int kind, int d, bool tags, int variant) {
     int nb = 0;
