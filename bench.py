@@ -42,10 +42,23 @@ WORKLOADS = {
 METRIC = "GCUPS for exact linear-memory DTW alignment vs plain GPU form; p50/p99 latency"
 
 
-def make_inputs(name: str, seed_offset: int = 0):
+def make_inputs(name: str, seed_offset: int = 0, size=None):
+    """The workload's pair; ``size`` = (M, N) resizes it (same generator and
+    seed; for profiling runs on smaller cases)."""
     if name == "int_pair":
+        if size:
+            return synth.int_pair(1 + seed_offset, size[0], size[1])
         return synth.workload_int_pair(seed=1 + seed_offset)
+    if size:
+        return synth.chroma_pair(0 + seed_offset, size[0], size[1])
     return synth.workload_plain_float(seed=0 + seed_offset)
+
+
+def parse_size(text):
+    if not text:
+        return None
+    m, n = text.lower().split("x")
+    return int(m), int(n)
 
 
 def dist_env():
@@ -257,7 +270,8 @@ def run_ours(args):
         # the library's autotuner picks the lane block and the base-case cutoff for this size
         from paper_2008_02734_b300 import autotune
         tuned = autotune.tune(WORKLOADS["int_pair"][1], WORKLOADS["int_pair"][2], reps=3)
-    X, Y = make_inputs(args.workload, seed_offset=rank)
+    size = parse_size(args.size)
+    X, Y = make_inputs(args.workload, seed_offset=rank, size=size)
     M, N = len(X), len(Y)
     Xd = torch.from_numpy(X).to(dev)
     Yd = torch.from_numpy(Y).to(dev)
@@ -293,6 +307,7 @@ def run_ours(args):
     # roofline pass (not timed above): per-level events around every sweep launch
     dtw.set_option(dtw.OPT_TIMING, 1)
     sweep_ms, sweep_launches, ops, cells_proc = 0.0, 0, 0.0, 0
+    sweep_cells = 0
     for k in range(args.steps):
         flush.zero_()
         step()
@@ -302,6 +317,7 @@ def run_ours(args):
         tagged = st["tag_cells"]
         ops += 5.0 * (st["sweep_cells"] - tagged) + 7.0 * tagged
         cells_proc += st["sweep_cells"] + st["base_cells"]
+        sweep_cells += st["sweep_cells"]
     torch.cuda.synchronize()
     dtw.set_option(dtw.OPT_TIMING, 0)
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -354,8 +370,23 @@ def run_ours(args):
     clk_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     peak_gops = sms * 4 * 32 * clk_mhz * 1e6 / 1e9  # one 32-lane instruction per SMSP per cycle
     achieved = ops / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
-    traffic, traffic_src = sweep_traffic()
-    roofline = {"bound": "alu", "kernel": "sweep_kernel", "achieved": achieved, "peak": peak_gops,
+    # the committed DRAM capture is of the integer pair's sweeps at the bench's size
+    traffic, traffic_src = sweep_traffic() if args.workload == "int_pair" and not args.size else \
+        (None, "no capture of this workload")
+    if args.workload == "plain_float":
+        # FP64 DP: one FP64 add per processed cell against the measured FP64-add rate
+        fp64_peak = sms * FP64_ADD_PER_SM_CLK * clk_mhz * 1e6 / 1e9  # Gcells/s
+        cps = sweep_cells / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None
+        roofline = {"bound": "fp64", "kernel": "sweep_kernel", "achieved": cps, "peak": fp64_peak,
+                    "unit": "Gcells/s", "frac": (cps / fp64_peak) if cps else None, "traffic": traffic,
+                    "traffic_source": traffic_src,
+                    "peak_source": f"{sms} SMs x {FP64_ADD_PER_SM_CLK} FP64 adds per SM and clock (measured, "
+                                   f"profiles/pipe_rates.md) x {clk_mhz:.0f} MHz ({src}); one FP64 add per cell",
+                    "sweep_ms_per_step": sweep_ms / args.steps, "sweep_launches_per_step": sweep_launches / args.steps,
+                    "processed_cells_per_step": cells_proc / args.steps}
+    else:
+        roofline = None
+    roofline = roofline or {"bound": "alu", "kernel": "sweep_kernel", "achieved": achieved, "peak": peak_gops,
                 "unit": "Gop/s", "frac": (achieved / peak_gops) if achieved else None, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over "
                                 "the sweep launches of one alignment)", "traffic_source": traffic_src,
@@ -389,7 +420,8 @@ def run_ours(args):
         "warmup": max(args.warmup, 3), "ms_per_step": total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32" if args.workload == "int_pair" else "f32-cost/f64-dp",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload][0], "M": M, "N": N, "pairs_per_rank": 1,
+        "config": {"workload": WORKLOADS[args.workload][0] + (f" (resized to {M} x {N})" if size else ""),
+                   "M": M, "N": N, "pairs_per_rank": 1,
                    "parallelism": f"replicas{ws}", "l2": "flushed between steps (256 MiB write outside the events)",
                    "autotuned": None if tuned is None else {"sweep_variant": tuned["variant"],
                                                            "split_windows": tuned["windows"],
@@ -445,17 +477,19 @@ def _golden_rows(name):
         return [ln.strip().split("|") for ln in f if ln.strip() and not ln.startswith("#")]
 
 
-def measure_batch(steps: int, warmup: int, tune: bool = True, check: bool = True):
-    """The uneven batch (256 chroma-like d=12 pairs) through dtw_align_batch:
-    time per batch (CUDA events, L2 flushed between steps), GCUPS, the end-to-end
-    figure from pinned host buffers, the roofline against the FP64-add pipe (the
-    FP64 DP's one add per cell) and the largest cost error against oracle 1's
-    stored costs (tests/golden/batch_chroma_256.txt)."""
+def measure_batch(steps: int, warmup: int, tune: bool = True, check: bool = True, int_data: bool = False):
+    """The uneven batch (256 chroma-like d=12 pairs; with ``int_data`` the same
+    shapes with 1-D int32 |x-y| data) through dtw_align_batch: time per batch
+    (CUDA events, L2 flushed between steps), GCUPS, the end-to-end figure from
+    pinned host buffers, the roofline (chroma: against the FP64-add pipe, the
+    FP64 DP's one add per cell; integer: against the ALU issue rate at 5
+    instructions per cell) and the largest cost error against oracle 1's stored
+    costs (tests/golden/batch_chroma_256.txt, batch_int_256.txt: 0 expected)."""
     import torch
 
     import paper_2008_02734_b300 as dtw
 
-    pairs = synth.workload_batch()
+    pairs = synth.workload_batch_int() if int_data else synth.workload_batch()
     B = len(pairs)
     cells = float(sum(len(x) * len(y) for x, y in pairs))
     Xs = [torch.from_numpy(x).cuda() for x, _ in pairs]
@@ -483,8 +517,9 @@ def measure_batch(steps: int, warmup: int, tune: bool = True, check: bool = True
     st = dtw.get_stats()
     processed = float(st["sweep_cells"] + st["base_cells"])
     err = None
+    golden = "batch_int_256.txt" if int_data else "batch_chroma_256.txt"
     if check:
-        ref = [float(r[3]) for r in _golden_rows("batch_chroma_256.txt")]
+        ref = [float(r[3]) for r in _golden_rows(golden)]
         err = max(abs(c - r) / r for (_, c), r in zip(res, ref))
     # end to end from pinned host buffers (paths come back to host buffers too)
     Xh = [torch.from_numpy(x).pin_memory() for x, _ in pairs]
@@ -499,22 +534,30 @@ def measure_batch(steps: int, warmup: int, tune: bool = True, check: bool = True
         e2e.append(1e3 * (time.perf_counter() - t))
     sms, mhz, src = _peak_rates()
     mean_ms = float(np.mean(ms))
-    fp64_peak = sms * FP64_ADD_PER_SM_CLK * mhz * 1e6 / 1e9  # Gcells/s
     achieved = processed / (mean_ms / 1e3) / 1e9
+    if int_data:
+        peak = sms * 4 * 32 * mhz * 1e6 / 5 / 1e9  # Gcells/s at 5 lane instructions per cell
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gcells/s", "frac": achieved / peak,
+                "peak_source": f"{sms} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz ({src}) / 5 algorithmic "
+                               "lane instructions per cell"}
+    else:
+        peak = sms * FP64_ADD_PER_SM_CLK * mhz * 1e6 / 1e9  # Gcells/s
+        roof = {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "Gcells/s", "frac": achieved / peak,
+                "peak_source": f"{sms} SMs x {FP64_ADD_PER_SM_CLK} FP64 adds per SM and clock (measured, "
+                               f"profiles/pipe_rates.md) x {mhz:.0f} MHz ({src}); one FP64 add per processed cell"}
+    data = "1-D int32 |x-y| (values U[0,255], Y = warp + U{-8..8}), int32 DP" if int_data else \
+        "chroma-like d=12 FP32, FP32 cost, FP64 DP"
     return {
-        "workload": f"uneven batch: {B} chroma-like d=12 FP32 pairs, M log-uniform [1000,20000], N = clip(r M), "
-                    "r log-uniform [0.8,1.25]; FP32 cost, FP64 DP",
+        "workload": f"uneven batch: {B} pairs, M log-uniform [1000,20000], N = clip(r M), "
+                    f"r log-uniform [0.8,1.25]; {data}",
         "pairs": B, "problem_cells": cells, "processed_cells_per_step": processed, "steps": steps,
         "ms_per_step": mean_ms, "gcups": cells / (mean_ms / 1e3) / 1e9, "latency_ms": _percentiles(ms),
         "e2e": {"gcups": cells / (np.mean(e2e) / 1e3) / 1e9, "ms": float(np.mean(e2e)),
                 "h2d_bytes_per_step": int(sum(x.nbytes + y.nbytes for x, y in pairs)),
                 "d2h_bytes_per_step": int(sum(8 * (len(x) + len(y) - 1) for x, y in pairs))},
         "gpu_launches": launches, "levels": st["levels"],
-        "roofline": {"bound": "fp64", "achieved": achieved, "peak": fp64_peak, "unit": "Gcells/s",
-                     "frac": achieved / fp64_peak,
-                     "peak_source": f"{sms} SMs x {FP64_ADD_PER_SM_CLK} FP64 adds per SM and clock (measured, "
-                                    f"profiles/pipe_rates.md) x {mhz:.0f} MHz ({src}); one FP64 add per processed cell"},
-        "max_rel_err_vs_oracle": err, "oracle_source": "tests/golden/batch_chroma_256.txt",
+        "roofline": roof,
+        "max_rel_err_vs_oracle": err, "oracle_source": "tests/golden/" + golden,
         "l2": "flushed between steps",
         "autotuned": None if tuned is None else {"base_area": tuned["base_area"], "split_windows": tuned["windows"]},
     }
@@ -524,11 +567,11 @@ def run_batch_workload(args):
     """The uneven batch: 256 chroma-like d=12 pairs, M log-uniform in [1000, 20000],
     N = clip(r M), r log-uniform in [0.8, 1.25]; all pairs through dtw_align_batch
     (every pair's boxes of a level share the launches).  value = sum(M N) / time."""
-    r = measure_batch(args.steps, args.warmup, tune=not args.no_tune)
+    r = measure_batch(args.steps, args.warmup, tune=not args.no_tune, int_data=args.batch_data == "int")
     line = {"metric": METRIC, "value": r["gcups"], "unit": "GCUPS", "n_gpus": 1,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": r["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-cost/f64-dp",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "i32" if args.batch_data == "int" else "f32-cost/f64-dp", "data": "synthetic",
             "config": {"workload": r["workload"], "pairs": r["pairs"], "problem_cells": r["problem_cells"],
                        "l2": r["l2"], "autotuned": r["autotuned"]},
             "latency_ms": r["latency_ms"],
@@ -896,7 +939,8 @@ def run_serving_workload(args):
 
 def run_pipes():
     """Issue rates of the cell update's instructions on this GPU (dtw_pipe_rates),
-    as thread instructions per second and per SM and clock at the measured clock."""
+    as thread instructions per second and per SM and clock at the measured clock,
+    and the dependent-chain latencies (cycles) of the recurrence's operations."""
     import torch
 
     import paper_2008_02734_b300 as dtw
@@ -905,14 +949,15 @@ def run_pipes():
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     with ClockSampler(0) as cs:
         rates = dtw.pipe_rates()
+        lat = dtw.op_latencies()
     clocks = cs.summary()
     # the measurement lasts a fraction of a second, so the median of the clock
     # samples mixes in idle readings; the kernels themselves run at the SM clock's
     # maximum (no throttle reason), which converts the rates
     mhz = clocks.get("sm_max_mhz") or measured_peaks()[0].get("sm_max_mhz", 2032.0)
     per = {k: v / (sms * mhz * 1e6) for k, v in rates.items()}
-    print(json.dumps({"pipes_per_s": rates, "pipes_per_sm_clock": per, "sms": sms, "sm_mhz": mhz,
-                      "clocks": clocks}))
+    print(json.dumps({"pipes_per_s": rates, "pipes_per_sm_clock": per, "latency_cycles": lat, "sms": sms,
+                      "sm_mhz": mhz, "clocks": clocks}))
     return 0
 
 
@@ -925,6 +970,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "precision", "serving", "edit", "local"],
                     default="int_pair")
     ap.add_argument("--batch", type=int, default=256, help="pairs of the batch workload")
+    ap.add_argument("--batch-data", choices=["chroma", "int"], default="chroma",
+                    help="batch workload data: d=12 chroma-like frames (FP64 DP) or 1-D int32 |x-y|")
     ap.add_argument("--requests", type=int, default=2000, help="requests of the serving workload")
     ap.add_argument("--rho", type=float, default=0.7, help="serving workload: offered load (share of capacity)")
     ap.add_argument("--max-len", type=int, default=20000, help="longest request of the serving workload")
@@ -942,6 +989,10 @@ def main():
                     help="integer sweep variant (lane block) to use instead of the autotuner's choice")
     ap.add_argument("--base-area", type=int, default=None,
                     help="base-case cutoff (cells) to use instead of the autotuner's choice")
+    ap.add_argument("--fused-split", type=int, default=None, choices=[0, 1, 2],
+                    help="where each level's split runs: 0 own launch, 1 library default, 2 in the sweep kernel")
+    ap.add_argument("--size", default=None,
+                    help="MxN: the pair workloads (int_pair, plain_float) resized, same generator (profiling)")
     ap.add_argument("--split-windows", type=int, default=None,
                     help="windows of split rows per box and level, at most (library default 7; 1: one split row)")
     ap.add_argument("--no-graph", action="store_true",
@@ -953,9 +1004,12 @@ def main():
         return run_pipes()
     if args.impl == "reference":
         return run_reference(args)
-    if args.split_windows is not None:
+    if args.split_windows is not None or args.fused_split is not None:
         import paper_2008_02734_b300 as dtw
-        dtw.set_option(dtw.OPT_SPLIT_WINDOWS, args.split_windows)
+        if args.split_windows is not None:
+            dtw.set_option(dtw.OPT_SPLIT_WINDOWS, args.split_windows)
+        if args.fused_split is not None:
+            dtw.set_option(dtw.OPT_FUSED_SPLIT, args.fused_split)
     if args.workload != "int_pair" and (args.no_graph or args.base_area is not None):
         import paper_2008_02734_b300 as dtw
         if args.no_graph:

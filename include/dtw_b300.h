@@ -299,7 +299,12 @@ DTW_API int dtw_get_stats(dtw_stats* out);
  *   [3] packed FP32x2 fused multiply-add (one instruction, two lanes of work)
  *   [4] correctly rounded FP32 square root (__fsqrt_rn; several instructions)
  *   [5] FP64 add
- *   rates_out  host, n doubles; entries past the sixth are not written
+ * and then, measured by one warp running a single chain of 2048 operations that
+ * each take the previous one's result (clock64 cycles per operation), the
+ * latencies that set the pace of a recurrence's dependency chain:
+ *   [6] __vimin3_s32   [7] __sad   [8] FP32 add   [9] FP64 add
+ *   [10] a warp shuffle (__shfl_up_sync by one lane)
+ *   rates_out  host, n doubles; entries past the eleventh are not written
  * Returns the number of entries written, DTW_EINVAL (NULL or n < 1), DTW_ENOMEM
  * or DTW_ECUDA.  Allocates and frees a small device buffer and a stream of its
  * own; blocks for some tens of milliseconds.

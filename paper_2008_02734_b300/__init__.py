@@ -426,6 +426,7 @@ def set_stream(stream) -> None:
 
 
 PIPE_OPS = ("min3_s32", "sad_u32", "ffma_f32", "ffma2_f32x2", "sqrt_rn_f32", "dadd_f64")
+LATENCY_OPS = ("min3_s32", "sad_u32", "fadd_f32", "dadd_f64", "shfl_up")
 
 
 def pipe_rates() -> dict:
@@ -436,6 +437,17 @@ def pipe_rates() -> dict:
     if n < 0:
         raise DTWError(n, "dtw_pipe_rates")
     return {PIPE_OPS[i]: out[i] for i in range(n)}
+
+
+def op_latencies() -> dict:
+    """Dependent-chain latencies (cycles per operation, one warp) of the cell
+    updates' chain operations, measured on the current device."""
+    n_all = len(PIPE_OPS) + len(LATENCY_OPS)
+    out = (ctypes.c_double * n_all)()
+    n = _get_lib().dtw_pipe_rates(out, n_all)
+    if n < 0:
+        raise DTWError(n, "dtw_pipe_rates")
+    return {LATENCY_OPS[i]: out[len(PIPE_OPS) + i] for i in range(max(0, n - len(PIPE_OPS)))}
 
 
 def get_stats() -> dict:

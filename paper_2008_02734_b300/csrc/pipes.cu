@@ -100,6 +100,65 @@ cudaError_t launch_op(int op, int blocks, int iters, uint32_t* sink, cudaStream_
     }
 }
 
+// Dependent-chain latency: one warp runs a single chain of kLatOps operations,
+// each taking the previous one's result, and thread 0 stores the clock64 cycles
+// the chain took.  Cycles per operation = the operation's latency on the chain
+// of a recurrence (the integer and FP64 cell updates of the sweep sit on one).
+constexpr int kLatOps = 2048;
+enum LatOp { LAT_MIN3 = 0, LAT_SAD, LAT_FADD, LAT_DADD, LAT_SHFL, LAT_COUNT };
+
+template <int OP>
+__global__ void __launch_bounds__(32) latency_kernel(int32_t a, int32_t b, float fa, long long* cycles,
+                                                     uint32_t* sink) {
+    uint32_t out = 0;
+    long long t0 = 0, t1 = 0;
+    if constexpr (OP == LAT_MIN3 || OP == LAT_SAD || OP == LAT_SHFL) {
+        int32_t x = a + (int32_t)threadIdx.x;
+        t0 = clock64();
+#pragma unroll 16
+        for (int i = 0; i < kLatOps; ++i) {
+            if constexpr (OP == LAT_MIN3) x = __vimin3_s32(x, b, a + i);
+            else if constexpr (OP == LAT_SAD) x = (int32_t)__sad(a, b, (unsigned)x);
+            else x = __shfl_up_sync(0xffffffffu, x, 1);
+        }
+        t1 = clock64();
+        out = (uint32_t)x;
+    } else if constexpr (OP == LAT_FADD) {
+        float x = fa;
+        t0 = clock64();
+#pragma unroll 16
+        for (int i = 0; i < kLatOps; ++i) x = __fadd_rn(x, fa);
+        t1 = clock64();
+        out = __float_as_uint(x);
+    } else {  // LAT_DADD
+        double x = (double)fa;
+        const double da = (double)fa;
+        t0 = clock64();
+#pragma unroll 16
+        for (int i = 0; i < kLatOps; ++i) x = __dadd_rn(x, da);
+        t1 = clock64();
+        out = (uint32_t)__double2loint(x);
+    }
+    sink[threadIdx.x] = out;
+    if (threadIdx.x == 0) *cycles = t1 - t0;
+}
+
+template <int OP>
+cudaError_t launch_lat(long long* cycles, uint32_t* sink, cudaStream_t st) {
+    latency_kernel<OP><<<1, 32, 0, st>>>(5, 7, 1.0f, cycles, sink);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_latency(int op, long long* cycles, uint32_t* sink, cudaStream_t st) {
+    switch (op) {
+        case LAT_MIN3: return launch_lat<LAT_MIN3>(cycles, sink, st);
+        case LAT_SAD: return launch_lat<LAT_SAD>(cycles, sink, st);
+        case LAT_FADD: return launch_lat<LAT_FADD>(cycles, sink, st);
+        case LAT_DADD: return launch_lat<LAT_DADD>(cycles, sink, st);
+        default: return launch_lat<LAT_SHFL>(cycles, sink, st);
+    }
+}
+
 }  // namespace
 }  // namespace dtwb
 
@@ -137,9 +196,27 @@ extern "C" DTW_API int dtw_pipe_rates(double* rates_out, int32_t n) {
         const double count = (double)blocks * kPipeThreads * (double)iters * kChains;
         rates_out[op] = count / (ms * 1e-3);
     }
+    // entries OP_COUNT.. : dependent latencies in cycles (the sink's first words
+    // hold the cycle count, the rest the chains' results)
+    const int nlat = rc == DTW_OK && n > (int)OP_COUNT ? (n - (int)OP_COUNT < (int)LAT_COUNT ? n - (int)OP_COUNT
+                                                                                           : (int)LAT_COUNT)
+                                                       : 0;
+    long long* cyc = reinterpret_cast<long long*>(sink);
+    for (int op = 0; op < nlat && rc == DTW_OK; ++op) {
+        long long h = 0;
+        cudaError_t e = launch_latency(op, cyc, sink + 64, st);  // warm-up (instruction cache)
+        if (e == cudaSuccess) e = launch_latency(op, cyc, sink + 64, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, cyc, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess || h <= 0) {
+            rc = DTW_ECUDA;
+            break;
+        }
+        rates_out[OP_COUNT + op] = (double)h / kLatOps;
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (st) cudaStreamDestroy(st);
     cudaFree(sink);
-    return rc == DTW_OK ? nops : rc;
+    return rc == DTW_OK ? nops + nlat : rc;
 }

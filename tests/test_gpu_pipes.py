@@ -16,3 +16,14 @@ def test_pipe_rates_plausible():
         assert r[k] > 1e11, (k, r[k])
     assert r["ffma_f32"] > 4 * r["dadd_f64"]
     assert r["ffma_f32"] > r["sqrt_rn_f32"]
+
+
+@pytest.mark.gpu
+def test_op_latencies_plausible():
+    """The dependent-chain latencies: positive, a shuffle and an FP64 add slower
+    than the one-instruction integer minimum on the chain."""
+    lat = dtw.op_latencies()
+    assert set(lat) == set(dtw.LATENCY_OPS)
+    assert all(1.0 < v < 10000.0 for v in lat.values()), lat
+    assert lat["dadd_f64"] > lat["fadd_f32"]
+    assert lat["shfl_up"] > lat["min3_s32"]
