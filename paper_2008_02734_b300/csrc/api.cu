@@ -125,7 +125,11 @@ int level_graph(Ctx& c, const std::vector<long long>& key, const SweepArgs& sa, 
         lg.exec = nullptr;
     }
     if (!lg.cap && cudaStreamCreateWithFlags(&lg.cap, cudaStreamNonBlocking) != cudaSuccess) return DTW_ECUDA;
+    // integer kinds: two sweep kernels, with and without tagged sweeps (the
+    // latter holds fewer registers, so more blocks fit an SM), chosen per level
+    const bool two = int_kind(kind);
     if (sweep_prepare(kind, d, int_kind(kind), c.variant) != cudaSuccess) return DTW_ECUDA;
+    if (two && sweep_prepare(kind, d, false, c.variant) != cudaSuccess) return DTW_ECUDA;
     cudaGraph_t g = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return DTW_ECUDA;
     int rc = DTW_OK;
@@ -142,9 +146,51 @@ int level_graph(Ctx& c, const std::vector<long long>& key, const SweepArgs& sa, 
     }
     if (e == cudaSuccess) {
         cudaGraph_t body = np.conditional.phGraph_out[0];
-        e = cudaStreamBeginCaptureToGraph(lg.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        cudaGraphNode_t last = nullptr;  // the body's node the split and plan follow
+        if (two) {
+            // body: select -> IF(no tagged box) { sweep } -> IF(tagged boxes) { sweep with tags } -> ...
+            cudaGraphConditionalHandle hk[2];
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+                e = cudaGraphConditionalHandleCreate(&hk[k], body, 0, 0);
+            if (e == cudaSuccess)
+                e = cudaStreamBeginCaptureToGraph(lg.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e1 = launch_sweep_select(ctl, hk[0], hk[1], lg.cap);
+                const cudaGraphNode_t* deps = nullptr;
+                size_t ndeps = 0;
+                cudaStreamCaptureStatus cs;
+                if (e1 == cudaSuccess) e1 = cudaStreamGetCaptureInfo(lg.cap, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+                if (e1 == cudaSuccess && ndeps == 1) last = deps[0];
+                else if (e1 == cudaSuccess) e1 = cudaErrorUnknown;
+                cudaGraph_t got = nullptr;
+                e = cudaStreamEndCapture(lg.cap, &got);
+                if (e == cudaSuccess) e = e1;
+            }
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+                cudaGraphNodeParams ip{};
+                ip.type = cudaGraphNodeTypeConditional;
+                ip.conditional.handle = hk[k];
+                ip.conditional.type = cudaGraphCondTypeIf;
+                ip.conditional.size = 1;
+                cudaGraphNode_t inode;
+                e = cudaGraphAddNode(&inode, body, &last, nullptr, 1, &ip);
+                if (e != cudaSuccess) break;
+                e = cudaStreamBeginCaptureToGraph(lg.cap, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t e1 = launch_sweep(kind, d, k == 1, sa, c.num_sms, 0, lg.cap, c.variant);
+                    cudaGraph_t got = nullptr;
+                    e = cudaStreamEndCapture(lg.cap, &got);
+                    if (e == cudaSuccess) e = e1;
+                }
+                last = inode;
+            }
+        }
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(lg.cap, body, last ? &last : nullptr, nullptr, last ? 1 : 0,
+                                              cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = launch_sweep(kind, d, int_kind(kind), sa, c.num_sms, 0, lg.cap, c.variant);
+            cudaError_t e1 = two ? cudaSuccess : launch_sweep(kind, d, false, sa, c.num_sms, 0, lg.cap, c.variant);
             if (e1 == cudaSuccess && sa.prog == nullptr) e1 = launch_split(sp, lg.cap);
             if (e1 == cudaSuccess) e1 = launch_plan(pn, lg.cap);
             if (e1 == cudaSuccess) e1 = launch_level_cond(ctl, h, max_levels, lg.cap);
@@ -479,7 +525,9 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         cudaEvent_t s0 = nullptr, s1 = nullptr;
         if (c.timing) s0 = T.mark();
         // integer levels may mix tagged and untagged boxes
-        e = launch_sweep(kind, d, mode == MODE_ALIGN && int_kind(kind), sa, c.num_sms, hc.n_tickets, st, c.variant);
+        // integer kinds: the kernel with tagged sweeps only for a level that has tagged boxes
+        e = launch_sweep(kind, d, mode == MODE_ALIGN && int_kind(kind) && hc.n_tag > 0, sa, c.num_sms, hc.n_tickets,
+                         st, c.variant);
         ++launches;
         if (c.timing) s1 = T.mark();
         ++sweeps;

@@ -168,7 +168,7 @@ struct LevelCtl {
     int32_t levels;              // levels planned on the device (graph-driven level loop)
     int32_t tmap_on;             // the current level's tickets follow the ticket map (group-major order)
     int32_t split_ticket;        // next split work item of the sweep kernel's split phase
-    int32_t pad_;
+    int32_t n_tag;               // boxes of the current level that take a tagged sweep (set by the plan)
 };
 
 // ---------------------------------------------------------------- memory order

@@ -134,6 +134,11 @@ cudaError_t launch_mark_pairs(const Box* boxes, const LevelCtl* ctl, int32_t* fl
 // Graph-driven level loop: sets the loop's condition to "another level": boxes
 // planned, no device error and fewer than max_levels levels so far.
 cudaError_t launch_level_cond(LevelCtl* ctl, cudaGraphConditionalHandle h, int max_levels, cudaStream_t st);
+// Graph-driven level loop, integer kinds: sets the two IF conditions of the
+// level's sweep kernels from the plan's count of tagged boxes (h_plain: none,
+// the kernel without tagged sweeps; h_tags: some).
+cudaError_t launch_sweep_select(const LevelCtl* ctl, cudaGraphConditionalHandle h_plain,
+                                cudaGraphConditionalHandle h_tags, cudaStream_t st);
 
 // Windows of split rows per box at most (DTW_OPT_SPLIT_WINDOWS), as read by the
 // serving engines and dtw_footprint (api.cu keeps it).

@@ -102,10 +102,12 @@ constexpr int kTmapBuckets = 1024;
 __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
     __shared__ long long carry[4];
     __shared__ unsigned long long cells_sh[2];
+    __shared__ int ntag_sh;
     __shared__ uint32_t ep_base;
     const int nslot = a.mode == MODE_COST ? 1 : 2;
     if (threadIdx.x < 4) carry[threadIdx.x] = 0;
     if (threadIdx.x < 2) cells_sh[threadIdx.x] = 0;
+    if (threadIdx.x == 0) ntag_sh = 0;
     __shared__ int nbox_sh;
     if (threadIdx.x == 0) {
         ep_base = a.ctl->epoch_base;
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             if (a.mode == MODE_COST) {
                 sw.rows = g.P;
             } else if (b.flags & BOX_TAG) {
+                if (dir == 0) atomicAdd(&ntag_sh, 1);
                 sw.rows = dir == 0 ? g.P : 0;
                 sw.out_row0 = g.r;
                 sw.nout = dir == 0 ? 1 : 0;
@@ -317,6 +320,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         c->split_ticket = 0;
         c->n_next = 0;
         c->n_cur = n_boxes;
+        c->n_tag = ntag_sh;
         if (a.reset_base) c->n_base = 0;
         c->need_buf = carry[1];
         c->epoch_base = ep_base + (uint32_t)total_bands + 1u;
@@ -706,6 +710,22 @@ __global__ void level_cond_kernel(LevelCtl* ctl, cudaGraphConditionalHandle h, i
 
 cudaError_t launch_level_cond(LevelCtl* ctl, cudaGraphConditionalHandle h, int max_levels, cudaStream_t st) {
     level_cond_kernel<<<1, 32, 0, st>>>(ctl, h, max_levels);
+    return cudaGetLastError();
+}
+
+// The level's sweep kernel (integer kinds): the one without tagged sweeps, whose
+// band steps hold fewer registers, unless the plan found a tagged box.
+__global__ void sweep_select_kernel(const LevelCtl* ctl, cudaGraphConditionalHandle h_plain,
+                                    cudaGraphConditionalHandle h_tags) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const bool tags = ctl->n_tag > 0;
+    cudaGraphSetConditional(h_plain, tags ? 0u : 1u);
+    cudaGraphSetConditional(h_tags, tags ? 1u : 0u);
+}
+
+cudaError_t launch_sweep_select(const LevelCtl* ctl, cudaGraphConditionalHandle h_plain,
+                                cudaGraphConditionalHandle h_tags, cudaStream_t st) {
+    sweep_select_kernel<<<1, 32, 0, st>>>(ctl, h_plain, h_tags);
     return cudaGetLastError();
 }
 
