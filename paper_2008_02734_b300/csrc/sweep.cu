@@ -99,7 +99,7 @@ constexpr int URS = 64;                  // slots (column blocks) of a row ring
 #define DTW_SWEEP_UNROLL 4
 #endif
 #ifndef DTW_SWEEP_UNROLL_EUC
-#define DTW_SWEEP_UNROLL_EUC 1
+#define DTW_SWEEP_UNROLL_EUC 0
 #endif
 // The block's last band warp hands its last row to the loader warp through one
 // more shared-memory ring, and the loader writes it to the global boundary row
@@ -118,7 +118,17 @@ constexpr int KC = DTW_SWEEP_KC;         // steps per group: rings are synchroni
 template <int KIND, bool FULL>
 __host__ __device__ constexpr bool drain_of() { return DTW_LOADER_DRAIN != 0 && !(int_kind(KIND) && FULL); }
 constexpr int kGroupUnroll = DTW_SWEEP_UNROLL;        // integer kind
-constexpr int kGroupUnrollEuc = DTW_SWEEP_UNROLL_EUC;  // Euclidean kind (longer steps, larger code)
+// Euclidean kinds (longer steps, larger code): steps per loop iteration of a
+// steady group, by kind and dimension.  Measured (chroma pair 2000 x 2500, the
+// 256-pair chroma batch, the 60000 x 75000 d=64 pair): d=12 with 2 steps 1.46 ms
+// and 94.1 ms against 1.54 and 95.4 with 1; the d=64 FP32-cost form with 4
+// steps 114.5 ms against 117.1 (with 2: 127.9); the BF16 form and the
+// compensated d=64 form unchanged.  DTW_SWEEP_UNROLL_EUC > 0 sets one factor
+// for every Euclidean variant.
+template <int KIND, int DIM>
+__host__ __device__ constexpr int euc_unroll() {
+    return DTW_SWEEP_UNROLL_EUC > 0 ? DTW_SWEEP_UNROLL_EUC : (DIM == 12 ? 2 : (DIM == 64 && KIND == KIND_EUC ? 4 : 1));
+}
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ int ld_acquire_cta(const int* p) {
@@ -937,7 +947,8 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
 #pragma unroll kGroupUnroll
                 for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{}, std::false_type{});
             } else {
-#pragma unroll kGroupUnrollEuc
+                constexpr int kEU = euc_unroll<KIND, DIM>();
+#pragma unroll kEU
                 for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{}, std::false_type{});
             }
         } else {
