@@ -117,7 +117,12 @@ constexpr int KC = DTW_SWEEP_KC;         // steps per group: rings are synchroni
 // the band's own stores against 2.52 with the drain; the others gain 2-6%).
 template <int KIND, bool FULL>
 __host__ __device__ constexpr bool drain_of() { return DTW_LOADER_DRAIN != 0 && !(int_kind(KIND) && FULL); }
-constexpr int kGroupUnroll = DTW_SWEEP_UNROLL;        // integer kind
+// Integer kinds: steps per loop iteration of a steady group; the local
+// alignment's sweeps (KIND_LOCAL, with the floor and the best-node tracking)
+// take 2 (their two passes 5.98 -> 5.71 ms on the 20000 x 24000 workload with
+// 2 for every integer kind, where the integer pair and edit distance lose 10%).
+template <int KIND>
+__host__ __device__ constexpr int int_unroll() { return KIND == KIND_LOCAL ? 2 : DTW_SWEEP_UNROLL; }
 // Euclidean kinds (longer steps, larger code): steps per loop iteration of a
 // steady group, by kind and dimension.  Measured (chroma pair 2000 x 2500, the
 // 256-pair chroma batch, the 60000 x 75000 d=64 pair): d=12 with 2 steps 1.46 ms
@@ -944,7 +949,8 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
 #pragma unroll
                 for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{}, std::false_type{});
             } else if constexpr (int_kind(KIND)) {
-#pragma unroll kGroupUnroll
+                constexpr int kIU = int_unroll<KIND>();
+#pragma unroll kIU
                 for (int i = 0; i < KC; ++i) step(s0 + i, std::false_type{}, std::false_type{});
             } else {
                 constexpr int kEU = euc_unroll<KIND, DIM>();
