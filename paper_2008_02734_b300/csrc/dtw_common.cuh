@@ -108,8 +108,9 @@ constexpr int kSplitWinMax = 15;
 constexpr int kOutRowsMax = 64;
 constexpr int kWinGap = 8;
 
-// One wavefront sweep over frame rows [0, rows) x frame columns [0, Q).
-struct Sweep {
+// One wavefront sweep over frame rows [0, rows) x frame columns [0, Q).  16-byte
+// aligned (144 bytes): the plan writes a level's descriptors with 16-byte stores.
+struct alignas(16) Sweep {
     const void* rowseq;  // features indexed by frame row p: rowseq[rbase + rstep*p]
     const void* colseq;  // features indexed by frame column q: colseq[cbase + cstep*q]
     int32_t rbase, rstep, cbase, cstep;

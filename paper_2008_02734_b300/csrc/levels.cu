@@ -259,8 +259,15 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         if (threadIdx.x < 4) carry[threadIdx.x] += t4[threadIdx.x];
         __syncthreads();
     }
-    atomicAdd(&cells_sh[0], my_cells);
-    atomicAdd(&cells_sh[1], my_tag);
+    // warp sums first: one shared atomic per warp instead of per thread
+    for (int o = 16; o; o >>= 1) {
+        my_cells += __shfl_down_sync(kFull, my_cells, o);
+        my_tag += __shfl_down_sync(kFull, my_tag, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&cells_sh[0], my_cells);
+        atomicAdd(&cells_sh[1], my_tag);
+    }
     __syncthreads();
     // Ticket map, group-major: ticket t -> (sweep, band group j), every sweep's
     // first group of G bands first, then every sweep's second group, and so on
@@ -277,10 +284,17 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         for (int i = threadIdx.x; i < kTmapBuckets; i += blockDim.x) tm_hist[i] = 0;
         if (threadIdx.x == 0) tm_ok = 1;
         __syncthreads();
-        for (int s = threadIdx.x; s < nsw; s += blockDim.x) {
-            const int ng = (a.sweeps[s].nbands + a.G - 1) / a.G;
-            if (ng >= kTmapBuckets) tm_ok = 0;
-            else if (ng > 0) atomicAdd(&tm_hist[ng], 1);
+        // deep levels hold thousands of sweeps with the same few group counts:
+        // the lanes of a warp with equal counts share one shared-memory atomic
+        for (int base = 0; base < nsw; base += blockDim.x) {
+            const int s = base + threadIdx.x;
+            int ng = s < nsw ? (a.sweeps[s].nbands + a.G - 1) / a.G : 0;
+            if (ng >= kTmapBuckets) {
+                tm_ok = 0;
+                ng = 0;
+            }
+            const unsigned peers = __match_any_sync(kFull, ng);
+            if (ng > 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&tm_hist[ng], __popc(peers));
         }
         __syncthreads();
         if (tm_ok) {
@@ -299,12 +313,21 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             }
             __syncthreads();
             if (tm_ok) {
-                for (int s = threadIdx.x; s < nsw; s += blockDim.x) {
-                    const int ng = (a.sweeps[s].nbands + a.G - 1) / a.G;
-                    if (ng == 0) continue;
-                    // descending group count: bucket ng starts after every sweep with more groups
-                    const int pos = tm_cnt[ng] + atomicAdd(&tm_hist[ng], 1);
-                    for (int j = 0; j < ng; ++j) a.tmap[tm_off[j] + pos] = make_int2(s, j);
+                const int lane = threadIdx.x & 31;
+                for (int base = 0; base < nsw; base += blockDim.x) {
+                    const int s = base + threadIdx.x;
+                    const int ng = s < nsw ? (a.sweeps[s].nbands + a.G - 1) / a.G : 0;
+                    // descending group count: bucket ng starts after every sweep with
+                    // more groups; lanes with equal counts take consecutive places
+                    const unsigned peers = __match_any_sync(kFull, ng);
+                    const int leader = __ffs(peers) - 1;
+                    int first = 0;
+                    if (ng > 0 && lane == leader) first = atomicAdd(&tm_hist[ng], __popc(peers));
+                    first = __shfl_sync(kFull, first, leader);
+                    if (ng > 0) {
+                        const int pos = tm_cnt[ng] + first + __popc(peers & ((1u << lane) - 1u));
+                        for (int j = 0; j < ng; ++j) a.tmap[tm_off[j] + pos] = make_int2(s, j);
+                    }
                 }
             }
         }
