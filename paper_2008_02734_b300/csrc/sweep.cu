@@ -483,9 +483,10 @@ __device__ __forceinline__ void tc_ld32(uint32_t ta, float* v) {
 // make it lag by some 50 steps rather than 40) then holds back the first
 // reader.  With two warps per block (the integer kind, 16-byte slots) the
 // region is 512 slots and a stream gets 512 (two readers) or 256 (one); with two
-// warps or fewer and large slots (more than 256 bytes) the least room applies.
+// warps or fewer and large slots (more than 256 bytes) the least room applies:
+// 128 slots, a stream 128 (two readers) or 64 (one).
 __host__ __device__ constexpr int kYSlotsOf(int G, bool big = false) {
-    return G > 4 ? 1024 : (G > 2 || big ? 320 : 512);
+    return G > 4 ? 1024 : (G > 2 ? 320 : (big ? 128 : 512));
 }
 __host__ __device__ constexpr int yslots(int G, int w, bool big = false) {
     return (G <= 2 && !big) ? (w >= 2 ? 512 : 256) : (w >= 5 ? 512 : (w >= 3 ? 256 : (w == 2 ? 128 : 64)));
