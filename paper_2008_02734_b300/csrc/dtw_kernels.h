@@ -104,7 +104,10 @@ struct BaseArgs {
     int kind, d;
 };
 // Largest box (cells) the base-case kernel accepts.
-constexpr long long kBaseAreaMax = 32768;
+#ifndef DTW_BASE_AREA_MAX
+#define DTW_BASE_AREA_MAX 32768
+#endif
+constexpr long long kBaseAreaMax = DTW_BASE_AREA_MAX;
 cudaError_t launch_base(const BaseArgs& a, cudaStream_t st);
 
 struct AssembleArgs {

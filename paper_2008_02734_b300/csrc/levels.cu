@@ -408,7 +408,12 @@ cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
 // Shared memory per warp: 2-bit backpointers of up to kBaseAreaMax cells
 // (rows are the shorter side, 16 pointers per word, each row word-aligned) and
 // the boundary row between consecutive 32-row bands.
-constexpr int kPtrWords = (int)(kBaseAreaMax / 16) + 182;  // P*ceil(Q/16) <= A/16 + sqrt(A)
+constexpr long long isqrt_ceil(long long a) {
+    long long r = 0;
+    while (r * r < a) ++r;
+    return r;
+}
+constexpr int kPtrWords = (int)(kBaseAreaMax / 16 + isqrt_ceil(kBaseAreaMax)) + 1;  // P*ceil(Q/16) <= A/16 + sqrt(A)
 constexpr int kRowBuf = (int)(kBaseAreaMax / 32);          // Q < A/32 whenever P > 32
 constexpr int kBaseWarps = 2;
 
