@@ -24,6 +24,7 @@
 // same launches.  With DTW_SERVE_TRACE set in the environment each engine logs
 // its iterations (admissions, level ends, finished tickets) to stderr.  Each box is computed exactly as in dtw_align, so a result does
 // not depend on which other requests share its launches.
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -209,6 +210,7 @@ struct Engine {
     }
 
     bool idle() const { return active.empty() && queue.empty(); }
+    bool busy = false;  // counted in g_busy_engines (under the server's mutex)
     LevelCtl* ctl() { return reinterpret_cast<LevelCtl*>(ws + L.ctl); }
     PairDesc* pairs() { return reinterpret_cast<PairDesc*>(ws + L.pairs); }
     PairRes* pres() { return reinterpret_cast<PairRes*>(ws + L.pres); }
@@ -252,6 +254,11 @@ Server& server() {
 }
 
 static bool g_trace = getenv("DTW_SERVE_TRACE") != nullptr;
+// Engines with work.  While another engine has work, an engine's sweeps run one
+// block per SM at most: a group's level of many bands would otherwise hold every
+// SM with persistent blocks, and the other group's blocks (a d=64 block takes
+// most of an SM's shared memory) would wait for that whole level.
+static std::atomic<int> g_busy_engines{0};
 static double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -398,7 +405,8 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
         SweepArgs sa{d_sweeps, ctl(), reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres,
                      d, spin_limit, -1};
         sa.tmap = reinterpret_cast<const int2*>(ws + L.tmap);
-        if (e == cudaSuccess) e = launch_sweep(kind, d, kind == KIND_ABS, sa, num_sms, 0, st);
+        const long long cap = g_busy_engines.load(std::memory_order_relaxed) > 1 ? num_sms : 0;
+        if (e == cudaSuccess) e = launch_sweep(kind, d, kind == KIND_ABS, sa, num_sms, cap, st);
         SplitArgs sp{cur, n_cur, pairs(), pres(), kind, d, halo, d_sweeps, d_sres, ws + L.outpool, nxt, d_base,
                      ctl(), base_area, (int)L.cap_box, (int)L.cap_base, d_boxdone, ws + L.partials, -1, num_sms};
         if (e == cudaSuccess) e = launch_split(sp, st);
@@ -482,6 +490,10 @@ void Server::engine_loop(Engine* en) {
             std::unique_lock<std::mutex> g(mu);
             cv.wait(g, [&] { return !en->idle(); });
             en->running = true;
+            if (!en->busy) {
+                en->busy = true;
+                g_busy_engines.fetch_add(1);
+            }
             if (!en->ws) {
                 // take the engine's share of what the budget has left; wait while
                 // another engine still holds more than its share
@@ -525,6 +537,10 @@ void Server::engine_loop(Engine* en) {
                 }
                 en->queue.clear();
                 en->running = false;
+                if (en->busy && en->idle()) {
+                    en->busy = false;
+                    g_busy_engines.fetch_sub(1);
+                }
                 continue;
             }
         }
@@ -553,6 +569,10 @@ void Server::engine_loop(Engine* en) {
             inflight.erase(r.first);
         }
         en->running = false;
+        if (en->busy && en->idle()) {
+            en->busy = false;
+            g_busy_engines.fetch_sub(1);
+        }
         if (budget && en->ws && en->idle()) {
             // an idle engine whose share has drifted gives its arena back
             const double want = (double)target_arena(en), have = (double)en->arena;

@@ -483,25 +483,31 @@ __device__ void split_item(const SplitArgs& a, int it, const int* prog, int spin
     if (threadIdx.x == 0) s_last = nitems == 1 || atomicAdd(&a.box_done[bi], 1) == nitems - 1;
     __syncthreads();
     if (s_last && nitems > 1) {
-        // merge the box's partial minima: one warp per split row, lanes over its
-        // window's column chunks
+        // merge the box's partial minima: a group of gs threads per split row
+        // (gs a power of two, every row in one pass where the block allows),
+        // its threads over the row's window's column chunks
         __threadfence();
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int m = wid; m < nr; m += nw) {
-            const int tt = m / ow, e = m - tt * ow;
+        int gs = 32;
+        while (gs > 1 && gs * nr > (int)blockDim.x) gs >>= 1;
+        const int per = (int)blockDim.x / gs, sub = (int)threadIdx.x % gs;
+        for (int m0 = 0; m0 < nr; m0 += per) {  // the same count of passes for every thread
+            const int m = m0 + (int)threadIdx.x / gs;
             RowMin<V> x{(V)0, 0, INT_MAX};
-            for (int c = lane; c < nch; c += 32) {
-                const RowMin<V> y = partials[(size_t)(fw.item0 + tt * nch + c) * kSplitRowsMax + e];
-                x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
+            if (m < nr) {
+                const int tt = m / ow, e = m - tt * ow;
+                for (int c = sub; c < nch; c += gs) {
+                    const RowMin<V> y = partials[(size_t)(fw.item0 + tt * nch + c) * kSplitRowsMax + e];
+                    x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
+                }
             }
-            for (int o = 16; o; o >>= 1) {
+            for (int o = gs >> 1; o; o >>= 1) {
                 RowMin<V> y;
                 y.v = __shfl_down_sync(kFull, x.v, o);
                 y.n = __shfl_down_sync(kFull, x.n, o);
                 y.q = __shfl_down_sync(kFull, x.q, o);
-                if (lane + o < 32) x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
+                if (sub + o < gs) x = (x.n == 0) ? y : (y.n == 0 ? x : merge(x, y));
             }
-            if (lane == 0) rm[m] = x;
+            if (m < nr && sub == 0) rm[m] = x;
         }
         __syncthreads();
     }

@@ -138,7 +138,9 @@ def test_groups_overlap_short_d64_during_long_d12():
     it would wait for a level of the long pair before each of its own), and both
     results equal the pairs aligned alone."""
     import time
-    Xl, Yl = synth.chroma_pair(501, 20000, 24000)
+    # the long request long enough (about 25 ms alone) that one of its levels
+    # outlasts the short request many times over
+    Xl, Yl = synth.chroma_pair(501, 30000, 36000)
     Xs, Ys = synth.mfcc_pair(502, 700, 800)
     dl, ds = (_cuda(Xl), _cuda(Yl)), (_cuda(Xs), _cuda(Ys))
     # warm both engines up (arena creation is not part of the measurement)
