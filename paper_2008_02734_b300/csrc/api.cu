@@ -114,7 +114,7 @@ int workspace(Ctx& c, size_t bytes, void** out) {
 // sweep -> split -> plan of the next level (which copies the next boxes into the
 // current list) -> condition kernel.  No host round trip per level.
 int level_graph(Ctx& c, const std::vector<long long>& key, const SweepArgs& sa, const SplitArgs& sp,
-                const PlanArgs& pn, LevelCtl* ctl, int kind, int d, int max_levels, cudaGraphExec_t* out) {
+                const PlanArgs& pn, LevelCtl* ctl, int kind, int d, int variant, int max_levels, cudaGraphExec_t* out) {
     auto& lg = c.lg;
     if (lg.exec && lg.key == key) {
         *out = lg.exec;
@@ -128,8 +128,8 @@ int level_graph(Ctx& c, const std::vector<long long>& key, const SweepArgs& sa, 
     // integer kinds: two sweep kernels, with and without tagged sweeps (the
     // latter holds fewer registers, so more blocks fit an SM), chosen per level
     const bool two = int_kind(kind);
-    if (sweep_prepare(kind, d, int_kind(kind), c.variant) != cudaSuccess) return DTW_ECUDA;
-    if (two && sweep_prepare(kind, d, false, c.variant) != cudaSuccess) return DTW_ECUDA;
+    if (sweep_prepare(kind, d, int_kind(kind), variant) != cudaSuccess) return DTW_ECUDA;
+    if (two && sweep_prepare(kind, d, false, variant) != cudaSuccess) return DTW_ECUDA;
     cudaGraph_t g = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return DTW_ECUDA;
     int rc = DTW_OK;
@@ -178,7 +178,7 @@ int level_graph(Ctx& c, const std::vector<long long>& key, const SweepArgs& sa, 
                 e = cudaStreamBeginCaptureToGraph(lg.cap, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeThreadLocal);
                 if (e == cudaSuccess) {
-                    cudaError_t e1 = launch_sweep(kind, d, k == 1, sa, c.num_sms, 0, lg.cap, c.variant);
+                    cudaError_t e1 = launch_sweep(kind, d, k == 1, sa, c.num_sms, 0, lg.cap, variant);
                     cudaGraph_t got = nullptr;
                     e = cudaStreamEndCapture(lg.cap, &got);
                     if (e == cudaSuccess) e = e1;
@@ -190,7 +190,7 @@ int level_graph(Ctx& c, const std::vector<long long>& key, const SweepArgs& sa, 
             e = cudaStreamBeginCaptureToGraph(lg.cap, body, last ? &last : nullptr, nullptr, last ? 1 : 0,
                                               cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = two ? cudaSuccess : launch_sweep(kind, d, false, sa, c.num_sms, 0, lg.cap, c.variant);
+            cudaError_t e1 = two ? cudaSuccess : launch_sweep(kind, d, false, sa, c.num_sms, 0, lg.cap, variant);
             if (e1 == cudaSuccess && sa.prog == nullptr) e1 = launch_split(sp, lg.cap);
             if (e1 == cudaSuccess) e1 = launch_plan(pn, lg.cap);
             if (e1 == cudaSuccess) e1 = launch_level_cond(ctl, h, max_levels, lg.cap);
@@ -440,6 +440,14 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
     const int U = sweep_block_cols(kind, d, c.variant);
     const int BR = sweep_band_rows(kind, d, c.variant);
     const int G = sweep_group_bands(kind);
+    // the first level's tickets (two half sweeps of a root box's longer side)
+    // choose between the sweep's latency and throughput forms
+    long long tickets0 = 0;
+    for (const Box& r : roots) {
+        const long long half = (std::max(r.H, r.W) + 1) / 2;
+        tickets0 += 2 * (((half + BR - 1) / BR + G - 1) / G);
+    }
+    const int sv = sweep_variant_for(kind, d, c.variant, tickets0, c.num_sms);
     Box* cur = boxA;
     Box* nxt = boxB;
     int levels = 0, sweeps = 0;
@@ -500,9 +508,9 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         const std::vector<long long> key{(long long)(uintptr_t)ws, (long long)L.total, L.cap_box, L.cap_base,
                                          L.cap_sweeps, L.cap_buf, L.cap_out, L.cap_items, kind, d, base_area,
                                          c.spin_limit, c.skip_publish, c.num_sms, max_levels, (long long)L.ctl,
-                                         c.variant, d_prog != nullptr, c.split_windows};
+                                         sv, d_prog != nullptr, c.split_windows};
         cudaGraphExec_t ex = nullptr;
-        int grc = level_graph(c, key, sa, sp, pn, d_ctl, kind, d, max_levels, &ex);
+        int grc = level_graph(c, key, sa, sp, pn, d_ctl, kind, d, sv, max_levels, &ex);
         if (grc != DTW_OK) return grc;
         if (cudaGraphLaunch(ex, st) != cudaSuccess) return DTW_ECUDA;
         hc.n_cur = 0;  // the loop ran on the device; its counters are read after the base case
@@ -527,7 +535,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         // integer levels may mix tagged and untagged boxes
         // integer kinds: the kernel with tagged sweeps only for a level that has tagged boxes
         e = launch_sweep(kind, d, mode == MODE_ALIGN && int_kind(kind) && hc.n_tag > 0, sa, c.num_sms, hc.n_tickets,
-                         st, c.variant);
+                         st, sv);
         ++launches;
         if (c.timing) s1 = T.mark();
         ++sweeps;

@@ -60,6 +60,11 @@ cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num
                          cudaStream_t st, int variant = 0);
 // One-time launch setup of the variant (attributes, occupancy); must precede a stream capture.
 cudaError_t sweep_prepare(int kind, int d, bool tags, int variant = 0);
+// The sweep variant a call runs: the integer kinds keep `variant`; the d = 12
+// Euclidean kinds take their throughput form (variant 1: more resident blocks,
+// fewer registers) when the first level's tickets, about `tickets0`, outnumber
+// the blocks the default form keeps resident; other kinds variant 0.
+int sweep_variant_for(int kind, int d, int variant, long long tickets0, int num_sms);
 
 // Level planning modes
 constexpr int MODE_ALIGN = 0;  // per box: two half sweeps, or one tagged sweep (BOX_TAG)

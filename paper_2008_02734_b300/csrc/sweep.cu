@@ -90,6 +90,13 @@ __host__ __device__ constexpr int threads_of() {
     // + the loader warp; the BF16 tensor-core form adds its tile warp
     return 32 * (group_of<KIND>() + 1 + (KIND == KIND_EUCB ? 1 : 0));
 }
+// Resident blocks per SM of the throughput form of the d = 12 Euclidean sweep:
+// the register cap that lets this many blocks share an SM (96 registers a
+// thread for four 160-thread blocks, against the compiler's 128 and three).
+#ifndef DTW_EUC_MINB
+#define DTW_EUC_MINB 4
+#endif
+constexpr int kEucMinB = DTW_EUC_MINB;
 constexpr int kGMax = 8;  // the frame ring partition covers up to 8 warps
 constexpr int URS = 64;                  // slots (column blocks) of a row ring
 #ifndef DTW_SWEEP_KC
@@ -1387,7 +1394,7 @@ __device__ __noinline__ void split_phase(const SweepArgs& A, SM& sm) {
 // two payload words per column; untagged integer sweeps use one.  FULL: steady
 // groups run fully unrolled (integer variant 3).
 template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL>
-__global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_constant__ SweepArgs A) {
+__device__ __forceinline__ void sweep_body(const SweepArgs& A) {
     constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
     constexpr int kG = group_of<KIND>();
     using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>;
@@ -1577,12 +1584,30 @@ __global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_
     }
 }
 
+// The kernel: with the compiler's register count (MB = 0), or with the count
+// that lets MB blocks reside on an SM.
+template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL>
+__global__ void __launch_bounds__(threads_of<KIND>()) sweep_kernel(const __grid_constant__ SweepArgs A) {
+    sweep_body<KIND, R, U, DIM, TAGS, FULL>(A);
+}
+template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL, int MB>
+__global__ void __launch_bounds__(threads_of<KIND>(), MB) sweep_kernel_mb(const __grid_constant__ SweepArgs A) {
+    sweep_body<KIND, R, U, DIM, TAGS, FULL>(A);
+}
+template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL, int MB>
+constexpr auto sweep_entry() {
+    if constexpr (MB > 0)
+        return &sweep_kernel_mb<KIND, R, U, DIM, TAGS, FULL, MB>;
+    else
+        return &sweep_kernel<KIND, R, U, DIM, TAGS, FULL>;
+}
+
 // ---------------------------------------------------------------- launchers
 
 // Grid: one block per ticket up to a full persistent grid.  With fewer tickets
 // than SMs every block gets an SM of its own, so a level with few bands spreads
 // its warps over the schedulers of the whole GPU.
-template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL = false>
+template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL = false, int MB = 0>
 static cudaError_t setup_one(int* nb_out) {
     constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
     constexpr size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>();
@@ -1597,11 +1622,11 @@ static cudaError_t setup_one(int* nb_out) {
     if (dev < 0 || dev >= kDevs) return cudaErrorInvalidDevice;
     int v = nb[dev].load(std::memory_order_acquire);
     if (v == 0) {
-        e = cudaFuncSetAttribute(sweep_kernel<KIND, R, U, DIM, TAGS, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(sweep_entry<KIND, R, U, DIM, TAGS, FULL, MB>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<KIND, R, U, DIM, TAGS, FULL>, threads_of<KIND>(), smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_entry<KIND, R, U, DIM, TAGS, FULL, MB>(), threads_of<KIND>(), smem);
         v = n < 1 ? 1 : n;
         nb[dev].store(v, std::memory_order_release);
     }
@@ -1609,17 +1634,17 @@ static cudaError_t setup_one(int* nb_out) {
     return cudaSuccess;
 }
 
-template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL = false>
+template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL = false, int MB = 0>
 static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blocks, cudaStream_t st) {
     constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
     constexpr size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>();
     int nb = 0;
-    cudaError_t e = setup_one<KIND, R, U, DIM, TAGS, FULL>(&nb);
+    cudaError_t e = setup_one<KIND, R, U, DIM, TAGS, FULL, MB>(&nb);
     if (e != cudaSuccess) return e;
     long long grid = (long long)num_sms * nb;
     if (max_blocks > 0 && max_blocks < grid) grid = max_blocks;
     if (max_blocks < 0 || grid < 1) grid = 1;
-    sweep_kernel<KIND, R, U, DIM, TAGS, FULL><<<(unsigned)grid, threads_of<KIND>(), smem, st>>>(A);
+    sweep_entry<KIND, R, U, DIM, TAGS, FULL, MB>()<<<(unsigned)grid, threads_of<KIND>(), smem, st>>>(A);
     return cudaGetLastError();
 }
 
@@ -1659,13 +1684,25 @@ cudaError_t sweep_prepare(int kind, int d, bool tags, int variant) {
     if (kind == KIND_LOCAL) return setup_one<KIND_LOCAL, kIntR, kIntU, 1, false>(&nb);
     if (kind == KIND_EUCB) return setup_one<KIND_EUCB, 1, 2, 64, false>(&nb);
     if (kind == KIND_EUCF) {
+        if (d == 12 && variant == 1) return setup_one<KIND_EUCF, kEucR, kEucU, 12, false, false, kEucMinB>(&nb);
         if (d == 12) return setup_one<KIND_EUCF, kEucR, kEucU, 12, false>(&nb);
         if (d == 64) return setup_one<KIND_EUCF, 1, 2, 64, false>(&nb);
         return setup_one<KIND_EUCF, 2, 2, 0, false>(&nb);
     }
+    if (d == 12 && variant == 1) return setup_one<KIND_EUC, kEucR, kEucU, 12, false, false, kEucMinB>(&nb);
     if (d == 12) return setup_one<KIND_EUC, kEucR, kEucU, 12, false>(&nb);
     if (d == 64) return setup_one<KIND_EUC, 1, 2, 64, false>(&nb);
     return setup_one<KIND_EUC, 2, 2, 0, false>(&nb);
+}
+
+int sweep_variant_for(int kind, int d, int variant, long long tickets0, int num_sms) {
+    if (int_kind(kind)) return variant;
+    if ((kind != KIND_EUC && kind != KIND_EUCF) || d != 12) return 0;
+    int nb = 0;
+    const cudaError_t e = kind == KIND_EUC ? setup_one<KIND_EUC, kEucR, kEucU, 12, false>(&nb)
+                                           : setup_one<KIND_EUCF, kEucR, kEucU, 12, false>(&nb);
+    if (e != cudaSuccess) return 0;  // the launch reports the error
+    return tickets0 > (long long)nb * num_sms ? 1 : 0;
 }
 
 cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, long long max_blocks,
@@ -1689,10 +1726,14 @@ cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num
     if (kind == KIND_LOCAL) return launch_one<KIND_LOCAL, kIntR, kIntU, 1, false>(A, num_sms, max_blocks, st);
     if (kind == KIND_EUCB) return launch_one<KIND_EUCB, 1, 2, 64, false>(A, num_sms, max_blocks, st);
     if (kind == KIND_EUCF) {
+        if (d == 12 && variant == 1)
+            return launch_one<KIND_EUCF, kEucR, kEucU, 12, false, false, kEucMinB>(A, num_sms, max_blocks, st);
         if (d == 12) return launch_one<KIND_EUCF, kEucR, kEucU, 12, false>(A, num_sms, max_blocks, st);
         if (d == 64) return launch_one<KIND_EUCF, 1, 2, 64, false>(A, num_sms, max_blocks, st);
         return launch_one<KIND_EUCF, 2, 2, 0, false>(A, num_sms, max_blocks, st);
     }
+    if (d == 12 && variant == 1)
+        return launch_one<KIND_EUC, kEucR, kEucU, 12, false, false, kEucMinB>(A, num_sms, max_blocks, st);
     if (d == 12) return launch_one<KIND_EUC, kEucR, kEucU, 12, false>(A, num_sms, max_blocks, st);
     // d = 64: one row per lane (its frame in registers), column frames read in place
     if (d == 64) return launch_one<KIND_EUC, 1, 2, 64, false>(A, num_sms, max_blocks, st);
