@@ -606,22 +606,23 @@ PRECISION_FORMS = (
 
 
 def measure_precision(steps: int, warmup: int, forms=("f32cost_f64dp", "f32cost_f32kahan", "bf16cost_f32kahan"),
-                      discrepancy: bool = True):
+                      discrepancy: bool = True, size=None):
     """The orchestral-length pair (60000 x 64-d MFCC-like frames vs a 75000-frame
     warp plus noise) in the given precision forms: time per alignment, GCUPS,
     relative error against the FP64 oracle's stored optimum, and the roofline of
     the form's binding bound (FP64 DP: the FP64-add pipe, one add per processed
     cell; compensated FP32 forms: the ALU issue rate at the form's algorithmic
-    instructions per cell)."""
+    instructions per cell).  ``size`` (M, N): a smaller pair from the same
+    generator, for profiling; it has no stored optimum."""
     import torch
 
     import paper_2008_02734_b300 as dtw
 
-    X, Y = synth.workload_precision()
+    X, Y = synth.workload_precision() if size is None else synth.workload_precision(M=size[0], N=size[1])
     M, N = len(X), len(Y)
     Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
     stream = torch.cuda.current_stream()
-    c_ref = golden_mfcc_cost()
+    c_ref = golden_mfcc_cost() if size is None else None
     sms, mhz, src = _peak_rates()
     issue = sms * 4 * 32 * mhz * 1e6 / 1e9  # lane instructions per ns
     out, paths = {}, {}
@@ -665,16 +666,17 @@ def measure_precision(steps: int, warmup: int, forms=("f32cost_f64dp", "f32cost_
         e = err.cpu().numpy().ravel()
         disc = {"of": "bf16cost_f32kahan path vs f32cost_f64dp path", "cells": int(err.shape[1]), "max_frames": emax,
                 "within_frames": {str(f): float(np.mean(e <= f)) for f in (0, 1, 2, 22, 43)}}
-    return {"workload": "orchestral-length pair: 60000 x 64-d MFCC-like vs 75000-frame warp + N(0,0.1^2)",
+    return {"workload": f"orchestral-length pair: {M} x 64-d MFCC-like vs {N}-frame warp + N(0,0.1^2)",
             "M": M, "N": N, "steps": steps, "oracle_cost": c_ref,
-            "oracle_source": "tests/golden/mfcc_pair_60000x75000.txt", "forms": out, "path_discrepancy": disc}
+            "oracle_source": "tests/golden/mfcc_pair_60000x75000.txt" if size is None else None, "forms": out,
+            "path_discrepancy": disc}
 
 
 def run_precision_workload(args):
     """The orchestral-length pair in each precision form; value is the exact
     (FP32 cost, FP64 DP) form's GCUPS."""
     forms = tuple(args.forms.split(",")) if args.forms else ("f32cost_f64dp", "f32cost_f32kahan", "bf16cost_f32kahan")
-    r = measure_precision(args.steps, args.warmup, forms=forms)
+    r = measure_precision(args.steps, args.warmup, forms=forms, size=parse_size(args.size))
     ex = r["forms"].get("f32cost_f64dp") or next(iter(r["forms"].values()))
     line = {"metric": METRIC, "value": ex["gcups"], "unit": "GCUPS", "n_gpus": 1,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ex["ms"],
@@ -992,7 +994,7 @@ def main():
     ap.add_argument("--fused-split", type=int, default=None, choices=[0, 1, 2],
                     help="where each level's split runs: 0 own launch, 1 library default, 2 in the sweep kernel")
     ap.add_argument("--size", default=None,
-                    help="MxN: the pair workloads (int_pair, plain_float) resized, same generator (profiling)")
+                    help="MxN: the pair workloads (int_pair, plain_float, precision) resized, same generator (profiling)")
     ap.add_argument("--split-windows", type=int, default=None,
                     help="windows of split rows per box and level, at most (library default 7; 1: one split row)")
     ap.add_argument("--no-graph", action="store_true",
