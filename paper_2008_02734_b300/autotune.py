@@ -23,6 +23,10 @@ from . import synth
 VARIANTS = (0, 1, 2, 3)
 WINDOWS = (1, 7, 15)
 BASE_AREAS = (4096, 16384, 32768)
+# split windows tried for a batch: the integer batch takes 3, the d=12 chroma
+# batch 15 (more of its work in the first level, whose sweeps keep every SM
+# busy, and fewer of the deeper levels, which do not)
+BATCH_WINDOWS = (1, 3, 7, 15)
 DEFAULT_WINDOWS = 7
 
 
@@ -62,7 +66,7 @@ def tune(M: int, N: int, *, variants=VARIANTS, windows=WINDOWS, base_areas=BASE_
             "table": table}
 
 
-def tune_batch(Xs, Ys, *, base_areas=BASE_AREAS, windows=(1, 3, 7), reps: int = 2, apply: bool = True,
+def tune_batch(Xs, Ys, *, base_areas=BASE_AREAS, windows=BATCH_WINDOWS, reps: int = 2, apply: bool = True,
                **align_kw) -> dict:
     """The base-case cutoff and split windows for a batch: times align_batch on
     the caller's own pairs (device tensors) for every candidate (median of
