@@ -498,7 +498,8 @@ def measure_batch(steps: int, warmup: int, tune: bool = True, check: bool = True
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     tuned = None
     if tune:
-        # the library's autotuner picks the base-case cutoff on this batch
+        # the library's autotuner picks the cutoff, the split windows and (integer
+        # data) the lane block on this batch
         from paper_2008_02734_b300 import autotune
         tuned = autotune.tune_batch(Xs, Ys)
     for _ in range(max(warmup, 3)):
@@ -559,7 +560,8 @@ def measure_batch(steps: int, warmup: int, tune: bool = True, check: bool = True
         "roofline": roof,
         "max_rel_err_vs_oracle": err, "oracle_source": "tests/golden/" + golden,
         "l2": "flushed between steps",
-        "autotuned": None if tuned is None else {"base_area": tuned["base_area"], "split_windows": tuned["windows"]},
+        "autotuned": None if tuned is None else {"base_area": tuned["base_area"], "split_windows": tuned["windows"],
+                                                "sweep_variant": tuned["variant"]},
     }
 
 

@@ -27,6 +27,8 @@ BASE_AREAS = (4096, 16384, 32768)
 # batch 15 (more of its work in the first level, whose sweeps keep every SM
 # busy, and fewer of the deeper levels, which do not)
 BATCH_WINDOWS = (1, 3, 7, 15)
+# integer lane blocks tried for a batch: R=4 (variant 0) and R=8 (variant 2)
+BATCH_INT_VARIANTS = (0, 2)
 DEFAULT_WINDOWS = 7
 
 
@@ -66,21 +68,27 @@ def tune(M: int, N: int, *, variants=VARIANTS, windows=WINDOWS, base_areas=BASE_
             "table": table}
 
 
-def tune_batch(Xs, Ys, *, base_areas=BASE_AREAS, windows=BATCH_WINDOWS, reps: int = 2, apply: bool = True,
-               **align_kw) -> dict:
-    """The base-case cutoff and split windows for a batch: times align_batch on
-    the caller's own pairs (device tensors) for every candidate (median of
-    ``reps`` after one warm-up) and returns {"base_area", "windows", "ms",
-    "table"}; with ``apply`` the fastest is set.  Results do not depend on
-    either (integer paths are canonical; float paths are optimal within the
-    float tolerance)."""
+def tune_batch(Xs, Ys, *, base_areas=BASE_AREAS, windows=BATCH_WINDOWS, variants=None, reps: int = 2,
+               apply: bool = True, **align_kw) -> dict:
+    """The base-case cutoff, split windows and (integer data) lane block for a
+    batch: times align_batch on the caller's own pairs (device tensors) for
+    every candidate (median of ``reps`` after one warm-up) and returns
+    {"variant", "base_area", "windows", "ms", "table"}; with ``apply`` the
+    fastest is set.  ``variants`` defaults to BATCH_INT_VARIANTS for int32 data;
+    float data has one lane block per dimension (variant None: left as it is).
+    Results do not depend on any of them (integer paths are canonical; float
+    paths are optimal within the float tolerance)."""
     import torch
 
     from . import align_batch
 
+    if variants is None:
+        variants = BATCH_INT_VARIANTS if Xs[0].dtype == torch.int32 else (None,)
     stream = torch.cuda.current_stream()
     table = []
-    for w, a in itertools.product(windows, base_areas):
+    for v, w, a in itertools.product(variants, windows, base_areas):
+        if v is not None:
+            set_option(OPT_SWEEP_VARIANT, v)
         set_option(OPT_SPLIT_WINDOWS, w)
         set_option(OPT_BASE_AREA, a)
         align_batch(Xs, Ys, **align_kw)
@@ -93,8 +101,11 @@ def tune_batch(Xs, Ys, *, base_areas=BASE_AREAS, windows=BATCH_WINDOWS, reps: in
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         ms.sort()
-        table.append({"windows": w, "base_area": a, "ms": ms[len(ms) // 2]})
+        table.append({"variant": v, "windows": w, "base_area": a, "ms": ms[len(ms) // 2]})
     best = min(table, key=lambda r: r["ms"])
+    if best["variant"] is not None:
+        set_option(OPT_SWEEP_VARIANT, best["variant"] if apply else 0)
     set_option(OPT_SPLIT_WINDOWS, best["windows"] if apply else DEFAULT_WINDOWS)
     set_option(OPT_BASE_AREA, best["base_area"] if apply else 16384)
-    return {"base_area": best["base_area"], "windows": best["windows"], "ms": best["ms"], "table": table}
+    return {"variant": best["variant"], "base_area": best["base_area"], "windows": best["windows"], "ms": best["ms"],
+            "table": table}

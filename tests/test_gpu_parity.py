@@ -368,6 +368,21 @@ def test_batch_autotuner_applies_a_candidate():
         assert oracle.path_cost(x, y, p.cpu().numpy()) == pytest.approx(c_ref, rel=REL_TOL, abs=1e-9)
 
 
+def test_batch_autotuner_integer_lane_blocks():
+    """On int32 data the batch tuner also tries the integer lane blocks; the
+    batch it leaves set still gives the oracle's canonical paths bit for bit."""
+    from paper_2008_02734_b300 import autotune
+    pairs = [synth.int_pair(70 + k, 400 + 60 * k, 380 + 70 * k) for k in range(5)]
+    Xs, Ys = [_cuda(x) for x, _ in pairs], [_cuda(y) for _, y in pairs]
+    r = autotune.tune_batch(Xs, Ys, base_areas=(4096,), windows=(3, 7))
+    assert r["variant"] in autotune.BATCH_INT_VARIANTS and r["windows"] in (3, 7)
+    assert len(r["table"]) == 2 * len(autotune.BATCH_INT_VARIANTS)
+    for (x, y), (p, c) in zip(pairs, dtw.align_batch(Xs, Ys)):
+        p_ref, c_ref = oracle.dtw(x, y)
+        assert c == c_ref
+        assert np.array_equal(p.cpu().numpy(), p_ref)
+
+
 def _golden_mfcc():
     with open(GOLDEN_MFCC) as f:
         rows = [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")]
