@@ -210,7 +210,6 @@ struct Engine {
     }
 
     bool idle() const { return active.empty() && queue.empty(); }
-    bool busy = false;  // counted in g_busy_engines (under the server's mutex)
     LevelCtl* ctl() { return reinterpret_cast<LevelCtl*>(ws + L.ctl); }
     PairDesc* pairs() { return reinterpret_cast<PairDesc*>(ws + L.pairs); }
     PairRes* pres() { return reinterpret_cast<PairRes*>(ws + L.pres); }
@@ -254,11 +253,15 @@ Server& server() {
 }
 
 static bool g_trace = getenv("DTW_SERVE_TRACE") != nullptr;
-// Engines with work.  While another engine has work, an engine's sweeps run one
-// block per SM at most: a group's level of many bands would otherwise hold every
-// SM with persistent blocks, and the other group's blocks (a d=64 block takes
-// most of an SM's shared memory) would wait for that whole level.
-static std::atomic<int> g_busy_engines{0};
+// Engines that exist.  While another engine exists, an engine's sweeps run on
+// 7/8 of the SMs at most, one block per SM: a group's level of many bands would
+// otherwise hold every SM with persistent blocks for the whole level (a level-0
+// block holds its ticket for milliseconds), and a request of another group that
+// arrives meanwhile would wait for that level to end.  Its plan kernel (1024
+// threads of 64 registers) and float split kernel (256 threads of about 250)
+// each need a whole SM's register file, which only an SM without a sweep block
+// has; a d=64 sweep block needs most of an SM's shared memory.
+static std::atomic<int> g_live_engines{0};
 static double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -405,7 +408,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
         SweepArgs sa{d_sweeps, ctl(), reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres,
                      d, spin_limit, -1};
         sa.tmap = reinterpret_cast<const int2*>(ws + L.tmap);
-        const long long cap = g_busy_engines.load(std::memory_order_relaxed) > 1 ? num_sms : 0;
+        const long long cap = g_live_engines.load(std::memory_order_relaxed) > 1 ? num_sms - num_sms / 8 : 0;
         if (e == cudaSuccess) e = launch_sweep(kind, d, kind == KIND_ABS, sa, num_sms, cap, st);
         SplitArgs sp{cur, n_cur, pairs(), pres(), kind, d, halo, d_sweeps, d_sres, ws + L.outpool, nxt, d_base,
                      ctl(), base_area, (int)L.cap_box, (int)L.cap_base, d_boxdone, ws + L.partials, -1, num_sms};
@@ -490,10 +493,6 @@ void Server::engine_loop(Engine* en) {
             std::unique_lock<std::mutex> g(mu);
             cv.wait(g, [&] { return !en->idle(); });
             en->running = true;
-            if (!en->busy) {
-                en->busy = true;
-                g_busy_engines.fetch_add(1);
-            }
             if (!en->ws) {
                 // take the engine's share of what the budget has left; wait while
                 // another engine still holds more than its share
@@ -537,10 +536,6 @@ void Server::engine_loop(Engine* en) {
                 }
                 en->queue.clear();
                 en->running = false;
-                if (en->busy && en->idle()) {
-                    en->busy = false;
-                    g_busy_engines.fetch_sub(1);
-                }
                 continue;
             }
         }
@@ -569,10 +564,6 @@ void Server::engine_loop(Engine* en) {
             inflight.erase(r.first);
         }
         en->running = false;
-        if (en->busy && en->idle()) {
-            en->busy = false;
-            g_busy_engines.fetch_sub(1);
-        }
         if (budget && en->ws && en->idle()) {
             // an idle engine whose share has drifted gives its arena back
             const double want = (double)target_arena(en), have = (double)en->arena;
@@ -617,6 +608,7 @@ int64_t dtw_submit(const dtw_request* r) {
         en->kind = kind;
         en->d = key.second;
         s.demand[en.get()] = 0.0;
+        g_live_engines.fetch_add(1);
         std::thread(&Server::engine_loop, &s, en.get()).detach();
     }
     // the group's demand: level scratch and features, linear in M + N
