@@ -476,6 +476,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         pa.tmap = d_tmap;
         pa.prog = d_prog;
         pa.nwin = c.split_windows;
+        pa.whole_groups = sweep_whole_groups(kind, d);
         pa.cap_tickets = L.cap_tickets;
         pa.map_min = c.num_sms;
         e = launch_plan(pa, st);
@@ -503,6 +504,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
         pn.map_min = c.num_sms;
         pn.prog = d_prog;
         pn.nwin = c.split_windows;
+        pn.whole_groups = sweep_whole_groups(kind, d);
         sa.prog = d_prog;
         sa.split = sp;
         const std::vector<long long> key{(long long)(uintptr_t)ws, (long long)L.total, L.cap_box, L.cap_base,
@@ -550,6 +552,7 @@ int run_batch(Ctx& c, int B, const void* const* X, const int64_t* M, const void*
             pa.tmap = d_tmap;
             pa.prog = d_prog;
             pa.nwin = c.split_windows;
+            pa.whole_groups = sweep_whole_groups(kind, d);
             pa.cap_tickets = L.cap_tickets;
             pa.map_min = c.num_sms;
             if (e == cudaSuccess) e = launch_plan(pa, st);

@@ -55,6 +55,10 @@ constexpr int kSweepVariants = 4;
 int sweep_block_cols(int kind, int d, int variant = 0);  // U
 int sweep_band_rows(int kind, int d, int variant = 0);   // 32*R
 int sweep_group_bands(int kind);  // bands per ticket (compute warps per block)
+// every ticket of the kind's sweep must hold bands of one sweep only (the BF16
+// form's MMAs, the d = 64 FP32-cost kinds' tight frame ring): the plan pads each
+// sweep's bands to whole groups
+bool sweep_whole_groups(int kind, int d);
 // max_blocks > 0 caps the grid (one block per ticket suffices); 0: a full persistent grid.
 cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num_sms, long long max_blocks,
                          cudaStream_t st, int variant = 0);
@@ -93,6 +97,7 @@ struct PlanArgs {
                                // their tickets run at once, so their order does not matter)
     int* prog = nullptr;       // non-null: reset the sweeps' split-row progress words (fused split)
     int nwin = 1;              // windows of split rows per box at most (odd; 1: one split row per box)
+    bool whole_groups = false; // pad each sweep's bands to whole groups of G (sweep_whole_groups)
 };
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st);
 

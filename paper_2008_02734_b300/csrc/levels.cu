@@ -217,10 +217,11 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
             sw.ematch = pd.ematch;
             sw.floor = a.local == 1 ? 1 : 0;
             nb = sw.nbands;
-            // the BF16 form's block takes a group of G bands of one sweep (the
-            // M rows of its MMAs): in the plain ticket order each sweep's bands
+            // a block that must take a group of G bands of one sweep (the BF16
+            // form: the M rows of its MMAs; the d = 64 FP32-cost kinds: their
+            // tight frame ring): in the plain ticket order each sweep's bands
             // start on a whole group (the padding bands stay idle)
-            if (a.kind == KIND_EUCB) nb = (nb + a.G - 1) / a.G * a.G;
+            if (a.whole_groups) nb = (nb + a.G - 1) / a.G * a.G;
             // boundary words per column: one for an untagged integer sweep, two otherwise
             const int nw = (int_kind(a.kind) && sw.tag_row < 0) ? 1 : 2;
             nbuf = (long long)nw * sw.nblk * a.U;

@@ -404,6 +404,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
         pa.cap_tickets = L.cap_tickets;
         pa.map_min = num_sms;
         pa.nwin = windows;
+        pa.whole_groups = sweep_whole_groups(kind, d);
         e = launch_plan(pa, st);
         SweepArgs sa{d_sweeps, ctl(), reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres,
                      d, spin_limit, -1};
@@ -422,6 +423,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
     pn.cap_tickets = L.cap_tickets;
     pn.map_min = num_sms;
     pn.nwin = windows;
+    pn.whole_groups = sweep_whole_groups(kind, d);
     if (e == cudaSuccess) e = launch_plan(pn, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_flags, 0, 4 * kSlots, st);
     if (e == cudaSuccess) e = launch_mark_pairs(nxt, ctl(), d_flags, st);

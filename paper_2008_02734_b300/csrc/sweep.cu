@@ -491,12 +491,19 @@ __device__ __forceinline__ void tc_ld32(uint32_t ta, float* v) {
 // reader.  With two warps per block (the integer kind, 16-byte slots) the
 // region is 512 slots and a stream gets 512 (two readers) or 256 (one); with two
 // warps or fewer and large slots (more than 256 bytes) the least room applies:
-// 128 slots, a stream 128 (two readers) or 64 (one).
+// 128 slots, a stream 128 (two readers) or 64 (one).  Four warps with large
+// slots (the d = 64 FP32-cost kinds, 528-byte slots): every ticket holds bands of
+// one sweep only (the plan pads each sweep's bands to whole groups), so the one
+// stream gets the least room of four readers, 40 x 3 + 31 + 8 + 32 = 191
+// blocks, as 192 slots (101 KB: two blocks per SM instead of one).
+constexpr int kYTight = 192;
+__host__ __device__ constexpr bool ytight(int G, bool big) { return big && G > 2 && G <= 4; }
 __host__ __device__ constexpr int kYSlotsOf(int G, bool big = false) {
-    return G > 4 ? 1024 : (G > 2 ? 320 : (big ? 128 : 512));
+    return G > 4 ? 1024 : (ytight(G, big) ? kYTight : (G > 2 ? 320 : (big ? 128 : 512)));
 }
 __host__ __device__ constexpr int yslots(int G, int w, bool big = false) {
-    return (G <= 2 && !big) ? (w >= 2 ? 512 : 256) : (w >= 5 ? 512 : (w >= 3 ? 256 : (w == 2 ? 128 : 64)));
+    return ytight(G, big) ? kYTight
+                          : ((G <= 2 && !big) ? (w >= 2 ? 512 : 256) : (w >= 5 ? 512 : (w >= 3 ? 256 : (w == 2 ? 128 : 64))));
 }
 __host__ __device__ constexpr int ychunk(int w) { return w >= 2 ? 32 : 16; }
 
@@ -610,6 +617,10 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     constexpr int YSW = SM::YSW;
     const uint32_t* yr = sm.yring + (size_t)sm.ybase[ys] * YSW;
     const int ymask = sm.yrs[ys] - 1;
+    // the frame ring slot of column block cb (cb >= -31); a tight ring is not a
+    // power of two
+    constexpr bool kTight = ytight(group_of<KIND>(), SM::kBigSlot);
+    auto yslot = [&](int cb) -> int { return kTight ? (int)((unsigned)(cb + kYTight) % (unsigned)kYTight) : (cb & ymask); };
     if (!has_above) {
         // the row above the sweep: D(-1, q) = infinity (Eq. "dtwboundary")
         uint32_t w[NW];
@@ -721,7 +732,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     constexpr bool YPF = int_kind(KIND) || DTW_EUC_YPREFETCH != 0 || YW == 0;
     auto load_frames = [&](int cb, YF* dst) {
         if constexpr (YW > 0) {
-            const uint32_t* ys = yr + (cb & ymask) * YSW;
+            const uint32_t* ys = yr + yslot(cb) * YSW;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if constexpr (std::is_same<YF, Frame<KIND, DIM>>::value) dst[u].load_shared(ys + u * YW);
@@ -736,7 +747,7 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
             // tensor-core form: costs come from the tiles; otherwise frames are loaded by the step itself
         } else if constexpr (int_kind(KIND) && U % 4 == 0) {
             uint32_t w[U];
-            ld_shared_words<U>(yr + (cb & ymask) * YSW, w);
+            ld_shared_words<U>(yr + yslot(cb) * YSW, w);
 #pragma unroll
             for (int u = 0; u < U; ++u) ny[u].v = (int32_t)w[u];
         } else if constexpr (YW > 0) {
@@ -1480,7 +1491,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& A) {
                 if (gb < n_bands) {
                     si = find_sweep(A.sweeps, n_sweeps, gb);
                     band = (int)(gb - A.sweeps[si].band_begin);
-                    // the BF16 form's plan pads each sweep's bands to whole groups
+                    // plans with whole groups pad each sweep's bands to a multiple of G
                     if (band >= A.sweeps[si].nbands) si = -1;
                 }
             }
@@ -1504,6 +1515,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& A) {
                 sm.yrs[j] = yslots(kG, w, SM::kBigSlot);
                 sm.ychb[j] = ychunk(w);
                 if (readers[j] > 0) base += yslots(kG, w, SM::kBigSlot);
+            }
+            if (base > kYSlotsOf(kG, SM::kBigSlot)) {
+                // the streams do not fit the frame region (a tight ring, whose
+                // tickets must hold one sweep): fail the level, run nothing
+                set_error(A.ctl, ERR_CAPACITY, -2);
+                for (int g = 0; g < kG; ++g) sweep_of[g] = -1;
             }
             if constexpr (TCK) {
                 // tiles of this ticket: the sweep's columns in 32s (every active
@@ -1663,6 +1680,9 @@ int sweep_band_rows(int kind, int d, int variant) {
     if (kind == KIND_ABS) return 32 * kIntRVar[(unsigned)variant < (unsigned)kSweepVariants ? variant : 0];
     if (edit_kind(kind)) return 32 * kIntR;
     return d == 12 ? 32 * kEucR : (d == 64 ? 32 : 64);
+}
+bool sweep_whole_groups(int kind, int d) {
+    return kind == KIND_EUCB || ((kind == KIND_EUC || kind == KIND_EUCF) && d == 64);
 }
 int sweep_group_bands(int kind) {
     return int_kind(kind) ? group_of<KIND_ABS>() : (kind == KIND_EUCB ? group_of<KIND_EUCB>() : group_of<KIND_EUC>());
