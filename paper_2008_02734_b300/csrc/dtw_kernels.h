@@ -45,6 +45,8 @@ struct SweepArgs {
     // queue empty run the level's split work items (split) while the sweeps end.
     int* prog = nullptr;
     SplitArgs split{};
+    int sms = 0;     // SMs of the device (set by the launch)
+    int ytight = 0;  // d = 64 FP32-cost kinds: the launch allocated the tight frame ring
 };
 
 // Sweep variants
@@ -67,7 +69,9 @@ cudaError_t sweep_prepare(int kind, int d, bool tags, int variant = 0);
 // The sweep variant a call runs: the integer kinds keep `variant`; the d = 12
 // Euclidean kinds take their throughput form (variant 1: more resident blocks,
 // fewer registers) when the first level's tickets, about `tickets0`, outnumber
-// the blocks the default form keeps resident; other kinds variant 0.
+// the blocks the default form keeps resident; the d = 64 FP32-cost kinds take
+// the tight frame ring (variant 1: two blocks per SM) when they are three times
+// the SMs or more; other kinds variant 0.
 int sweep_variant_for(int kind, int d, int variant, long long tickets0, int num_sms);
 
 // Level planning modes

@@ -492,18 +492,22 @@ __device__ __forceinline__ void tc_ld32(uint32_t ta, float* v) {
 // region is 512 slots and a stream gets 512 (two readers) or 256 (one); with two
 // warps or fewer and large slots (more than 256 bytes) the least room applies:
 // 128 slots, a stream 128 (two readers) or 64 (one).  Four warps with large
-// slots (the d = 64 FP32-cost kinds, 528-byte slots): every ticket holds bands of
-// one sweep only (the plan pads each sweep's bands to whole groups), so the one
-// stream gets the least room of four readers, 40 x 3 + 31 + 8 + 32 = 191
-// blocks, as 192 slots (101 KB: two blocks per SM instead of one).
+// slots (the d = 64 FP32-cost kinds, 528-byte slots) can also run with a tight
+// ring: every ticket holds bands of one sweep only (the plan pads each sweep's
+// bands to whole groups), so the one stream gets the least room of four
+// readers, 40 x 3 + 31 + 8 + 32 = 191 blocks, as 192 slots (101 KB instead of
+// 169: two blocks per SM instead of one).  The launch picks the ring: the
+// tight one leaves out the end of the region (the ring is the last member of
+// the block's shared memory).
 constexpr int kYTight = 192;
-__host__ __device__ constexpr bool ytight(int G, bool big) { return big && G > 2 && G <= 4; }
+__host__ __device__ constexpr bool ytight_capable(int G, bool big) { return big && G > 2 && G <= 4; }
 __host__ __device__ constexpr int kYSlotsOf(int G, bool big = false) {
-    return G > 4 ? 1024 : (ytight(G, big) ? kYTight : (G > 2 ? 320 : (big ? 128 : 512)));
+    return G > 4 ? 1024 : (G > 2 ? 320 : (big ? 128 : 512));
 }
-__host__ __device__ constexpr int yslots(int G, int w, bool big = false) {
-    return ytight(G, big) ? kYTight
-                          : ((G <= 2 && !big) ? (w >= 2 ? 512 : 256) : (w >= 5 ? 512 : (w >= 3 ? 256 : (w == 2 ? 128 : 64))));
+__host__ __device__ constexpr int yslots(int G, int w, bool big = false, bool tight = false) {
+    return (tight && ytight_capable(G, big))
+               ? kYTight
+               : ((G <= 2 && !big) ? (w >= 2 ? 512 : 256) : (w >= 5 ? 512 : (w >= 3 ? 256 : (w == 2 ? 128 : 64))));
 }
 __host__ __device__ constexpr int ychunk(int w) { return w >= 2 ? 32 : 16; }
 
@@ -522,13 +526,14 @@ struct StripSmem {
     static constexpr int YSW = FrameSlot<U, YW>::W;  // words per frame ring slot
     __align__(16) uint32_t uring[G + 1][URS * U * NWMAX];  // ring G: the last warp's row, for the loader
     static constexpr bool kBigSlot = YSW > 64;
-    __align__(16) uint32_t yring[YW > 0 ? kYSlotsOf(G, kBigSlot) * YSW : 4];
     int uprog[G + 1], ucons[G + 1], yprog[G], ycons[G];
     int ybase[G], yrs[G], ychb[G];  // per stream: first slot, slots, blocks per loader round
     int sweep_of[G], band_of[G], ystream[G];
     long long ticket;
     int stop;
     int ntiles;  // BF16 tensor-core form: tiles of this ticket's sweep
+    // last: a launch with the tight ring allocates only its first kYTight slots
+    __align__(16) uint32_t yring[YW > 0 ? kYSlotsOf(G, kBigSlot) * YSW : 4];
 };
 
 // Column frame held by a lane: in registers, or (large fixed dimensions) a
@@ -619,8 +624,8 @@ __device__ __noinline__ void run_band(const Sweep* __restrict__ sp, int sweep_id
     const int ymask = sm.yrs[ys] - 1;
     // the frame ring slot of column block cb (cb >= -31); a tight ring is not a
     // power of two
-    constexpr bool kTight = ytight(group_of<KIND>(), SM::kBigSlot);
-    auto yslot = [&](int cb) -> int { return kTight ? (int)((unsigned)(cb + kYTight) % (unsigned)kYTight) : (cb & ymask); };
+    const bool tight = ytight_capable(group_of<KIND>(), SM::kBigSlot) && A.ytight != 0;
+    auto yslot = [&](int cb) -> int { return tight ? (int)((unsigned)(cb + kYTight) % (unsigned)kYTight) : (cb & ymask); };
     if (!has_above) {
         // the row above the sweep: D(-1, q) = infinity (Eq. "dtwboundary")
         uint32_t w[NW];
@@ -1361,9 +1366,14 @@ __device__ __forceinline__ void run_band_s(bool special, const Sweep* sp, int si
 // the operands, norms, cost tiles and synchronisation of TcShared.
 static_assert(kGEucB == kTcBands && kTcBands * 32 == kTcRows, "the BF16 form's block holds the M = 128 rows of one MMA");
 template <int KIND, int U, int NWMAX, int DIM>
-constexpr size_t strip_smem_bytes() {
-    constexpr size_t base = (sizeof(StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>) + 127) & ~(size_t)127;
-    return base + (KIND == KIND_EUCB ? sizeof(TcShared) + 128 : 0);
+constexpr size_t strip_smem_bytes(bool tight = false) {
+    using SM = StripSmem<U, NWMAX, FrameWords<KIND, DIM>::v, group_of<KIND>()>;
+    constexpr size_t base = (sizeof(SM) + 127) & ~(size_t)127;
+    // the tight ring: the region's slots beyond kYTight are not allocated
+    constexpr size_t cut = ytight_capable(group_of<KIND>(), SM::kBigSlot)
+                               ? (size_t)(kYSlotsOf(group_of<KIND>(), SM::kBigSlot) - kYTight) * SM::YSW * 4
+                               : 0;
+    return base - (tight ? cut : 0) + (KIND == KIND_EUCB ? sizeof(TcShared) + 128 : 0);
 }
 
 // Index of the sweep holding level band gb: the last sweep whose band_begin is
@@ -1428,6 +1438,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& A) {
     // with fewer tickets than blocks only the first n_tickets blocks work: a grid
     // fixed in advance then still puts a level's few strips on separate SMs
     if ((long long)blockIdx.x >= n_tickets) return;
+    const bool ytight = ytight_capable(kG, SM::kBigSlot) && A.ytight != 0;
+    // tight ring: a second block per SM pays only while tickets are plentiful
+    // (three rounds of one block per SM or more); with fewer, the SMs holding
+    // two blocks slow their bands and, through the band chain, the whole sweep
+    if (ytight && n_tickets < 3LL * A.sms && (int)blockIdx.x >= A.sms) return;
     if constexpr (TCK) {
         // the block's TMEM slots (its tile warp allocates and frees them), the
         // slots' mbarriers (one arrival: the MMAs' commit) and the counters
@@ -1512,11 +1527,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& A) {
             for (int j = 0; j < kG; ++j) {
                 const int w = readers[j] > 0 ? readers[j] : 1;
                 sm.ybase[j] = base;
-                sm.yrs[j] = yslots(kG, w, SM::kBigSlot);
+                sm.yrs[j] = yslots(kG, w, SM::kBigSlot, ytight);
                 sm.ychb[j] = ychunk(w);
-                if (readers[j] > 0) base += yslots(kG, w, SM::kBigSlot);
+                if (readers[j] > 0) base += yslots(kG, w, SM::kBigSlot, ytight);
             }
-            if (base > kYSlotsOf(kG, SM::kBigSlot)) {
+            if (base > (ytight ? kYTight : kYSlotsOf(kG, SM::kBigSlot))) {
                 // the streams do not fit the frame region (a tight ring, whose
                 // tickets must hold one sweep): fail the level, run nothing
                 set_error(A.ctl, ERR_CAPACITY, -2);
@@ -1625,43 +1640,49 @@ constexpr auto sweep_entry() {
 // than SMs every block gets an SM of its own, so a level with few bands spreads
 // its warps over the schedulers of the whole GPU.
 template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL = false, int MB = 0>
-static cudaError_t setup_one(int* nb_out) {
+static cudaError_t setup_one(int* nb_out, bool tight = false) {
     constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
     constexpr size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>();
     static_assert(smem <= 227 * 1024, "the block's rings exceed the shared memory of an SM (see yslots)");
-    // per device: the attribute is set in (and the occupancy read for) the
-    // context of the device that is current
+    // per device and ring: the attribute is set in (and the occupancy read for)
+    // the context of the device that is current; the attribute allows the full
+    // region, a launch with the tight ring asks for less
     constexpr int kDevs = 64;
-    static std::atomic<int> nb[kDevs];
+    static std::atomic<int> nb[kDevs][2];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kDevs) return cudaErrorInvalidDevice;
-    int v = nb[dev].load(std::memory_order_acquire);
+    int v = nb[dev][tight ? 1 : 0].load(std::memory_order_acquire);
     if (v == 0) {
         e = cudaFuncSetAttribute(sweep_entry<KIND, R, U, DIM, TAGS, FULL, MB>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_entry<KIND, R, U, DIM, TAGS, FULL, MB>(), threads_of<KIND>(), smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_entry<KIND, R, U, DIM, TAGS, FULL, MB>(), threads_of<KIND>(),
+                                                      strip_smem_bytes<KIND, U, NWMAX, DIM>(tight));
         v = n < 1 ? 1 : n;
-        nb[dev].store(v, std::memory_order_release);
+        nb[dev][tight ? 1 : 0].store(v, std::memory_order_release);
     }
     *nb_out = v;
     return cudaSuccess;
 }
 
 template <int KIND, int R, int U, int DIM, bool TAGS, bool FULL = false, int MB = 0>
-static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blocks, cudaStream_t st) {
+static cudaError_t launch_one(const SweepArgs& A, int num_sms, long long max_blocks, cudaStream_t st,
+                              bool tight = false) {
     constexpr int NWMAX = (!int_kind(KIND) || TAGS) ? 2 : 1;
-    constexpr size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>();
+    const size_t smem = strip_smem_bytes<KIND, U, NWMAX, DIM>(tight);
     int nb = 0;
-    cudaError_t e = setup_one<KIND, R, U, DIM, TAGS, FULL, MB>(&nb);
+    cudaError_t e = setup_one<KIND, R, U, DIM, TAGS, FULL, MB>(&nb, tight);
     if (e != cudaSuccess) return e;
     long long grid = (long long)num_sms * nb;
     if (max_blocks > 0 && max_blocks < grid) grid = max_blocks;
     if (max_blocks < 0 || grid < 1) grid = 1;
-    sweep_entry<KIND, R, U, DIM, TAGS, FULL, MB>()<<<(unsigned)grid, threads_of<KIND>(), smem, st>>>(A);
+    SweepArgs B = A;
+    B.sms = num_sms;
+    B.ytight = tight ? 1 : 0;
+    sweep_entry<KIND, R, U, DIM, TAGS, FULL, MB>()<<<(unsigned)grid, threads_of<KIND>(), smem, st>>>(B);
     return cudaGetLastError();
 }
 
@@ -1706,18 +1727,22 @@ cudaError_t sweep_prepare(int kind, int d, bool tags, int variant) {
     if (kind == KIND_EUCF) {
         if (d == 12 && variant == 1) return setup_one<KIND_EUCF, kEucR, kEucU, 12, false, false, kEucMinB>(&nb);
         if (d == 12) return setup_one<KIND_EUCF, kEucR, kEucU, 12, false>(&nb);
-        if (d == 64) return setup_one<KIND_EUCF, 1, 2, 64, false>(&nb);
+        if (d == 64) return setup_one<KIND_EUCF, 1, 2, 64, false>(&nb, variant == 1);
         return setup_one<KIND_EUCF, 2, 2, 0, false>(&nb);
     }
     if (d == 12 && variant == 1) return setup_one<KIND_EUC, kEucR, kEucU, 12, false, false, kEucMinB>(&nb);
     if (d == 12) return setup_one<KIND_EUC, kEucR, kEucU, 12, false>(&nb);
-    if (d == 64) return setup_one<KIND_EUC, 1, 2, 64, false>(&nb);
+    if (d == 64) return setup_one<KIND_EUC, 1, 2, 64, false>(&nb, variant == 1);
     return setup_one<KIND_EUC, 2, 2, 0, false>(&nb);
 }
 
 int sweep_variant_for(int kind, int d, int variant, long long tickets0, int num_sms) {
     if (int_kind(kind)) return variant;
-    if ((kind != KIND_EUC && kind != KIND_EUCF) || d != 12) return 0;
+    if (kind != KIND_EUC && kind != KIND_EUCF) return 0;
+    // d = 64: the tight frame ring (two blocks per SM) when the first level has
+    // three rounds of tickets for one block per SM or more
+    if (d == 64) return tickets0 >= 3LL * num_sms ? 1 : 0;
+    if (d != 12) return 0;
     int nb = 0;
     const cudaError_t e = kind == KIND_EUC ? setup_one<KIND_EUC, kEucR, kEucU, 12, false>(&nb)
                                            : setup_one<KIND_EUCF, kEucR, kEucU, 12, false>(&nb);
@@ -1749,14 +1774,14 @@ cudaError_t launch_sweep(int kind, int d, bool tags, const SweepArgs& A, int num
         if (d == 12 && variant == 1)
             return launch_one<KIND_EUCF, kEucR, kEucU, 12, false, false, kEucMinB>(A, num_sms, max_blocks, st);
         if (d == 12) return launch_one<KIND_EUCF, kEucR, kEucU, 12, false>(A, num_sms, max_blocks, st);
-        if (d == 64) return launch_one<KIND_EUCF, 1, 2, 64, false>(A, num_sms, max_blocks, st);
+        if (d == 64) return launch_one<KIND_EUCF, 1, 2, 64, false>(A, num_sms, max_blocks, st, variant == 1);
         return launch_one<KIND_EUCF, 2, 2, 0, false>(A, num_sms, max_blocks, st);
     }
     if (d == 12 && variant == 1)
         return launch_one<KIND_EUC, kEucR, kEucU, 12, false, false, kEucMinB>(A, num_sms, max_blocks, st);
     if (d == 12) return launch_one<KIND_EUC, kEucR, kEucU, 12, false>(A, num_sms, max_blocks, st);
     // d = 64: one row per lane (its frame in registers), column frames read in place
-    if (d == 64) return launch_one<KIND_EUC, 1, 2, 64, false>(A, num_sms, max_blocks, st);
+    if (d == 64) return launch_one<KIND_EUC, 1, 2, 64, false>(A, num_sms, max_blocks, st, variant == 1);
     return launch_one<KIND_EUC, 2, 2, 0, false>(A, num_sms, max_blocks, st);
 }
 
