@@ -33,17 +33,20 @@ DEFAULT_WINDOWS = 7
 
 
 def tune(M: int, N: int, *, variants=VARIANTS, windows=WINDOWS, base_areas=BASE_AREAS, reps: int = 3,
-         apply: bool = True) -> dict:
+         apply: bool = True, flush_l2: bool = True) -> dict:
     """Times every (variant, windows, base area) on an integer pair of M x N
     frames with CUDA events (median of ``reps`` after one warm-up) and returns
     {"variant", "windows", "base_area", "ms", "table"}; with ``apply`` the
-    fastest is set."""
+    fastest is set.  ``flush_l2``: each timed call starts with a cold L2 (a
+    256 MiB write before it, outside the events), as in a stream of alignments
+    of different pairs."""
     import torch
 
     X, Y = synth.int_pair(12345, M, N)
     Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
     path = torch.empty((M + N - 1, 2), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if flush_l2 else None
     table = []
     for v, w, a in itertools.product(variants, windows, base_areas):
         set_option(OPT_SWEEP_VARIANT, v)
@@ -52,6 +55,8 @@ def tune(M: int, N: int, *, variants=VARIANTS, windows=WINDOWS, base_areas=BASE_
         align(Xd, Yd, path_out=path)
         ms = []
         for _ in range(reps):
+            if flush is not None:
+                flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             align(Xd, Yd, path_out=path)
