@@ -254,7 +254,7 @@ Server& server() {
 
 static bool g_trace = getenv("DTW_SERVE_TRACE") != nullptr;
 // Engines that exist.  While another engine exists, an engine's sweeps run on
-// 7/8 of the SMs at most, one block per SM: a group's level of many bands would
+// 15/16 of the SMs at most, one block per SM: a group's level of many bands would
 // otherwise hold every SM with persistent blocks for the whole level (a level-0
 // block holds its ticket for milliseconds), and a request of another group that
 // arrives meanwhile would wait for that level to end.  Its plan kernel (1024
@@ -409,7 +409,7 @@ int Engine::iterate(std::mutex& mu, std::vector<std::pair<long long, Result>>& o
         SweepArgs sa{d_sweeps, ctl(), reinterpret_cast<unsigned long long*>(ws + L.bufpool), ws + L.outpool, d_sres,
                      d, spin_limit, -1};
         sa.tmap = reinterpret_cast<const int2*>(ws + L.tmap);
-        const long long cap = g_live_engines.load(std::memory_order_relaxed) > 1 ? num_sms - num_sms / 8 : 0;
+        const long long cap = g_live_engines.load(std::memory_order_relaxed) > 1 ? num_sms - num_sms / 16 : 0;
         if (e == cudaSuccess) e = launch_sweep(kind, d, kind == KIND_ABS, sa, num_sms, cap, st);
         SplitArgs sp{cur, n_cur, pairs(), pres(), kind, d, halo, d_sweeps, d_sres, ws + L.outpool, nxt, d_base,
                      ctl(), base_area, (int)L.cap_box, (int)L.cap_base, d_boxdone, ws + L.partials, -1, num_sms};
